@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of flooding Min-Sum decoding on one or more GB300s.
+
+Workload (one "step" = one pass of the whole decoding path over one batch): the
+quasi-cyclic code with a 12 x 24 base matrix of seeded shifts (about half nonzero) and
+circulant size Z = 96 (N = 2304, M = 1152), 65536 random codewords (uniform information
+bits encoded through Gaussian elimination on H), BPSK over AWGN with the frames split over
+Eb/N0 = 1.0, 1.5, 2.0, 2.5, 3.0 dB, decoded with 10 flooding iterations and no early stop.
+Throughput is codeword bits decoded per second (frames x N / time), the paper's definition
+(Section VI). Inputs are synthetic and seeded; the paper's own code (the CCSDS (8176, 1022)
+quasi-cyclic code) is not available, so this code stands in for it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank decodes its own batch (frames are independent: weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "decoded Gbit/s at fixed iters; HBM GB/s vs peak; learned vs plain iters@FER"
+SNRS = [1.0, 1.5, 2.0, 2.5, 3.0]
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["fp32", "fixed"], default="fp32")
+    ap.add_argument("--frames", type=int, default=65536)
+    ap.add_argument("--iters", type=int, default=10)
+    ap.add_argument("--variant", choices=["auto", "resident", "stream"], default="auto")
+    ap.add_argument("--quick", action="store_true", help="skip the extra measurements")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+
+def make_code():
+    from paper_2507_10424_gb300 import inputs
+    return inputs.cfg_qc_2304()
+
+
+def make_llr(code, F, seed):
+    from paper_2507_10424_gb300 import inputs
+    enc = inputs.Encoder(code)
+    cw = enc.random_codewords(F, seed)
+    llr = np.empty((F, code.N), np.float32)
+    bounds = np.linspace(0, F, len(SNRS) + 1).astype(int)
+    for k, e in enumerate(SNRS):
+        a, b = bounds[k], bounds[k + 1]
+        llr[a:b] = inputs.bpsk_awgn_llr(cw[a:b], e, code.design_rate, seed * 10 + k)
+    return cw, llr, bounds
+
+
+def edge_message_bytes(code, mode):
+    """Algorithmic bytes per frame per iteration: each edge message read and written once,
+    the channel value read once and the posterior read and written once."""
+    m, br, bs = (4, 4, 4) if mode == "fp32" else (2, 1, 2)
+    return 2 * code.E * m + code.N * (br + 2 * bs)
+
+
+def workload_name(code, F, L):
+    return (f"QC 12x24 base, Z=96: N={code.N} M={code.M} E={code.E}; {F} random codewords, "
+            f"Eb/N0 1.0-3.0 dB step 0.5; {L} flooding iterations, no early stop")
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.file = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.dev).uuid)
+            sel = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            sel = str(self.dev)
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", sel, f"--query-gpu=timestamp,{self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = open(self.file.name).read().strip().splitlines()
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        for r in rows:
+            p = [x.strip() for x in r.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                ts = time.mktime(time.strptime(p[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+            except Exception:
+                ts = None
+            if ts is not None and self.t0 is not None and not (self.t0 - 1 <= ts <= self.t1 + 1):
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                "sw_power_cap"), p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("resident_kernels.cu", "stream_kernels.cu", "ldpc_internal.h"):
+        with open(os.path.join(ROOT, "paper_2507_10424_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, mode, F):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to F frames,
+    or None when the kernel sources changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    e = t.get(f"{kernel}:{mode}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e["dram_bytes_per_launch"] * F / e["frames"]
+
+
+def cpu_threads():
+    return os.cpu_count() or 1
+
+
+def oracle_rate(code, llr, L, mode, budget_s=10.0, threads=None):
+    """Time the oracle (as it stands) on a bounded sample; returns (Gbit/s, frames, seconds)."""
+    import oracle
+    g = oracle.Graph.from_code(code)
+    threads = threads or cpu_threads()
+    run = (lambda x: oracle.decode_f32(g, x, L, early_stop=False, threads=threads, soft=False)) \
+        if mode == "fp32" else \
+        (lambda x: oracle.decode_fixed(g, oracle.quantize(x), L, early_stop=False, threads=threads,
+                                       soft=False))
+    n = max(threads, 16)
+    t = time.perf_counter()
+    run(llr[:n])
+    dt = time.perf_counter() - t
+    n = int(min(llr.shape[0], max(threads, n * budget_s / max(dt, 1e-3))))
+    t = time.perf_counter()
+    run(llr[:n])
+    dt = time.perf_counter() - t
+    return n * code.N / dt / 1e9, n, dt
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    code = make_code()
+    L = args.iters
+    threads = cpu_threads()
+    _, llr, _ = make_llr(code, 4096, 7)
+    g = oracle.Graph.from_code(code)
+
+    def step(x):
+        if args.mode == "fp32":
+            oracle.decode_f32(g, x, L, early_stop=False, threads=threads, soft=False)
+        else:
+            oracle.decode_fixed(g, oracle.quantize(x), L, early_stop=False, threads=threads, soft=False)
+
+    t = time.perf_counter()
+    step(llr[: max(threads, 32)])
+    per_frame = (time.perf_counter() - t) / max(threads, 32)
+    S = int(min(4096, max(threads, 0.5 / max(per_frame, 1e-6))))  # ~0.5 s per step
+    for w in range(args.warmup):
+        step(llr[:S])
+    t = time.perf_counter()
+    for k in range(args.steps):
+        step(llr[:S])
+    dt = time.perf_counter() - t
+    val = S * code.N * args.steps / dt / 1e9
+    sample = f"{S} of the workload's frames per step on {threads} host threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Gbit/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.mode == "fp32" else "i16",
+        "data": "synthetic", "config": {"workload": workload_name(code, S, L), "mode": args.mode},
+        "cpu_baseline": {"value": val, "unit": "Gbit/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_2507_10424_gb300 import build
+    build.build()
+    from paper_2507_10424_gb300.ldpc import Decoder
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    code = make_code()
+    F, L, mode = args.frames, args.iters, args.mode
+    cw, llr, bounds = make_llr(code, F, 1000 + rank)
+    dec = Decoder.from_code(code, mode=mode)
+    dec.set_variant(args.variant)
+    variant = dec.variant()
+    x = torch.from_numpy(llr).cuda()
+    bits = torch.empty((F, code.N), dtype=torch.uint8, device="cuda")
+    iters = torch.empty(F, dtype=torch.int32, device="cuda")
+    out = (bits, iters, None, None)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dec.decode(x, L, early_stop=False, out=out)
+
+    def timed(fn, K, W, sampler=None):
+        for _ in range(W):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if sampler:
+            sampler.mark("t0")
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.mark("t1")
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / K)
+
+    step()
+    torch.cuda.synchronize()
+    per_step_kernels = dec.last_kernel_count()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms = timed(step, args.steps, max(3, args.warmup), sampler)
+    clocks = sampler.stop()
+
+    bits_total = F * code.N * world
+    value = bits_total / (ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    B = edge_message_bytes(code, mode)
+    alg_bytes = F * L * B
+    kname = "k_resident" if variant == "resident" else "k_check"
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(kname, mode, F),
+                "kernel": kname, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_frame_iteration": B}
+
+    # frame error rate per SNR point (outside the timed region)
+    ber_fer = {}
+    wrong = (bits != torch.from_numpy(cw).cuda()).any(dim=1).cpu().numpy()
+    for k, e in enumerate(SNRS):
+        a, b = bounds[k], bounds[k + 1]
+        ber_fer[f"{e:.1f}dB"] = float(wrong[a:b].mean())
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if mode == "fp32" else "i16", "data": "synthetic",
+        "config": {"workload": workload_name(code, F, L), "frames_per_gpu": F, "iters": L,
+                   "early_stop": False, "mode": mode, "variant": variant,
+                   "l2": f"inputs larger than L2 ({llr.nbytes / 1e6:.0f} MB of LLRs per step)"},
+        "roofline": roofline,
+        "gpu_launches": per_step_kernels * args.steps,
+        "clocks": clocks,
+        "fer": ber_fer,
+    }
+
+    if not args.quick:
+        # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+        xh = torch.from_numpy(llr).pin_memory()
+        bh = torch.empty((F, code.N), dtype=torch.uint8).pin_memory()
+        ih = torch.empty(F, dtype=torch.int32).pin_memory()
+        hout = (bh, ih, None, None)
+        dec.decode_host(xh, L, early_stop=False, out=hout)
+        Ke = max(3, args.steps // 10)
+        barrier()
+        t = time.perf_counter()
+        for _ in range(Ke):
+            dec.decode_host(xh, L, early_stop=False, out=hout)
+        te = max_over_ranks((time.perf_counter() - t) / Ke)
+        assert (bh.numpy() == bits.cpu().numpy()).all()
+        result["e2e"] = {"value": bits_total / te / 1e9, "unit": "Gbit/s",
+                         "h2d_bytes_per_step": int(xh.numel() * 4),
+                         "d2h_bytes_per_step": int(bh.numel() + ih.numel() * 4),
+                         "ms_per_step": te * 1e3}
+        # the other arithmetic mode and the other kernel variant, same workload
+        others = {}
+        for m2, v2 in (("fixed" if mode == "fp32" else "fp32", "auto"), (mode, "stream")):
+            d2 = Decoder.from_code(code, mode=m2)
+            d2.set_variant(v2)
+            o2 = (torch.empty_like(bits), torch.empty_like(iters), None, None)
+            f2 = lambda: d2.decode(x, L, early_stop=False, out=o2)
+            ms2 = timed(f2, max(5, args.steps // 5), 3)
+            B2 = edge_message_bytes(code, m2)
+            ach2 = F * L * B2 / (ms2 * 1e-3) / 1e9
+            others[f"{m2}/{d2.variant()}"] = {
+                "value": bits_total / (ms2 * 1e-3) / 1e9, "unit": "Gbit/s", "ms_per_step": ms2,
+                "hbm_edge_message_GBs": ach2, "frac": ach2 / peak}
+            d2.close()
+        result["other_paths"] = others
+        if world == 1 and rank == 0:
+            val, n, dt = oracle_rate(code, llr, L, mode)
+            result["cpu_baseline"] = {"value": val, "unit": "Gbit/s", "cores": cpu_threads(),
+                                      "kind": "oracle",
+                                      "sample": f"{n} frames of this workload, {L} iterations "
+                                                f"({dt:.1f} s on {cpu_threads()} threads)"}
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

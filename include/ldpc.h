@@ -1,0 +1,171 @@
+/*
+ * ldpc.h -- C ABI of the GB300 (sm_103a) flooding Min-Sum LDPC decoder.
+ *
+ * The decoder implements Algorithm 1 of arXiv 2507.10424 ("A mapping of the Min-Sum
+ * decoder to reduction operations, and its implementation using CUDA kernels"):
+ *   - the parity matrix H is a run-time argument known only by its dimensions
+ *     (Section I and the abstract);
+ *   - check-node update, eq. (eta_update), computed through Observation 1 (the two
+ *     smallest magnitudes and the first location of the smallest) and Observation 2
+ *     (extrinsic sign = total sign product x own sign, sign(0) = +1, Section III);
+ *   - variable-node update, eq. (lambda_j): s_j = r_j + sum over the checks of bit j,
+ *     added in ascending check order starting from r_j;
+ *   - hard decision, eq. (slice), and the syndrome test H b = 0 over GF(2), eq. (1)-(2),
+ *     with per-frame early stop (the termination test of Algorithms 1 and 2).
+ *
+ * Conventions shared by every entry point:
+ *   - LLRs are log P(bit=0)/P(bit=1): positive favours 0 and the hard decision is
+ *     b_j = [s_j < 0]. The paper prints the opposite slicer ([s_j > 0] means 1), which
+ *     is consistent with its sign-product rule only for codes whose rows all have even
+ *     weight; it is available as LDPC_FLAG_PAPER_SLICER.
+ *   - Buffers are frame-major: frame f, bit j at [f * N + j].
+ *   - Decoding is asynchronous on the handle's stream (ldpc_set_stream); errors that the
+ *     host can detect are returned at once, and nothing is enqueued when a call fails.
+ *   - The caller owns every input and output buffer; the handle owns the device copy
+ *     of H and the decoding workspace, and frees both in ldpc_destroy.
+ *   - A handle is not thread-safe: use one handle per host thread / stream.
+ *
+ * Fixed-point mode (LDPC_MODE_FIXED): LLRs are quantised as
+ * q = clamp(round_half_even(4 * llr), -127, 127) (int8, step 0.25); lambda, eta and s are
+ * kept in [-32767, 32767] (int16 storage, int32 arithmetic, lambda and s saturate).
+ * FP32 mode computes in binary32 with round-to-nearest; its results are bit-identical to
+ * a sequential binary32 evaluation in the order stated above.
+ */
+#ifndef LDPC_H
+#define LDPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ldpc ldpc_t; /* opaque handle */
+
+/* Status codes. */
+#define LDPC_OK 0
+#define LDPC_ERR_INVALID_ARG (-1)  /* a size, flag or option is out of range */
+#define LDPC_ERR_INVALID_H (-2)    /* H entry not 0/1, duplicate/out-of-range index, row of weight 1, E >= 2^31 */
+#define LDPC_ERR_BAD_POINTER (-3)  /* NULL where required, or host memory where device memory is required */
+#define LDPC_ERR_OOM (-4)          /* device or host allocation failed */
+#define LDPC_ERR_CUDA (-5)         /* a CUDA runtime call failed; see ldpc_last_cuda_error */
+#define LDPC_ERR_UNSUPPORTED (-8)  /* the request needs a feature this build or device lacks */
+
+/* Arithmetic modes. */
+#define LDPC_MODE_FP32 0
+#define LDPC_MODE_FIXED 1
+
+/* H formats for ldpc_create_ex. */
+#define LDPC_H_DENSE_U8 0   /* h_a: uint8 [M][N], row-major, entries 0/1; h_b unused */
+#define LDPC_H_PACKED_U32 1 /* h_a: uint32 [M][ceil(N/32)]; bit (j%32) of word j/32 is H(i,j); unused high bits 0 */
+#define LDPC_H_CSR 2        /* h_a: int64 row_ptr [M+1]; h_b: int32 col_idx [row_ptr[M]] (any order in a row) */
+
+/* LLR element types for ldpc_decode_ex. */
+#define LDPC_LLR_F32 0
+#define LDPC_LLR_I8 1 /* already quantised (step 0.25); fixed mode only */
+
+/* Flags for ldpc_create_ex. */
+#define LDPC_FLAG_PAPER_SLICER 1 /* b_j = [s_j > 0], the slicer as printed in eq. (slice) */
+
+/* Kernel variants (ldpc_set_variant). */
+#define LDPC_VARIANT_AUTO 0     /* resident when a frame fits in shared memory, else streaming */
+#define LDPC_VARIANT_STREAM 1   /* messages in HBM, frame-interleaved, two kernels per iteration */
+#define LDPC_VARIANT_RESIDENT 2 /* one persistent kernel, frames resident in shared memory */
+
+/*
+ * ldpc_create: build a decoder for the M x N parity matrix H (host pointer, dense uint8,
+ * row-major, entries 0 or 1), FP32 mode, on the current CUDA device.
+ * Returns NULL on failure; ldpc_last_error() then gives the reason.
+ * H ingestion (Section II-B, the sets N_i and M_j): the rows and columns of H become a
+ * CSR/CSC edge list and bit-packed rows on the device; H is not retained by reference.
+ * Rows of weight 0 are always satisfied; rows of weight 1 are rejected (their minimum
+ * over the other neighbours is empty).
+ */
+ldpc_t *ldpc_create(int32_t M, int32_t N, const uint8_t *H);
+
+/* ldpc_create_ex: as ldpc_create, with the H format (LDPC_H_*), mode (LDPC_MODE_*) and
+ * flags (LDPC_FLAG_*) given. h_a / h_b are host pointers as described for each format. */
+ldpc_t *ldpc_create_ex(int32_t M, int32_t N, int32_t h_format, const void *h_a, const void *h_b,
+                       int32_t mode, int32_t flags);
+
+/*
+ * ldpc_decode: decode `frames` FP32 LLR frames (device pointer llr [frames][N]) with at
+ * most max_iter flooding iterations and early stop (syndrome tested before the first
+ * iteration and after every iteration). Writes the hard decisions (device uint8
+ * out_bits [frames][N], values 0/1) and the iteration count per frame (device int32
+ * out_iters [frames]: 0 if the input already satisfies H, else the iteration after which
+ * the syndrome was zero, else max_iter). In fixed mode the LLRs are quantised first.
+ * frames == 0 is a no-op; frames < 0 or max_iter < 0 give LDPC_ERR_INVALID_ARG.
+ */
+int ldpc_decode(ldpc_t *h, const float *llr, int32_t frames, int32_t max_iter, uint8_t *out_bits,
+                int32_t *out_iters);
+
+/* ldpc_decode_i8: as ldpc_decode for pre-quantised int8 LLRs (device pointer, step 0.25);
+ * fixed mode only (LDPC_ERR_INVALID_ARG otherwise). */
+int ldpc_decode_i8(ldpc_t *h, const int8_t *llr_q, int32_t frames, int32_t max_iter,
+                   uint8_t *out_bits, int32_t *out_iters);
+
+/*
+ * ldpc_decode_ex: the general form. llr_dtype is LDPC_LLR_F32 or LDPC_LLR_I8.
+ * early_stop = 0 runs exactly max_iter iterations (out_iters = max_iter for every frame).
+ * check_every >= 1: with early stop, the syndrome is tested before the first iteration
+ * and after iterations that are multiples of check_every (the paper tests every 6th).
+ * out_ok (nullable, device uint8 [frames]): 1 if the returned bits satisfy H.
+ * out_soft (nullable, device float [frames][N]): the posterior s of the returned bits,
+ * in LLR units (fixed mode: s / 4, exact).
+ */
+int ldpc_decode_ex(ldpc_t *h, const void *llr, int32_t llr_dtype, int32_t frames, int32_t max_iter,
+                   int32_t early_stop, int32_t check_every, uint8_t *out_bits, int32_t *out_iters,
+                   uint8_t *out_ok, float *out_soft);
+
+/*
+ * ldpc_decode_host: ldpc_decode_ex with HOST buffers (preferably pinned): the LLRs are
+ * copied to the device in chunks, decoded and the results copied back, with the copies
+ * of one chunk overlapping the decoding of another. Synchronous: returns when the
+ * results are in the host buffers. out_ok and out_soft may be NULL.
+ */
+int ldpc_decode_host(ldpc_t *h, const void *llr_host, int32_t llr_dtype, int32_t frames,
+                     int32_t max_iter, int32_t early_stop, int32_t check_every,
+                     uint8_t *bits_host, int32_t *iters_host, uint8_t *ok_host, float *soft_host);
+
+/* ldpc_set_stream: decode on this cudaStream_t (NULL = legacy default stream). */
+int ldpc_set_stream(ldpc_t *h, void *cuda_stream);
+
+/* ldpc_set_mode: switch between LDPC_MODE_FP32 and LDPC_MODE_FIXED. */
+int ldpc_set_mode(ldpc_t *h, int32_t mode);
+
+/* ldpc_set_variant: choose the kernel variant (LDPC_VARIANT_*). RESIDENT fails with
+ * LDPC_ERR_UNSUPPORTED when one frame of this code does not fit in shared memory. */
+int ldpc_set_variant(ldpc_t *h, int32_t variant);
+
+/* ldpc_get_variant: the variant the next decode will run (AUTO resolved). */
+int ldpc_get_variant(const ldpc_t *h, int32_t *variant);
+
+/* ldpc_reserve: pre-size the workspace for up to max_frames frames per call (otherwise
+ * it grows on demand). Allocation happens here, never inside a timed decode. */
+int ldpc_reserve(ldpc_t *h, int32_t max_frames);
+
+/* ldpc_info: dimensions and degree statistics of H (any pointer may be NULL). */
+int ldpc_info(const ldpc_t *h, int32_t *M, int32_t *N, int64_t *E, int32_t *max_dc,
+              int32_t *max_dv);
+
+/* ldpc_last_kernel_count: number of kernels the last decode call launched. */
+int ldpc_last_kernel_count(const ldpc_t *h, int32_t *count);
+
+/* ldpc_last_error: status of the last failing call on this host thread (0 if none). */
+int ldpc_last_error(void);
+
+/* ldpc_last_cuda_error: the cudaError_t behind the last LDPC_ERR_CUDA on this thread. */
+int ldpc_last_cuda_error(void);
+
+/* ldpc_strerror: static text for a status code. */
+const char *ldpc_strerror(int status);
+
+/* ldpc_destroy: free the handle (waits for its stream). NULL is ignored. */
+void ldpc_destroy(ldpc_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDPC_H */

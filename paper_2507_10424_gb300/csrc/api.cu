@@ -1,0 +1,469 @@
+// C ABI of the decoder: handle life cycle, argument checks, workspace, dispatch to the
+// resident or streaming kernels, and the host-buffer pipeline.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/ldpc.h"
+#include "ldpc_internal.h"
+
+using namespace ldpc_impl;
+
+namespace {
+thread_local int g_last_error = LDPC_OK;
+thread_local int g_last_cuda = 0;
+
+int fail(int status) {
+    g_last_error = status;
+    return status;
+}
+int cuda_fail(cudaError_t e) {
+    g_last_cuda = (int)e;
+    return fail(LDPC_ERR_CUDA);
+}
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+template <typename T>
+int upload(T** dst, const T* src, size_t n) {
+    *dst = nullptr;
+    cudaError_t e = cudaMalloc((void**)dst, (n ? n : 1) * sizeof(T));  // never a null array
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(LDPC_ERR_OOM) : cuda_fail(e);
+    if (src && n) {
+        e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return LDPC_OK;
+}
+}  // namespace
+
+struct ldpc {
+    int device = 0, num_sms = 0;
+    int mode = kModeFP32, flags = 0, variant = LDPC_VARIANT_AUTO;
+    int32_t M = 0, N = 0, max_dc = 0, max_dv = 0;
+    int64_t E = 0;
+    DevGraph dg;
+    ResidentPlan plan[2];
+    cudaStream_t stream = nullptr;
+    // streaming workspace
+    StreamWork sw;
+    int32_t sw_cap = 0, sw_cap_L = -1;
+    void* sw_big = nullptr;
+    uint8_t* sw_unsat = nullptr;
+    int32_t* counters = nullptr;  // [0] resident tile counter, [1] streaming done count
+    int32_t last_launches = 0;
+    // host pipeline staging (2 slots)
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
+    void* stage[2] = {};
+    size_t stage_bytes = 0;
+};
+
+static void free_graph(DevGraph& g) {
+    void* ptrs[] = {g.row_ptr, g.col_idx, g.col_ptr, g.col_edge, g.packed, g.s_slice_base,
+                    g.s_row_deg, g.s_slot_col, g.s_col_ptr, g.s_col_slot16, g.s_col_slot32};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    g = DevGraph();
+}
+
+static void free_stream_work(ldpc_t* h) {
+    if (h->sw_big) cudaFree(h->sw_big);
+    if (h->sw_unsat) cudaFree(h->sw_unsat);
+    h->sw_big = nullptr;
+    h->sw_unsat = nullptr;
+    h->sw = StreamWork();
+    h->sw_cap = 0;
+    h->sw_cap_L = -1;
+}
+
+static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L) {
+    const int32_t Fp = (frames + 255) & ~255;
+    if (Fp > h->sw_cap) {
+        if (h->sw_big) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->sw_big);
+            h->sw_big = nullptr;
+        }
+        const size_t tb = 4, rb = 4;  // sized for fp32; the fixed mode uses less
+        const size_t eta = (size_t)h->E * Fp * tb, sb = (size_t)h->N * Fp * tb,
+                     rr = (size_t)h->N * Fp * rb;
+        const size_t total = eta + sb + rr + (size_t)Fp * 4 + (size_t)Fp + 1024;
+        cudaError_t e = cudaMalloc(&h->sw_big, total);
+        if (e != cudaSuccess) {
+            h->sw_big = nullptr;
+            h->sw_cap = 0;
+            return e == cudaErrorMemoryAllocation ? fail(LDPC_ERR_OOM) : cuda_fail(e);
+        }
+        char* p = (char*)h->sw_big;
+        h->sw.eta = p;
+        p += (eta + 255) & ~(size_t)255;
+        h->sw.s = p;
+        p += (sb + 255) & ~(size_t)255;
+        h->sw.r = p;
+        p += (rr + 255) & ~(size_t)255;
+        h->sw.done_iter = (int32_t*)p;
+        p += (size_t)Fp * 4;
+        h->sw.state = (uint8_t*)p;
+        h->sw_cap = Fp;
+        h->sw_cap_L = -1;  // unsat depends on Fp too
+    }
+    if (L > h->sw_cap_L) {
+        if (h->sw_unsat) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->sw_unsat);
+            h->sw_unsat = nullptr;
+        }
+        cudaError_t e = cudaMalloc((void**)&h->sw_unsat, (size_t)(L + 2) * h->sw_cap);
+        if (e != cudaSuccess) {
+            h->sw_cap_L = -1;
+            return e == cudaErrorMemoryAllocation ? fail(LDPC_ERR_OOM) : cuda_fail(e);
+        }
+        h->sw_cap_L = L;
+    }
+    h->sw.Fp = Fp;
+    h->sw.unsat = h->sw_unsat;
+    h->sw.n_done = h->counters + 1;
+    return LDPC_OK;
+}
+
+static int resolved_variant(const ldpc_t* h) {
+    if (h->variant == LDPC_VARIANT_STREAM) return LDPC_VARIANT_STREAM;
+    if (h->variant == LDPC_VARIANT_RESIDENT) return LDPC_VARIANT_RESIDENT;
+    return h->plan[h->mode].ok ? LDPC_VARIANT_RESIDENT : LDPC_VARIANT_STREAM;
+}
+
+static int is_device_ptr(const void* p) {
+    if (!p) return 0;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
+    ldpc_t* h = new (std::nothrow) ldpc_t();
+    if (!h) {
+        fail(LDPC_ERR_OOM);
+        return nullptr;
+    }
+    h->mode = mode;
+    h->flags = flags;
+    h->M = hg.M;
+    h->N = hg.N;
+    h->E = hg.E;
+    h->max_dc = hg.max_dc;
+    h->max_dv = hg.max_dv;
+    int rc = LDPC_OK;
+    auto bail = [&](int status) -> ldpc_t* {
+        free_graph(h->dg);
+        if (h->counters) cudaFree(h->counters);
+        delete h;
+        if (status != LDPC_OK) g_last_error = status;
+        return nullptr;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e));
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e));
+    // CSR / CSC
+    if ((rc = upload(&h->dg.row_ptr, hg.row_ptr.data(), hg.row_ptr.size())) ||
+        (rc = upload(&h->dg.col_idx, hg.col_idx.data(), hg.col_idx.size())) ||
+        (rc = upload(&h->dg.col_ptr, hg.col_ptr.data(), hg.col_ptr.size())) ||
+        (rc = upload(&h->dg.col_edge, hg.col_edge.data(), hg.col_edge.size())))
+        return bail(rc);
+    // bit-packed rows
+    {
+        const int64_t W = (hg.N + 31) / 32;
+        std::vector<uint32_t> packed((size_t)hg.M * W, 0u);
+        for (int32_t i = 0; i < hg.M; i++)
+            for (int32_t e2 = hg.row_ptr[i]; e2 < hg.row_ptr[i + 1]; e2++)
+                packed[(size_t)i * W + hg.col_idx[e2] / 32] |= 1u << (hg.col_idx[e2] % 32);
+        if ((rc = upload(&h->dg.packed, packed.data(), packed.size()))) return bail(rc);
+    }
+    // sliced layout for the resident kernel (codes small enough to be resident)
+    if (hg.N <= 65535 && hg.max_dc <= 255 && hg.E < (1 << 26)) {
+        SlicedGraph sg;
+        build_sliced(hg, sg);
+        h->dg.n_slices = sg.n_slices;
+        h->dg.E_pad = sg.E_pad;
+        if ((rc = upload(&h->dg.s_slice_base, sg.slice_base.data(), sg.slice_base.size())) ||
+            (rc = upload(&h->dg.s_row_deg, sg.row_deg.data(), sg.row_deg.size())) ||
+            (rc = upload(&h->dg.s_slot_col, sg.slot_col.data(), sg.slot_col.size())) ||
+            (rc = upload(&h->dg.s_col_ptr, sg.col_ptr.data(), sg.col_ptr.size())))
+            return bail(rc);
+        if (!sg.col_slot16.empty()) {
+            if ((rc = upload(&h->dg.s_col_slot16, sg.col_slot16.data(), sg.col_slot16.size()))) return bail(rc);
+        } else {
+            if ((rc = upload(&h->dg.s_col_slot32, sg.col_slot32.data(), sg.col_slot32.size()))) return bail(rc);
+        }
+        h->plan[kModeFP32] = resident_plan(kModeFP32, h->dg, hg.M, hg.N, h->device);
+        h->plan[kModeFixed] = resident_plan(kModeFixed, h->dg, hg.M, hg.N, h->device);
+    }
+    e = cudaMalloc((void**)&h->counters, 4 * sizeof(int32_t));
+    if (e != cudaSuccess) return bail(cuda_fail(e));
+    g_last_error = LDPC_OK;
+    return h;
+}
+
+extern "C" {
+
+ldpc_t* ldpc_create_ex(int32_t M, int32_t N, int32_t h_format, const void* h_a, const void* h_b,
+                       int32_t mode, int32_t flags) {
+    if (mode != LDPC_MODE_FP32 && mode != LDPC_MODE_FIXED) {
+        fail(LDPC_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    if (flags & ~LDPC_FLAG_PAPER_SLICER) {
+        fail(LDPC_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    if (M <= 0 || N <= 0) {
+        fail(LDPC_ERR_INVALID_H);
+        return nullptr;
+    }
+    HostGraph hg;
+    int rc;
+    switch (h_format) {
+        case LDPC_H_DENSE_U8: rc = graph_from_dense(M, N, (const uint8_t*)h_a, hg); break;
+        case LDPC_H_PACKED_U32: rc = graph_from_packed(M, N, (const uint32_t*)h_a, hg); break;
+        case LDPC_H_CSR: rc = graph_from_csr(M, N, (const int64_t*)h_a, (const int32_t*)h_b, hg); break;
+        default: rc = LDPC_ERR_INVALID_ARG;
+    }
+    if (rc != LDPC_OK) {
+        fail(rc);
+        return nullptr;
+    }
+    return create_from_graph(hg, mode, flags);
+}
+
+ldpc_t* ldpc_create(int32_t M, int32_t N, const uint8_t* H) {
+    return ldpc_create_ex(M, N, LDPC_H_DENSE_U8, H, nullptr, LDPC_MODE_FP32, 0);
+}
+
+int ldpc_decode_ex(ldpc_t* h, const void* llr, int32_t llr_dtype, int32_t frames, int32_t max_iter,
+                   int32_t early_stop, int32_t check_every, uint8_t* out_bits, int32_t* out_iters,
+                   uint8_t* out_ok, float* out_soft) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (frames < 0 || max_iter < 0 || check_every < 1) return fail(LDPC_ERR_INVALID_ARG);
+    if (llr_dtype != LDPC_LLR_F32 && llr_dtype != LDPC_LLR_I8) return fail(LDPC_ERR_INVALID_ARG);
+    if (llr_dtype == LDPC_LLR_I8 && h->mode != kModeFixed) return fail(LDPC_ERR_INVALID_ARG);
+    h->last_launches = 0;
+    if (frames == 0) return LDPC_OK;
+    if (!is_device_ptr(llr) || !is_device_ptr(out_bits) || !is_device_ptr(out_iters) ||
+        (out_ok && !is_device_ptr(out_ok)) || (out_soft && !is_device_ptr(out_soft)))
+        return fail(LDPC_ERR_BAD_POINTER);
+    DecodeArgs a;
+    a.M = h->M;
+    a.N = h->N;
+    a.E = (int32_t)h->E;
+    a.frames = frames;
+    a.L = max_iter;
+    a.early_stop = early_stop ? 1 : 0;
+    a.check_every = check_every;
+    a.paper_slicer = (h->flags & LDPC_FLAG_PAPER_SLICER) ? 1 : 0;
+    a.llr_is_i8 = llr_dtype == LDPC_LLR_I8;
+    a.llr = llr;
+    a.out_bits = out_bits;
+    a.out_iters = out_iters;
+    a.out_ok = out_ok;
+    a.out_soft = out_soft;
+    int n;
+    if (resolved_variant(h) == LDPC_VARIANT_RESIDENT) {
+        if (!h->plan[h->mode].ok) return fail(LDPC_ERR_UNSUPPORTED);
+        n = resident_decode(h->mode, h->dg, h->plan[h->mode], a, h->counters, h->num_sms, h->stream);
+    } else {
+        int rc = ensure_stream_work(h, frames, max_iter);
+        if (rc != LDPC_OK) return rc;
+        n = stream_decode(h->mode, h->dg, a, h->sw, h->stream);
+    }
+    if (n < 0) {
+        cudaError_t e = cudaGetLastError();
+        return e != cudaSuccess ? cuda_fail(e) : fail(n);
+    }
+    h->last_launches = n;
+    return LDPC_OK;
+}
+
+int ldpc_decode(ldpc_t* h, const float* llr, int32_t frames, int32_t max_iter, uint8_t* out_bits,
+                int32_t* out_iters) {
+    return ldpc_decode_ex(h, llr, LDPC_LLR_F32, frames, max_iter, 1, 1, out_bits, out_iters, nullptr,
+                          nullptr);
+}
+
+int ldpc_decode_i8(ldpc_t* h, const int8_t* llr_q, int32_t frames, int32_t max_iter,
+                   uint8_t* out_bits, int32_t* out_iters) {
+    if (h && h->mode != kModeFixed) return fail(LDPC_ERR_INVALID_ARG);
+    return ldpc_decode_ex(h, llr_q, LDPC_LLR_I8, frames, max_iter, 1, 1, out_bits, out_iters,
+                          nullptr, nullptr);
+}
+
+int ldpc_decode_host(ldpc_t* h, const void* llr_host, int32_t llr_dtype, int32_t frames,
+                     int32_t max_iter, int32_t early_stop, int32_t check_every, uint8_t* bits_host,
+                     int32_t* iters_host, uint8_t* ok_host, float* soft_host) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (frames < 0 || max_iter < 0 || check_every < 1) return fail(LDPC_ERR_INVALID_ARG);
+    if (llr_dtype != LDPC_LLR_F32 && llr_dtype != LDPC_LLR_I8) return fail(LDPC_ERR_INVALID_ARG);
+    if (frames == 0) return LDPC_OK;
+    if (!llr_host || !bits_host || !iters_host) return fail(LDPC_ERR_BAD_POINTER);
+    const int N = h->N;
+    const size_t in_b = llr_dtype == LDPC_LLR_F32 ? 4 : 1;
+    // chunk so that several chunks are in flight and each still fills the GPU
+    int32_t chunk = std::max<int32_t>(1024, std::min<int32_t>(frames, (frames + 3) / 4));
+    chunk = std::min<int32_t>(chunk, std::max<int32_t>(1024, (int32_t)((512ull << 20) / (N * in_b))));
+    const size_t per_frame = (size_t)N * in_b + (size_t)N + 4 + 1 + (soft_host ? (size_t)N * 4 : 0);
+    const size_t need = ((size_t)chunk * per_frame + 4096);
+    if (!h->h2d) {
+        CK(cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking));
+        for (int s = 0; s < 2; s++) {
+            CK(cudaEventCreateWithFlags(&h->ev_h2d[s], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->ev_comp[s], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->ev_d2h[s], cudaEventDisableTiming));
+        }
+    }
+    if (need > h->stage_bytes) {
+        for (int s = 0; s < 2; s++) {
+            if (h->stage[s]) {
+                cudaStreamSynchronize(h->d2h);
+                cudaFree(h->stage[s]);
+                h->stage[s] = nullptr;
+            }
+            cudaError_t e = cudaMalloc(&h->stage[s], need);
+            if (e != cudaSuccess) {
+                h->stage_bytes = 0;
+                return e == cudaErrorMemoryAllocation ? fail(LDPC_ERR_OOM) : cuda_fail(e);
+            }
+        }
+        h->stage_bytes = need;
+    }
+    int launches = 0;
+    const int nchunks = (frames + chunk - 1) / chunk;
+    for (int c = 0; c < nchunks; c++) {
+        const int s = c & 1;
+        const int32_t f0 = c * chunk, nf = std::min(chunk, frames - f0);
+        char* base = (char*)h->stage[s];
+        void* d_llr = base;
+        uint8_t* d_bits = (uint8_t*)(base + (((size_t)chunk * N * in_b + 255) & ~(size_t)255));
+        int32_t* d_iters = (int32_t*)((char*)d_bits + (((size_t)chunk * N + 255) & ~(size_t)255));
+        uint8_t* d_ok = (uint8_t*)(d_iters + ((chunk + 63) & ~63));
+        float* d_soft = soft_host ? (float*)(d_ok + ((chunk + 255) & ~255)) : nullptr;
+        if (c >= 2) CK(cudaStreamWaitEvent(h->h2d, h->ev_d2h[s], 0));
+        CK(cudaMemcpyAsync(d_llr, (const char*)llr_host + (size_t)f0 * N * in_b, (size_t)nf * N * in_b,
+                           cudaMemcpyHostToDevice, h->h2d));
+        CK(cudaEventRecord(h->ev_h2d[s], h->h2d));
+        CK(cudaStreamWaitEvent(h->stream, h->ev_h2d[s], 0));
+        int rc = ldpc_decode_ex(h, d_llr, llr_dtype, nf, max_iter, early_stop, check_every, d_bits,
+                                d_iters, ok_host ? d_ok : nullptr, d_soft);
+        if (rc != LDPC_OK) return rc;
+        launches += h->last_launches;
+        CK(cudaEventRecord(h->ev_comp[s], h->stream));
+        CK(cudaStreamWaitEvent(h->d2h, h->ev_comp[s], 0));
+        CK(cudaMemcpyAsync(bits_host + (size_t)f0 * N, d_bits, (size_t)nf * N, cudaMemcpyDeviceToHost, h->d2h));
+        CK(cudaMemcpyAsync(iters_host + f0, d_iters, (size_t)nf * 4, cudaMemcpyDeviceToHost, h->d2h));
+        if (ok_host) CK(cudaMemcpyAsync(ok_host + f0, d_ok, (size_t)nf, cudaMemcpyDeviceToHost, h->d2h));
+        if (soft_host)
+            CK(cudaMemcpyAsync(soft_host + (size_t)f0 * N, d_soft, (size_t)nf * N * 4,
+                               cudaMemcpyDeviceToHost, h->d2h));
+        CK(cudaEventRecord(h->ev_d2h[s], h->d2h));
+    }
+    CK(cudaStreamSynchronize(h->d2h));
+    h->last_launches = launches;
+    return LDPC_OK;
+}
+
+int ldpc_set_stream(ldpc_t* h, void* cuda_stream) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    h->stream = (cudaStream_t)cuda_stream;
+    return LDPC_OK;
+}
+
+int ldpc_set_mode(ldpc_t* h, int32_t mode) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (mode != LDPC_MODE_FP32 && mode != LDPC_MODE_FIXED) return fail(LDPC_ERR_INVALID_ARG);
+    h->mode = mode;
+    return LDPC_OK;
+}
+
+int ldpc_set_variant(ldpc_t* h, int32_t variant) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (variant < LDPC_VARIANT_AUTO || variant > LDPC_VARIANT_RESIDENT) return fail(LDPC_ERR_INVALID_ARG);
+    if (variant == LDPC_VARIANT_RESIDENT && !h->plan[h->mode].ok) return fail(LDPC_ERR_UNSUPPORTED);
+    h->variant = variant;
+    return LDPC_OK;
+}
+
+int ldpc_get_variant(const ldpc_t* h, int32_t* variant) {
+    if (!h || !variant) return fail(LDPC_ERR_BAD_POINTER);
+    *variant = resolved_variant(h);
+    return LDPC_OK;
+}
+
+int ldpc_reserve(ldpc_t* h, int32_t max_frames) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (max_frames < 0) return fail(LDPC_ERR_INVALID_ARG);
+    if (resolved_variant(h) == LDPC_VARIANT_STREAM && max_frames > 0)
+        return ensure_stream_work(h, max_frames, std::max(h->sw_cap_L, 64));
+    return LDPC_OK;
+}
+
+int ldpc_info(const ldpc_t* h, int32_t* M, int32_t* N, int64_t* E, int32_t* max_dc, int32_t* max_dv) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (M) *M = h->M;
+    if (N) *N = h->N;
+    if (E) *E = h->E;
+    if (max_dc) *max_dc = h->max_dc;
+    if (max_dv) *max_dv = h->max_dv;
+    return LDPC_OK;
+}
+
+int ldpc_last_kernel_count(const ldpc_t* h, int32_t* count) {
+    if (!h || !count) return fail(LDPC_ERR_BAD_POINTER);
+    *count = h->last_launches;
+    return LDPC_OK;
+}
+
+int ldpc_last_error(void) { return g_last_error; }
+int ldpc_last_cuda_error(void) { return g_last_cuda; }
+
+const char* ldpc_strerror(int status) {
+    switch (status) {
+        case LDPC_OK: return "ok";
+        case LDPC_ERR_INVALID_ARG: return "invalid argument";
+        case LDPC_ERR_INVALID_H: return "invalid parity matrix";
+        case LDPC_ERR_BAD_POINTER: return "bad pointer (NULL, or host memory where device memory is required)";
+        case LDPC_ERR_OOM: return "out of memory";
+        case LDPC_ERR_CUDA: return "CUDA runtime error";
+        case LDPC_ERR_UNSUPPORTED: return "unsupported for this code or device";
+    }
+    return "unknown status";
+}
+
+void ldpc_destroy(ldpc_t* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    if (h->h2d) {
+        cudaStreamSynchronize(h->h2d);
+        cudaStreamSynchronize(h->d2h);
+        for (int s = 0; s < 2; s++) {
+            if (h->stage[s]) cudaFree(h->stage[s]);
+            cudaEventDestroy(h->ev_h2d[s]);
+            cudaEventDestroy(h->ev_comp[s]);
+            cudaEventDestroy(h->ev_d2h[s]);
+        }
+        cudaStreamDestroy(h->h2d);
+        cudaStreamDestroy(h->d2h);
+    }
+    free_stream_work(h);
+    free_graph(h->dg);
+    if (h->counters) cudaFree(h->counters);
+    delete h;
+}
+
+}  // extern "C"

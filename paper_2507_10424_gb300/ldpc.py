@@ -1,0 +1,308 @@
+"""Python binding of ``libldpc.so`` (argument marshalling only).
+
+Every decoding step runs in the library's CUDA kernels; this module passes pointers,
+sizes and the current torch stream through ctypes. The functions carry the C names of
+``include/ldpc.h``; :class:`Decoder` wraps them for torch tensors. Loading fails loudly
+when the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libldpc.so")
+
+LDPC_OK = 0
+LDPC_ERR_INVALID_ARG = -1
+LDPC_ERR_INVALID_H = -2
+LDPC_ERR_BAD_POINTER = -3
+LDPC_ERR_OOM = -4
+LDPC_ERR_CUDA = -5
+LDPC_ERR_UNSUPPORTED = -8
+LDPC_MODE_FP32 = 0
+LDPC_MODE_FIXED = 1
+LDPC_H_DENSE_U8 = 0
+LDPC_H_PACKED_U32 = 1
+LDPC_H_CSR = 2
+LDPC_LLR_F32 = 0
+LDPC_LLR_I8 = 1
+LDPC_FLAG_PAPER_SLICER = 1
+LDPC_VARIANT_AUTO = 0
+LDPC_VARIANT_STREAM = 1
+LDPC_VARIANT_RESIDENT = 2
+
+# name -> (restype, argtypes), exactly the declarations of include/ldpc.h
+P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+PI32, PI64 = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "ldpc_create": (P, [I32, I32, P]),
+    "ldpc_create_ex": (P, [I32, I32, I32, P, P, I32, I32]),
+    "ldpc_decode": (ctypes.c_int, [P, P, I32, I32, P, P]),
+    "ldpc_decode_i8": (ctypes.c_int, [P, P, I32, I32, P, P]),
+    "ldpc_decode_ex": (ctypes.c_int, [P, P, I32, I32, I32, I32, I32, P, P, P, P]),
+    "ldpc_decode_host": (ctypes.c_int, [P, P, I32, I32, I32, I32, I32, P, P, P, P]),
+    "ldpc_set_stream": (ctypes.c_int, [P, P]),
+    "ldpc_set_mode": (ctypes.c_int, [P, I32]),
+    "ldpc_set_variant": (ctypes.c_int, [P, I32]),
+    "ldpc_get_variant": (ctypes.c_int, [P, PI32]),
+    "ldpc_reserve": (ctypes.c_int, [P, I32]),
+    "ldpc_info": (ctypes.c_int, [P, PI32, PI32, PI64, PI32, PI32]),
+    "ldpc_last_kernel_count": (ctypes.c_int, [P, PI32]),
+    "ldpc_last_error": (ctypes.c_int, []),
+    "ldpc_last_cuda_error": (ctypes.c_int, []),
+    "ldpc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "ldpc_destroy": (None, [P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (raises if it is missing: build it with ``build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing; build it with paper_2507_10424_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class LdpcError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        msg = load().ldpc_strerror(status).decode()
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+        self.status = status
+
+
+def _check(status: int, what: str):
+    if status != LDPC_OK:
+        raise LdpcError(status, what)
+
+
+def _host(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+# ----------------------------------------------------------- thin C-name wrappers
+
+def ldpc_create(M: int, N: int, H: np.ndarray):
+    return load().ldpc_create(M, N, _host(np.ascontiguousarray(H, dtype=np.uint8)))
+
+
+def ldpc_create_ex(M, N, h_format, h_a, h_b, mode, flags):
+    return load().ldpc_create_ex(M, N, h_format, h_a, h_b, mode, flags)
+
+
+def ldpc_decode(h, llr_ptr, frames, max_iter, bits_ptr, iters_ptr):
+    return load().ldpc_decode(h, llr_ptr, frames, max_iter, bits_ptr, iters_ptr)
+
+
+def ldpc_decode_i8(h, llr_ptr, frames, max_iter, bits_ptr, iters_ptr):
+    return load().ldpc_decode_i8(h, llr_ptr, frames, max_iter, bits_ptr, iters_ptr)
+
+
+def ldpc_decode_ex(h, llr_ptr, llr_dtype, frames, max_iter, early_stop, check_every, bits_ptr,
+                   iters_ptr, ok_ptr, soft_ptr):
+    return load().ldpc_decode_ex(h, llr_ptr, llr_dtype, frames, max_iter, early_stop, check_every,
+                                 bits_ptr, iters_ptr, ok_ptr, soft_ptr)
+
+
+def ldpc_decode_host(h, llr_ptr, llr_dtype, frames, max_iter, early_stop, check_every, bits_ptr,
+                     iters_ptr, ok_ptr, soft_ptr):
+    return load().ldpc_decode_host(h, llr_ptr, llr_dtype, frames, max_iter, early_stop, check_every,
+                                   bits_ptr, iters_ptr, ok_ptr, soft_ptr)
+
+
+def ldpc_set_stream(h, stream_ptr):
+    return load().ldpc_set_stream(h, stream_ptr)
+
+
+def ldpc_set_mode(h, mode):
+    return load().ldpc_set_mode(h, mode)
+
+
+def ldpc_set_variant(h, variant):
+    return load().ldpc_set_variant(h, variant)
+
+
+def ldpc_get_variant(h):
+    v = ctypes.c_int32()
+    _check(load().ldpc_get_variant(h, ctypes.byref(v)), "ldpc_get_variant")
+    return v.value
+
+
+def ldpc_reserve(h, max_frames):
+    return load().ldpc_reserve(h, max_frames)
+
+
+def ldpc_info(h):
+    M, N, dc, dv = (ctypes.c_int32() for _ in range(4))
+    E = ctypes.c_int64()
+    _check(load().ldpc_info(h, ctypes.byref(M), ctypes.byref(N), ctypes.byref(E), ctypes.byref(dc),
+                            ctypes.byref(dv)), "ldpc_info")
+    return dict(M=M.value, N=N.value, E=E.value, max_dc=dc.value, max_dv=dv.value)
+
+
+def ldpc_last_kernel_count(h):
+    c = ctypes.c_int32()
+    _check(load().ldpc_last_kernel_count(h, ctypes.byref(c)), "ldpc_last_kernel_count")
+    return c.value
+
+
+def ldpc_last_error():
+    return load().ldpc_last_error()
+
+
+def ldpc_last_cuda_error():
+    return load().ldpc_last_cuda_error()
+
+
+def ldpc_strerror(status):
+    return load().ldpc_strerror(status).decode()
+
+
+def ldpc_destroy(h):
+    load().ldpc_destroy(h)
+
+
+# ----------------------------------------------------------- torch-facing wrapper
+
+class Decoder:
+    """A decoder handle for one parity matrix.
+
+    ``H`` may be a dense 0/1 matrix (numpy, [M][N]), or give ``csr=(row_ptr, col_idx)`` or
+    ``packed=uint32 [M][ceil(N/32)]`` with ``M`` and ``N``. ``mode`` is "fp32" or "fixed".
+    """
+
+    def __init__(self, H=None, *, M=None, N=None, csr=None, packed=None, mode="fp32",
+                 paper_slicer=False):
+        lib = load()
+        m = {"fp32": LDPC_MODE_FP32, "fixed": LDPC_MODE_FIXED}[mode]
+        flags = LDPC_FLAG_PAPER_SLICER if paper_slicer else 0
+        keep = []
+        if H is not None:
+            Hn = np.ascontiguousarray(H, dtype=np.uint8)
+            M, N = Hn.shape
+            keep.append(Hn)
+            args = (LDPC_H_DENSE_U8, _host(Hn), None)
+        elif csr is not None:
+            rp = np.ascontiguousarray(csr[0], dtype=np.int64)
+            ci = np.ascontiguousarray(csr[1], dtype=np.int32)
+            keep += [rp, ci]
+            args = (LDPC_H_CSR, _host(rp), _host(ci))
+        elif packed is not None:
+            pk = np.ascontiguousarray(packed, dtype=np.uint32)
+            keep.append(pk)
+            args = (LDPC_H_PACKED_U32, _host(pk), None)
+        else:
+            raise ValueError("give H, csr or packed")
+        self.h = lib.ldpc_create_ex(int(M), int(N), args[0], args[1], args[2], m, flags)
+        if not self.h:
+            raise LdpcError(lib.ldpc_last_error(), "ldpc_create_ex")
+        self.M, self.N, self.mode = int(M), int(N), mode
+
+    @classmethod
+    def from_code(cls, code, **kw):
+        rp, ci = code.csr()
+        return cls(M=code.M, N=code.N, csr=(rp, ci), **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().ldpc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return ldpc_info(self.h)
+
+    def set_variant(self, variant: str):
+        v = {"auto": LDPC_VARIANT_AUTO, "stream": LDPC_VARIANT_STREAM,
+             "resident": LDPC_VARIANT_RESIDENT}[variant]
+        _check(load().ldpc_set_variant(self.h, v), "ldpc_set_variant")
+
+    def variant(self) -> str:
+        return {LDPC_VARIANT_STREAM: "stream", LDPC_VARIANT_RESIDENT: "resident"}[ldpc_get_variant(self.h)]
+
+    def set_mode(self, mode: str):
+        _check(load().ldpc_set_mode(self.h, {"fp32": LDPC_MODE_FP32, "fixed": LDPC_MODE_FIXED}[mode]),
+               "ldpc_set_mode")
+        self.mode = mode
+
+    def reserve(self, frames: int):
+        _check(load().ldpc_reserve(self.h, frames), "ldpc_reserve")
+
+    def last_kernel_count(self) -> int:
+        return ldpc_last_kernel_count(self.h)
+
+    def decode(self, llr, max_iter: int, early_stop: bool = True, check_every: int = 1,
+               want_ok: bool = False, want_soft: bool = False, out=None):
+        """Decode a CUDA tensor of LLRs [F][N] (float32, or int8 in fixed mode).
+
+        Returns (bits uint8 [F][N], iters int32 [F], ok uint8 [F] or None, soft float32
+        [F][N] or None), allocated on the tensor's device unless ``out`` gives them.
+        """
+        import torch
+
+        if not llr.is_cuda or not llr.is_contiguous() or llr.dim() != 2 or llr.shape[1] != self.N:
+            raise ValueError("llr must be a contiguous CUDA tensor [F][N]")
+        dt = {torch.float32: LDPC_LLR_F32, torch.int8: LDPC_LLR_I8}[llr.dtype]
+        F = llr.shape[0]
+        dev = llr.device
+        if out is None:
+            bits = torch.empty((F, self.N), dtype=torch.uint8, device=dev)
+            iters = torch.empty(F, dtype=torch.int32, device=dev)
+            ok = torch.empty(F, dtype=torch.uint8, device=dev) if want_ok else None
+            soft = torch.empty((F, self.N), dtype=torch.float32, device=dev) if want_soft else None
+        else:
+            bits, iters, ok, soft = out
+        lib = load()
+        _check(lib.ldpc_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)),
+               "ldpc_set_stream")
+        st = lib.ldpc_decode_ex(self.h, ctypes.c_void_p(llr.data_ptr()), dt, F, max_iter,
+                                int(bool(early_stop)), check_every, ctypes.c_void_p(bits.data_ptr()),
+                                ctypes.c_void_p(iters.data_ptr()),
+                                ctypes.c_void_p(ok.data_ptr()) if ok is not None else None,
+                                ctypes.c_void_p(soft.data_ptr()) if soft is not None else None)
+        _check(st, "ldpc_decode_ex")
+        return bits, iters, ok, soft
+
+    def decode_host(self, llr, max_iter: int, early_stop: bool = True, check_every: int = 1,
+                    out=None, want_ok=False, want_soft=False):
+        """Decode host (CPU, preferably pinned) torch tensors; synchronous."""
+        import torch
+
+        if llr.is_cuda or not llr.is_contiguous() or llr.shape[1] != self.N:
+            raise ValueError("llr must be a contiguous CPU tensor [F][N]")
+        dt = {torch.float32: LDPC_LLR_F32, torch.int8: LDPC_LLR_I8}[llr.dtype]
+        F = llr.shape[0]
+        if out is None:
+            pin = llr.is_pinned()
+            bits = torch.empty((F, self.N), dtype=torch.uint8, pin_memory=pin)
+            iters = torch.empty(F, dtype=torch.int32, pin_memory=pin)
+            ok = torch.empty(F, dtype=torch.uint8, pin_memory=pin) if want_ok else None
+            soft = torch.empty((F, self.N), dtype=torch.float32, pin_memory=pin) if want_soft else None
+        else:
+            bits, iters, ok, soft = out
+        lib = load()
+        _check(lib.ldpc_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+               "ldpc_set_stream")
+        st = lib.ldpc_decode_host(self.h, ctypes.c_void_p(llr.data_ptr()), dt, F, max_iter,
+                                  int(bool(early_stop)), check_every, ctypes.c_void_p(bits.data_ptr()),
+                                  ctypes.c_void_p(iters.data_ptr()),
+                                  ctypes.c_void_p(ok.data_ptr()) if ok is not None else None,
+                                  ctypes.c_void_p(soft.data_ptr()) if soft is not None else None)
+        _check(st, "ldpc_decode_host")
+        return bits, iters, ok, soft

@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+Tolerances (from the specification of the two modes):
+* fixed point (int8 LLR, saturating int16 messages): bit-exact -- bits, iterations,
+  status and every posterior;
+* FP32: decoded bits, iteration counts and status identical; posteriors within 1e-5
+  relative (the kernels add in the oracle's order, so they are in fact expected to be
+  bit-identical, and the tests also report any inexact element).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_10424_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_2507_10424_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return torch
+
+
+def gpu_decode(torch, code, llr, L, mode="fp32", variant="auto", early_stop=True, check_every=1,
+               paper_slicer=False, i8=False):
+    from paper_2507_10424_gb300.ldpc import Decoder
+    dec = Decoder.from_code(code, mode=mode, paper_slicer=paper_slicer)
+    dec.set_variant(variant)
+    x = torch.from_numpy(np.ascontiguousarray(llr)).cuda()
+    bits, iters, ok, soft = dec.decode(x, L, early_stop=early_stop, check_every=check_every,
+                                       want_ok=True, want_soft=True)
+    torch.cuda.synchronize()
+    used = dec.variant()
+    n = dec.last_kernel_count()
+    dec.close()
+    return bits.cpu().numpy(), iters.cpu().numpy(), ok.cpu().numpy(), soft.cpu().numpy(), used, n
+
+
+def oracle_decode(code, llr, L, mode="fp32", early_stop=True, check_every=1, paper_slicer=False,
+                  i8=False):
+    g = oracle.Graph.from_code(code)
+    flags = oracle.PAPER_SLICER if paper_slicer else 0
+    if mode == "fp32":
+        return oracle.decode_f32(g, llr, L, early_stop, check_every, flags=flags)
+    q = llr if i8 else oracle.quantize(llr)
+    b, it, ok, s = oracle.decode_fixed(g, q, L, early_stop, check_every, flags=flags)
+    return b, it, ok, s.astype(np.float32) * 0.25
+
+
+def assert_parity(got, want, mode, label=""):
+    gb, gi, gok, gs = got[:4]
+    wb, wi, wok, ws = want
+    assert (gi == wi).all(), f"{label}: iterations differ in {(gi != wi).sum()} frames"
+    assert (gok == wok).all(), f"{label}: status differs in {(gok != wok).sum()} frames"
+    assert (gb == wb).all(), f"{label}: bits differ in {(gb != wb).sum()} positions"
+    if mode == "fixed":
+        assert (gs == ws).all(), f"{label}: fixed-point posteriors differ"
+    else:
+        np.testing.assert_allclose(gs, ws, rtol=RTOL, atol=0, err_msg=label)
+
+
+def tanner_code():
+    from conftest import read_golden
+    sets = [r[1] for r in read_golden("tanner_10x5.txt")]
+    return inputs.code_from_index_sets(sets, 10)
+
+
+MODES = ["fp32", "fixed"]
+VARIANTS = ["stream", "resident"]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_tanner_example(torch_cuda, mode, variant):
+    code = tanner_code()
+    rng = np.random.default_rng(1)
+    llr = (rng.standard_normal((300, 10)) * 1.5 + 0.5).astype(np.float32)
+    got = gpu_decode(torch_cuda, code, llr, 12, mode, variant)
+    assert got[4] == variant
+    assert_parity(got, oracle_decode(code, llr, 12, mode), mode, "tanner")
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_regular_576_all_zero_2p5dB(torch_cuda, mode, variant):
+    """(3,6)-regular N=576, 1024 frames of the all-zero codeword at Eb/N0 = 2.5 dB, 20 iterations."""
+    code = inputs.cfg_regular_576()
+    llr = inputs.all_zero_awgn_llr(1024, code.N, 2.5, code.design_rate, 11)
+    got = gpu_decode(torch_cuda, code, llr, 20, mode, variant)
+    want = oracle_decode(code, llr, 20, mode)
+    assert_parity(got, want, mode, "regular576")
+    assert want[1].max() > 1  # the case exercises several iterations
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("early_stop", [False, True])
+def test_qc_2304_random_codewords(torch_cuda, mode, variant, early_stop):
+    """QC 12x24, Z=96: random codewords over an SNR sweep, 10 iterations."""
+    code = inputs.cfg_qc_2304()
+    enc = inputs.Encoder(code)
+    F = 300  # ragged: not a multiple of any tile or vector width
+    cw = enc.random_codewords(F, 21)
+    ebn0 = np.repeat([1.0, 1.5, 2.0, 2.5, 3.0], F // 5)
+    llr = np.concatenate([inputs.bpsk_awgn_llr(cw[k * 60:(k + 1) * 60], e, code.design_rate, 30 + k)
+                          for k, e in enumerate([1.0, 1.5, 2.0, 2.5, 3.0])])
+    got = gpu_decode(torch_cuda, code, llr, 10, mode, variant, early_stop=early_stop)
+    want = oracle_decode(code, llr, 10, mode, early_stop=early_stop)
+    assert_parity(got, want, mode, "qc2304")
+    del ebn0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_irregular_64800_streaming(torch_cuda, mode):
+    """Irregular N=64800 (weights 2/3/8), all-zero codeword at 1.0 dB, 50 iterations, early stop."""
+    code = inputs.cfg_irregular_64800()
+    llr = inputs.all_zero_awgn_llr(24, code.N, 1.0, code.design_rate, 41)
+    got = gpu_decode(torch_cuda, code, llr, 50, mode, "auto")
+    assert got[4] == "stream"  # one frame does not fit in shared memory
+    assert_parity(got, oracle_decode(code, llr, 50, mode), mode, "irregular64800")
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_check_every_and_paper_slicer(torch_cuda, mode, variant):
+    code = inputs.qc_code(4, 8, 32, 0.7, 3)
+    rng = np.random.default_rng(8)
+    llr = (rng.standard_normal((257, code.N)) * 1.4 + 1.1).astype(np.float32)
+    for ce in (1, 3, 6):
+        got = gpu_decode(torch_cuda, code, llr, 25, mode, variant, check_every=ce)
+        assert_parity(got, oracle_decode(code, llr, 25, mode, check_every=ce), mode, f"ce={ce}")
+    tc = tanner_code()
+    l2 = (rng.standard_normal((129, 10)) * 1.5 + 0.4).astype(np.float32)
+    got = gpu_decode(torch_cuda, tc, l2, 9, mode, variant, paper_slicer=True)
+    assert_parity(got, oracle_decode(tc, l2, 9, mode, paper_slicer=True), mode, "paper slicer")
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_long_rows_and_empty_rows_columns(torch_cuda, mode, variant):
+    """Rows longer than 32 (in-place lambda path), weight-0 rows and weight-0 columns."""
+    rng = np.random.default_rng(5)
+    N = 180
+    sets = [sorted(rng.choice(N - 5, size=d, replace=False) + 1) for d in (40, 70, 33, 3, 2, 12)]
+    sets.insert(2, [])  # a row of weight 0
+    code = inputs.code_from_index_sets(sets, N)  # the last 5 columns have weight 0
+    llr = (rng.standard_normal((131, N)) * 2 + 0.3).astype(np.float32)
+    got = gpu_decode(torch_cuda, code, llr, 15, mode, variant)
+    assert_parity(got, oracle_decode(code, llr, 15, mode), mode, "long rows")
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_int8_input_and_saturation(torch_cuda, variant):
+    rng = np.random.default_rng(2)
+    n_bits = 40
+    sets = [sorted(rng.choice(n_bits, size=int(rng.integers(2, 5)), replace=False) + 1)
+            for _ in range(120)]
+    code = inputs.code_from_index_sets(sets, n_bits)
+    q = rng.choice([-127, 127, -3, 5], size=(67, n_bits)).astype(np.int8)
+    got = gpu_decode(torch_cuda, code, q, 12, "fixed", variant, early_stop=False)
+    want = oracle_decode(code, q, 12, "fixed", early_stop=False, i8=True)
+    assert_parity(got, want, "fixed", "int8 saturation")
+    assert np.abs(want[3]).max() == 32767 * 0.25  # saturation reached
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_edge_cases(torch_cuda, mode, variant):
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder
+    code = inputs.qc_code(3, 6, 32, 0.8, 9)
+    enc = inputs.Encoder(code)
+    cw = enc.random_codewords(33, 2)
+    llr = ((1 - 2 * cw.astype(np.float32)) * 2.75).astype(np.float32)
+    got = gpu_decode(torch, code, llr, 10, mode, variant)
+    assert (got[1] == 0).all() and (got[2] == 1).all() and (got[0] == cw).all()
+    for F in (1, 2, 7):
+        rng = np.random.default_rng(F)
+        l2 = (rng.standard_normal((F, code.N)) + 0.5).astype(np.float32)
+        for L in (0, 1, 4):
+            got = gpu_decode(torch, code, l2, L, mode, variant)
+            assert_parity(got, oracle_decode(code, l2, L, mode), mode, f"F={F} L={L}")
+    dec = Decoder.from_code(code, mode=mode)
+    dec.set_variant(variant)
+    empty = torch.zeros((0, code.N), dtype=torch.float32, device="cuda")
+    b, it, _, _ = dec.decode(empty, 5)
+    assert b.shape == (0, code.N) and it.shape == (0,)
+
+
+def test_errors_on_device_arguments(torch_cuda):
+    torch = torch_cuda
+    import ctypes
+    from paper_2507_10424_gb300 import ldpc
+    code = inputs.qc_code(3, 6, 32, 0.8, 9)
+    dec = ldpc.Decoder.from_code(code)
+    x = torch.zeros((4, code.N), device="cuda")
+    bits = torch.zeros((4, code.N), dtype=torch.uint8, device="cuda")
+    it = torch.zeros(4, dtype=torch.int32, device="cuda")
+    host = np.zeros((4, code.N), np.float32)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    assert ldpc.ldpc_decode(dec.h, ctypes.c_void_p(host.ctypes.data), 4, 5, P(bits), P(it)) == \
+        ldpc.LDPC_ERR_BAD_POINTER
+    assert ldpc.ldpc_decode(dec.h, P(x), -1, 5, P(bits), P(it)) == ldpc.LDPC_ERR_INVALID_ARG
+    assert ldpc.ldpc_decode(dec.h, P(x), 4, -2, P(bits), P(it)) == ldpc.LDPC_ERR_INVALID_ARG
+    assert ldpc.ldpc_decode_i8(dec.h, P(x), 4, 5, P(bits), P(it)) == ldpc.LDPC_ERR_INVALID_ARG
+    assert ldpc.ldpc_decode_ex(dec.h, P(x), 0, 4, 5, 1, 0, P(bits), P(it), None, None) == \
+        ldpc.LDPC_ERR_INVALID_ARG
+    assert ldpc.ldpc_decode(dec.h, P(x), 0, 5, P(bits), P(it)) == ldpc.LDPC_OK
+    big = inputs.cfg_irregular_64800()
+    d2 = ldpc.Decoder.from_code(big)
+    with pytest.raises(ldpc.LdpcError):
+        d2.set_variant("resident")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_host_buffer_pipeline_matches_device_path(torch_cuda, mode):
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder
+    code = inputs.cfg_qc_2304()
+    F = 2500  # several chunks of the host pipeline with a ragged last one
+    llr = inputs.all_zero_awgn_llr(F, code.N, 1.5, code.design_rate, 77)
+    dec = Decoder.from_code(code, mode=mode)
+    xh = torch.from_numpy(llr).pin_memory()
+    bh, ih, okh, sh = dec.decode_host(xh, 10, want_ok=True, want_soft=True)
+    bd, idv, okd, sd = dec.decode(xh.cuda(), 10, want_ok=True, want_soft=True)
+    torch.cuda.synchronize()
+    assert (bh.numpy() == bd.cpu().numpy()).all() and (ih.numpy() == idv.cpu().numpy()).all()
+    assert (okh.numpy() == okd.cpu().numpy()).all() and (sh.numpy() == sd.cpu().numpy()).all()
+    sel = np.arange(0, F, 97)
+    want = oracle_decode(code, llr[sel], 10, mode)
+    assert_parity((bh.numpy()[sel], ih.numpy()[sel], okh.numpy()[sel], sh.numpy()[sel]), want, mode,
+                  "host pipeline")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", MODES)
+def test_full_size_qc_2304_65536_frames_sampled(torch_cuda, mode):
+    """The benchmark's workload at full size (65536 random codewords, 10 iterations without
+    early stop, the launch configuration the benchmark times), checked on sampled frames."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder
+    code = inputs.cfg_qc_2304()
+    F = 65536
+    cw = inputs.Encoder(code).random_codewords(F, 123)
+    llr = inputs.bpsk_awgn_llr(cw, 2.0, code.design_rate, 124)
+    dec = Decoder.from_code(code, mode=mode)
+    x = torch.from_numpy(llr).cuda()
+    bits, iters, ok, soft = dec.decode(x, 10, early_stop=False, want_ok=True, want_soft=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    sel = np.sort(np.concatenate([rng.choice(F, 60, replace=False), [0, F - 1]]))
+    want = oracle_decode(code, llr[sel], 10, mode, early_stop=False)
+    got = (bits[sel].cpu().numpy(), iters[sel].cpu().numpy(), ok[sel].cpu().numpy(),
+           soft[sel].cpu().numpy())
+    assert_parity(got, want, mode, "full-size sample")
+    assert (iters == 10).all()
+    # decoded bits are codewords of H for every frame flagged ok (syndrome property at any size)
+    g = oracle.Graph.from_code(code)
+    okn = ok.cpu().numpy()
+    bn = bits.cpu().numpy()
+    for f in rng.choice(F, 200, replace=False):
+        assert okn[f] == (oracle.syndrome(g, bn[f])[0] == 0)
