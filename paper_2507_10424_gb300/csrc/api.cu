@@ -64,8 +64,8 @@ struct ldpc {
 };
 
 static void free_graph(DevGraph& g) {
-    void* ptrs[] = {g.row_ptr, g.col_idx, g.col_ptr, g.col_edge, g.packed, g.s_slice_base,
-                    g.s_row_deg, g.s_slot_col, g.s_col_ptr, g.s_col_slot16, g.s_col_slot32};
+    void* ptrs[] = {g.row_ptr, g.col_idx, g.col_ptr, g.col_edge, g.packed, g.r_base,
+                    g.r_deg, g.r_slot_pos, g.c_base, g.c_deg, g.c_slot, g.col_pos};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     g = DevGraph();
@@ -187,24 +187,25 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
                 packed[(size_t)i * W + hg.col_idx[e2] / 32] |= 1u << (hg.col_idx[e2] % 32);
         if ((rc = upload(&h->dg.packed, packed.data(), packed.size()))) return bail(rc);
     }
-    // sliced layout for the resident kernel (codes small enough to be resident)
-    if (hg.N <= 65535 && hg.max_dc <= 255 && hg.E < (1 << 26)) {
-        SlicedGraph sg;
-        build_sliced(hg, sg);
-        h->dg.n_slices = sg.n_slices;
-        h->dg.E_pad = sg.E_pad;
-        if ((rc = upload(&h->dg.s_slice_base, sg.slice_base.data(), sg.slice_base.size())) ||
-            (rc = upload(&h->dg.s_row_deg, sg.row_deg.data(), sg.row_deg.size())) ||
-            (rc = upload(&h->dg.s_slot_col, sg.slot_col.data(), sg.slot_col.size())) ||
-            (rc = upload(&h->dg.s_col_ptr, sg.col_ptr.data(), sg.col_ptr.size())))
+    // sliced layouts for the resident kernel (codes small enough to be resident)
+    SlicedGraph sg;
+    if (build_sliced(hg, sg)) {
+        DevGraph& d = h->dg;
+        d.n_rslices = sg.n_rslices;
+        d.n_cslices = sg.n_cslices;
+        d.E_pad = sg.E_pad;
+        d.Ec_pad = sg.Ec_pad;
+        if ((rc = upload(&d.r_base, sg.r_base.data(), sg.r_base.size())) ||
+            (rc = upload(&d.r_deg, sg.r_deg.data(), sg.r_deg.size())) ||
+            (rc = upload(&d.r_slot_pos, sg.r_slot_pos.data(), sg.r_slot_pos.size())) ||
+            (rc = upload(&d.c_base, sg.c_base.data(), sg.c_base.size())) ||
+            (rc = upload(&d.c_deg, sg.c_deg.data(), sg.c_deg.size())) ||
+            (rc = upload(&d.c_slot, sg.c_slot.data(), sg.c_slot.size())) ||
+            (rc = upload(&d.col_pos, sg.col_pos.data(), sg.col_pos.size())))
             return bail(rc);
-        if (!sg.col_slot16.empty()) {
-            if ((rc = upload(&h->dg.s_col_slot16, sg.col_slot16.data(), sg.col_slot16.size()))) return bail(rc);
-        } else {
-            if ((rc = upload(&h->dg.s_col_slot32, sg.col_slot32.data(), sg.col_slot32.size()))) return bail(rc);
-        }
-        h->plan[kModeFP32] = resident_plan(kModeFP32, h->dg, hg.M, hg.N, h->device);
-        h->plan[kModeFixed] = resident_plan(kModeFixed, h->dg, hg.M, hg.N, h->device);
+        d.sliced = 1;
+        h->plan[kModeFP32] = resident_plan(kModeFP32, d, hg.N, h->device);
+        h->plan[kModeFixed] = resident_plan(kModeFixed, d, hg.N, h->device);
     }
     e = cudaMalloc((void**)&h->counters, 4 * sizeof(int32_t));
     if (e != cudaSuccess) return bail(cuda_fail(e));

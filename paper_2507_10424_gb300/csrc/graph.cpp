@@ -105,47 +105,67 @@ int graph_from_csr(int32_t M, int32_t N, const int64_t* row_ptr, const int32_t* 
     return finish_graph(g);
 }
 
-void build_sliced(const HostGraph& g, SlicedGraph& sg) {
-    const int32_t M = g.M;
-    std::vector<int32_t> order(M);
+// Degree-sorted order of n items (descending degree, stable).
+static std::vector<int32_t> sorted_by_degree(const std::vector<int32_t>& ptr) {
+    const int32_t n = (int32_t)ptr.size() - 1;
+    std::vector<int32_t> order(n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        return (g.row_ptr[a + 1] - g.row_ptr[a]) > (g.row_ptr[b + 1] - g.row_ptr[b]);
+        return (ptr[a + 1] - ptr[a]) > (ptr[b + 1] - ptr[b]);
     });
-    sg.n_slices = (M + 31) / 32;
-    sg.slice_base.assign(sg.n_slices + 1, 0);
-    sg.row_deg.assign((size_t)sg.n_slices * 32, 0);
-    for (int32_t s = 0; s < sg.n_slices; s++) {
+    return order;
+}
+
+// Slices of 32 lanes over `order`; returns the total slot count.
+static int32_t make_slices(const std::vector<int32_t>& ptr, const std::vector<int32_t>& order,
+                           std::vector<int32_t>& base, std::vector<uint8_t>& deg) {
+    const int32_t n = (int32_t)order.size(), ns = (n + 31) / 32;
+    base.assign(ns + 1, 0);
+    deg.assign((size_t)ns * 32, 0);
+    for (int32_t s = 0; s < ns; s++) {
         int32_t w = 0;
-        for (int32_t l = 0; l < 32 && s * 32 + l < M; l++) {
-            int32_t i = order[s * 32 + l];
-            int32_t d = g.row_ptr[i + 1] - g.row_ptr[i];
-            sg.row_deg[s * 32 + l] = (uint8_t)d;
+        for (int32_t l = 0; l < 32 && s * 32 + l < n; l++) {
+            const int32_t x = order[s * 32 + l], d = ptr[x + 1] - ptr[x];
+            deg[s * 32 + l] = (uint8_t)d;
             w = std::max(w, d);
         }
-        sg.slice_base[s + 1] = sg.slice_base[s] + 32 * w;
+        base[s + 1] = base[s] + 32 * w;
     }
-    sg.E_pad = sg.slice_base[sg.n_slices];
-    sg.slot_col.assign(sg.E_pad, 0);
+    return base[ns];
+}
+
+bool build_sliced(const HostGraph& g, SlicedGraph& sg) {
+    if (g.N > 65535 || g.max_dc > 255 || g.max_dv > 255) return false;
+    const std::vector<int32_t> rorder = sorted_by_degree(g.row_ptr);
+    const std::vector<int32_t> corder = sorted_by_degree(g.col_ptr);
+    sg.n_rslices = (g.M + 31) / 32;
+    sg.n_cslices = (g.N + 31) / 32;
+    sg.E_pad = make_slices(g.row_ptr, rorder, sg.r_base, sg.r_deg);
+    sg.Ec_pad = make_slices(g.col_ptr, corder, sg.c_base, sg.c_deg);
+    if (sg.E_pad >= 65536 || sg.Ec_pad >= 65536) return false;
+    sg.col_pos.assign(g.N, 0);
+    for (int32_t p = 0; p < g.N; p++) sg.col_pos[corder[p]] = (uint16_t)p;
+    // row side: slot of every edge, and the sorted column position it reads
     std::vector<int32_t> slot_of_edge(g.E);
-    for (int32_t s = 0; s < sg.n_slices; s++)
-        for (int32_t l = 0; l < 32 && s * 32 + l < M; l++) {
-            int32_t i = order[s * 32 + l];
+    sg.r_slot_pos.assign(sg.E_pad, 0);
+    for (int32_t s = 0; s < sg.n_rslices; s++)
+        for (int32_t l = 0; l < 32 && s * 32 + l < g.M; l++) {
+            const int32_t i = rorder[s * 32 + l];
             for (int32_t k = 0; k < g.row_ptr[i + 1] - g.row_ptr[i]; k++) {
-                int32_t slot = sg.slice_base[s] + 32 * k + l;
-                int32_t e = g.row_ptr[i] + k;
-                sg.slot_col[slot] = (uint16_t)g.col_idx[e];
+                const int32_t slot = sg.r_base[s] + 32 * k + l, e = g.row_ptr[i] + k;
+                sg.r_slot_pos[slot] = sg.col_pos[g.col_idx[e]];
                 slot_of_edge[e] = slot;
             }
         }
-    sg.col_ptr = g.col_ptr;
-    if (sg.E_pad < 65536) {
-        sg.col_slot16.resize(g.E);
-        for (int64_t t = 0; t < g.E; t++) sg.col_slot16[t] = (uint16_t)slot_of_edge[g.col_edge[t]];
-    } else {
-        sg.col_slot32.resize(g.E);
-        for (int64_t t = 0; t < g.E; t++) sg.col_slot32[t] = slot_of_edge[g.col_edge[t]];
-    }
+    // column side: the row slots of a column's edges in ascending row order
+    sg.c_slot.assign(sg.Ec_pad, 0);
+    for (int32_t s = 0; s < sg.n_cslices; s++)
+        for (int32_t l = 0; l < 32 && s * 32 + l < g.N; l++) {
+            const int32_t j = corder[s * 32 + l];
+            for (int32_t k = 0; k < g.col_ptr[j + 1] - g.col_ptr[j]; k++)
+                sg.c_slot[sg.c_base[s] + 32 * k + l] = (uint16_t)slot_of_edge[g.col_edge[g.col_ptr[j] + k]];
+        }
+    return true;
 }
 
 }  // namespace ldpc_impl

@@ -33,21 +33,27 @@ int graph_from_csr(int32_t M, int32_t N, const int64_t* row_ptr, const int32_t* 
                    HostGraph& g);
 
 // ---------------------------------------------------------------------------------------
-// Sliced layout used by the resident kernel: rows sorted by degree (descending, stable),
-// grouped into slices of 32; slot (row lane l of slice s, k-th edge) sits at
-// slice_base[s] + 32 k + l, so that the 32 lanes of a warp touch 32 consecutive words.
+// Sliced layouts of the resident kernel. Rows and columns are each sorted by degree
+// (descending, stable) and grouped into slices of 32 lanes; the k-th edge of lane l of
+// slice s sits at base[s] + 32 k + l, so a warp's 32 lanes touch 32 consecutive entries.
+//   row side:    r_slot_pos[row slot]  = sorted position of the edge's column
+//   column side: c_slot[column slot]   = row slot of the edge (edges in ascending row order)
+//   col_pos[j]                         = sorted position of column j
+// Posteriors and channel values are stored by sorted column position.
 // ---------------------------------------------------------------------------------------
 struct SlicedGraph {
-    int32_t n_slices = 0;
-    int32_t E_pad = 0;                // total slots incl. padding
-    std::vector<int32_t> slice_base;  // n_slices + 1
-    std::vector<uint8_t> row_deg;     // 32 * n_slices (0 for missing rows)
-    std::vector<uint16_t> slot_col;   // E_pad: column of each slot (0 for padding)
-    std::vector<int32_t> col_ptr;     // N+1
-    std::vector<uint16_t> col_slot16; // E: slot ids of column j's edges, ascending row (E_pad < 65536)
-    std::vector<int32_t> col_slot32;  // same, when E_pad >= 65536
+    int32_t n_rslices = 0, n_cslices = 0;
+    int32_t E_pad = 0, Ec_pad = 0;      // row-side and column-side slots incl. padding
+    std::vector<int32_t> r_base;        // n_rslices + 1
+    std::vector<uint8_t> r_deg;         // 32 * n_rslices (0 for missing rows)
+    std::vector<uint16_t> r_slot_pos;   // E_pad
+    std::vector<int32_t> c_base;        // n_cslices + 1
+    std::vector<uint8_t> c_deg;         // 32 * n_cslices (0 for missing columns)
+    std::vector<uint16_t> c_slot;       // Ec_pad
+    std::vector<uint16_t> col_pos;      // N
 };
-void build_sliced(const HostGraph& g, SlicedGraph& sg);
+// Returns false when the code cannot use 16-bit slot ids or 8-bit degrees.
+bool build_sliced(const HostGraph& g, SlicedGraph& sg);
 
 // Device copies of the graph.
 struct DevGraph {
@@ -59,13 +65,15 @@ struct DevGraph {
     // bit-packed rows, uint32 [M][ceil(N/32)]
     uint32_t* packed = nullptr;
     // sliced layout (resident kernel)
-    int32_t* s_slice_base = nullptr;
-    uint8_t* s_row_deg = nullptr;
-    uint16_t* s_slot_col = nullptr;
-    int32_t* s_col_ptr = nullptr;
-    uint16_t* s_col_slot16 = nullptr;
-    int32_t* s_col_slot32 = nullptr;
-    int32_t n_slices = 0, E_pad = 0;
+    int32_t* r_base = nullptr;
+    uint8_t* r_deg = nullptr;
+    uint16_t* r_slot_pos = nullptr;
+    int32_t* c_base = nullptr;
+    uint8_t* c_deg = nullptr;
+    uint16_t* c_slot = nullptr;
+    uint16_t* col_pos = nullptr;
+    int32_t n_rslices = 0, n_cslices = 0, E_pad = 0, Ec_pad = 0;
+    int32_t sliced = 0;  // the sliced layout exists
 };
 
 // ---------------------------------------------------------------------------------------
@@ -105,12 +113,13 @@ size_t stream_bytes(int mode, int32_t N, int64_t E, int32_t Fp, int32_t L);
 
 struct ResidentPlan {
     int ok = 0;           // the code fits
-    int FT = 0;           // frames per tile
+    int FT = 0;           // frames per tile (interleaved in shared memory)
+    int idx_smem = 0;     // index arrays copied to shared memory
     int threads = 0;      // CTA size
     int ctas_per_sm = 0;
     size_t smem = 0;      // dynamic shared memory per CTA
 };
-ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t M, int32_t N, int device);
+ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device);
 int resident_decode(int mode, const DevGraph& dg, const ResidentPlan& p, const DecodeArgs& a,
                     int32_t* tile_counter, int num_sms, cudaStream_t st);
 

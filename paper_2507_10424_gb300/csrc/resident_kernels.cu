@@ -1,19 +1,27 @@
-// Resident variant: one persistent kernel. Each CTA takes tiles of FT frames from an
-// atomic work counter and runs every flooding iteration of Algorithm 1 for that tile with
-// the edge messages eta and posteriors s of all FT frames held in shared memory; only the
-// channel LLRs are read from, and the decisions written to, global memory.
+// Resident variant: one persistent kernel per decode. Each CTA takes tiles of FT frames
+// from an atomic work counter and runs every flooding iteration of Algorithm 1 for its
+// tile with the edge messages eta, the posteriors s and the channel values r of all FT
+// frames held in shared memory; global memory sees only the channel LLRs once and the
+// decisions once per frame.
 //
-// Shared-memory layout per frame f: eta_f[E_pad] in the sliced order (slot of the k-th
-// edge of row-lane l of slice sl = slice_base[sl] + 32 k + l, so a warp's 32 lanes touch
-// 32 consecutive words), then s_f[N_pad].
+// Shared-memory layout: the FT frames of a tile are interleaved, so that one vector load
+// (FT x 4 bytes in FP32, FT x 2 bytes in fixed point) serves every frame of an edge:
+//   eta[row slot][FT]      row slots in the row-sliced order (slot of the k-th edge of
+//                          lane l of slice q = r_base[q] + 32 k + l),
+//   s[position][FT], r[position][FT]   by degree-sorted column position,
+//   the index arrays of both sliced layouts (when they fit).
 //
-// One iteration = phase A (rows) + phase B (columns), separated by CTA barriers:
-//   phase A, thread per row-lane, all FT frames: lambda = s_col - eta (eta^prev = 0 in
-//     the first iteration), Observation 1 (min0, first location, min1) and Observation 2
-//     (XOR of sign bits), eta = +-(min1 at the location, else min0); the same sweep XORs
-//     the decisions of the gathered s, i.e. the syndrome (eq. 1-2) of the current s;
-//   phase B, thread per column, all FT frames: s_j = r_j + sum of eta in ascending row
-//     order (eq. lambda_j). Frames whose syndrome was zero stop before phase B.
+// One iteration = phase A (rows) then phase B (columns), separated by CTA barriers:
+//   phase A, one thread per row lane: lambda = s - eta (eta^prev = 0 in the first
+//     iteration; eq. eta_update), Observation 1 (min0, first location, min1) and
+//     Observation 2 (XOR of sign bits), then eta = +-(min1 at the location, else min0).
+//     The same sweep XORs the decisions of the gathered s: the syndrome of the current s
+//     (eq. 1-2);
+//   phase B, one thread per column lane: s = r + the column's eta in ascending row order
+//     (eq. lambda_j).
+// A frame whose syndrome is zero is written out at once (iterations = k); it keeps being
+// computed with its tile (no per-frame branches in the inner loops) but is never written
+// again. The tile ends when all its frames are out or after max_iter iterations.
 #include <algorithm>
 
 #include "../../include/ldpc.h"
@@ -22,7 +30,7 @@
 namespace ldpc_impl {
 namespace {
 
-constexpr int kMaxThreads = 1024;
+constexpr int kMaxThreads = 768;  // 85 registers per thread at one CTA per SM
 
 template <int MODE>
 struct RT;
@@ -37,6 +45,11 @@ struct RT<kModeFixed> {
     using A = int32_t;
 };
 
+template <typename T, int V>
+struct alignas(sizeof(T) * V) VecR {
+    T x[V];
+};
+
 __device__ __forceinline__ int32_t rsat16(int32_t v) { return max(-kSat, min(kSat, v)); }
 __device__ __forceinline__ float rlam(float s, float e) { return s - e; }
 __device__ __forceinline__ int32_t rlam(int32_t s, int32_t e) { return rsat16(s - e); }
@@ -44,6 +57,8 @@ __device__ __forceinline__ float rabs(float x) { return fabsf(x); }
 __device__ __forceinline__ int32_t rabs(int32_t x) { return abs(x); }
 __device__ __forceinline__ float rbig(float) { return __int_as_float(0x7f800000); }
 __device__ __forceinline__ int32_t rbig(int32_t) { return 0x7fffffff; }
+__device__ __forceinline__ float rsat_out(float v) { return v; }
+__device__ __forceinline__ int32_t rsat_out(int32_t v) { return rsat16(v); }
 template <typename A>
 __device__ __forceinline__ uint32_t rslice(A s, int paper) {
     return paper ? (s > A(0)) : (s < A(0));
@@ -55,14 +70,50 @@ __device__ __forceinline__ int8_t rquant(float x) {
     return (int8_t)__float2int_rn(t);
 }
 
+// Byte offsets of the shared-memory regions (host and device agree on them).
+struct ResLayout {
+    uint32_t eta, s, r, rpos, cslot, cpos, rdeg, cdeg, rbase, cbase, total;
+};
+__host__ __device__ inline uint32_t al16(uint32_t x) { return (x + 15u) & ~15u; }
+__host__ __device__ inline ResLayout res_layout(int tb, int FT, int E_pad, int Ec_pad, int n_rsl,
+                                                int n_csl, int N, bool idx) {
+    ResLayout L{};
+    uint32_t o = 0;
+    L.eta = o;
+    o = al16(o + (uint32_t)E_pad * FT * tb);
+    L.s = o;
+    o = al16(o + (uint32_t)n_csl * 32 * FT * tb);
+    L.r = o;
+    o = al16(o + (uint32_t)n_csl * 32 * FT * tb);
+    if (idx) {
+        L.rpos = o;
+        o = al16(o + (uint32_t)E_pad * 2);
+        L.cslot = o;
+        o = al16(o + (uint32_t)Ec_pad * 2);
+        L.cpos = o;
+        o = al16(o + (uint32_t)N * 2);
+        L.rdeg = o;
+        o = al16(o + (uint32_t)n_rsl * 32);
+        L.cdeg = o;
+        o = al16(o + (uint32_t)n_csl * 32);
+        L.rbase = o;
+        o = al16(o + (uint32_t)(n_rsl + 1) * 4);
+        L.cbase = o;
+        o = al16(o + (uint32_t)(n_csl + 1) * 4);
+    }
+    L.total = o;
+    return L;
+}
+
 struct ResArgs {
-    const int32_t* slice_base;
-    const uint8_t* row_deg;
-    const uint16_t* slot_col;
-    const int32_t* col_ptr;
-    const uint16_t* col_slot16;
-    const int32_t* col_slot32;
-    int32_t n_tasks, E_pad, N, N_pad;
+    const int32_t* r_base;
+    const uint8_t* r_deg;
+    const uint16_t* r_slot_pos;
+    const int32_t* c_base;
+    const uint8_t* c_deg;
+    const uint16_t* c_slot;
+    const uint16_t* col_pos;
+    int32_t n_rsl, n_csl, E_pad, Ec_pad, N;
     const void* llr;
     int32_t llr_i8;
     int32_t frames, n_tiles, L, early_stop, check_every, paper;
@@ -73,6 +124,16 @@ struct ResArgs {
     int32_t* tile_counter;
 };
 
+struct Idx {
+    const int32_t* r_base;
+    const uint8_t* r_deg;
+    const uint16_t* r_slot_pos;
+    const int32_t* c_base;
+    const uint8_t* c_deg;
+    const uint16_t* c_slot;
+    const uint16_t* col_pos;
+};
+
 // Channel value of (frame, bit) in the arithmetic of the mode.
 template <int MODE>
 __device__ __forceinline__ typename RT<MODE>::A chan(const ResArgs& a, size_t idx) {
@@ -81,230 +142,344 @@ __device__ __forceinline__ typename RT<MODE>::A chan(const ResArgs& a, size_t id
     return (int32_t)rquant(__ldg((const float*)a.llr + idx));
 }
 
-template <int MODE, int FT>
-__global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
+// Raw bits of a value whose sign bit is the decision "negative" (the values never hold
+// -0.0: channel values are canonicalised at load, and round-to-nearest sums and
+// differences of non-(-0) values are never -0.0).
+__device__ __forceinline__ uint32_t bits_of(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ uint32_t bits_of(int32_t x) { return (uint32_t)x; }
+// Sign-bit word of the hard decision: standard [s < 0], or the paper's [s > 0] = [0 - s < 0].
+template <bool PAPER, typename A>
+__device__ __forceinline__ uint32_t dec_bits(A s) { return PAPER ? bits_of(A(0) - s) : bits_of(s); }
+// m with the sign bit of `sgn` (m >= 0).
+__device__ __forceinline__ float with_sign(float m, uint32_t sgn) {
+    return __uint_as_float(__float_as_uint(m) | (sgn & 0x80000000u));
+}
+__device__ __forceinline__ int32_t with_sign(int32_t m, uint32_t sgn) { return (int32_t)sgn < 0 ? -m : m; }
+// lambda = s - eta, saturated in fixed point.
+__device__ __forceinline__ float lam_sat(float s, float e) { return s - e; }
+__device__ __forceinline__ int32_t lam_sat(int32_t s, int32_t e) { return rsat16(s - e); }
+
+// Task of round k for this thread: rounds alternate direction so that the work of a
+// thread's tasks (sorted by decreasing degree) evens out. Strictly increasing in k.
+__device__ __forceinline__ int snake(int k, int nth) {
+    return k * nth + ((k & 1) ? (nth - 1 - (int)threadIdx.x) : (int)threadIdx.x);
+}
+
+// Phase A for every row lane of the CTA's tile. Sweep 1 forms lambda for every edge,
+// keeps min0 and min1 (Observation 1) and the XOR of the sign bits (Observation 2), and
+// stashes lambda in the edge's slot; sweep 2 turns each stashed lambda into the new
+// message: magnitude min1 where |lambda| = min0 (on a tie min1 = min0, so the first
+// location needs no tracking), else min0; sign = total sign x own sign.
+template <int MODE, int FT, bool FIRST, bool SYN, bool UPD, bool PAPER>
+__device__ __forceinline__ void phase_a(const Idx& ix, VecR<typename RT<MODE>::T, FT>* eta,
+                                        const VecR<typename RT<MODE>::T, FT>* s, int n_rtasks,
+                                        uint32_t* unsat_w) {
     using T = typename RT<MODE>::T;
     using A = typename RT<MODE>::A;
+    using VT = VecR<T, FT>;
+    constexpr int UNR = FT >= 4 ? 2 : 4;  // unrolling of the edge sweeps, bounded by registers
+    const int nth = blockDim.x;
+    for (int k = 0;; k++) {
+        const int task = snake(k, nth);  // strictly increasing in k
+        if (task >= n_rtasks) break;
+        const int d = ix.r_deg[task];
+        if (d == 0) continue;
+        const int base = ix.r_base[task >> 5] + (task & 31);
+        A min0[FT], min1[FT];
+        uint32_t sx[FT], zx[FT];
+#pragma unroll
+        for (int f = 0; f < FT; f++) {
+            min0[f] = rbig(A());
+            min1[f] = rbig(A());
+            sx[f] = 0;
+            zx[f] = 0;
+        }
+#pragma unroll UNR
+        for (int t = 0; t < d; t++) {
+            const int slot = base + 32 * t;
+            const VT sv = s[ix.r_slot_pos[slot]];
+            if (SYN) {
+#pragma unroll
+                for (int f = 0; f < FT; f++) zx[f] ^= dec_bits<PAPER>((A)sv.x[f]);
+            }
+            if (UPD) {
+                VT ev;
+                if (!FIRST) ev = eta[slot];
+                VT lv;
+#pragma unroll
+                for (int f = 0; f < FT; f++) {
+                    const A lam = FIRST ? (A)sv.x[f] : lam_sat((A)sv.x[f], (A)ev.x[f]);
+                    const A m = rabs(lam);
+                    min1[f] = min(min1[f], max(min0[f], m));
+                    min0[f] = min(min0[f], m);
+                    sx[f] ^= bits_of(lam);
+                    lv.x[f] = (T)lam;
+                }
+                eta[slot] = lv;  // stash lambda for sweep 2
+            }
+        }
+        if (SYN) {
+            uint32_t z = 0;
+#pragma unroll
+            for (int f = 0; f < FT; f++) z |= (zx[f] >> 31) << f;
+            if (z) atomicOr(unsat_w, z);
+        }
+        if (UPD) {
+#pragma unroll UNR
+            for (int t = 0; t < d; t++) {
+                const int slot = base + 32 * t;
+                const VT lv = eta[slot];
+                VT out;
+#pragma unroll
+                for (int f = 0; f < FT; f++) {
+                    const A lam = (A)lv.x[f];
+                    const A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
+                    out.x[f] = (T)with_sign(m, bits_of(lam) ^ sx[f]);
+                }
+                eta[slot] = out;
+            }
+        }
+    }
+}
+
+// Phase B for every column position of the tile.
+template <int MODE, int FT>
+__device__ __forceinline__ void phase_b(const Idx& ix, const VecR<typename RT<MODE>::T, FT>* eta,
+                                        VecR<typename RT<MODE>::T, FT>* s,
+                                        const VecR<typename RT<MODE>::T, FT>* r, int N) {
+    using T = typename RT<MODE>::T;
+    using A = typename RT<MODE>::A;
+    using VT = VecR<T, FT>;
+    const int nth = blockDim.x;
+    for (int k = 0;; k++) {
+        const int p = snake(k, nth);
+        if (p >= N) break;
+        const int d = ix.c_deg[p];
+        const int base = ix.c_base[p >> 5] + (p & 31);
+        const VT rv = r[p];
+        A acc[FT];
+#pragma unroll
+        for (int f = 0; f < FT; f++) acc[f] = (A)rv.x[f];
+#pragma unroll 4
+        for (int t = 0; t < d; t++) {
+            const VT ev = eta[ix.c_slot[base + 32 * t]];
+#pragma unroll
+            for (int f = 0; f < FT; f++) acc[f] = acc[f] + (A)ev.x[f];
+        }
+        VT out;
+#pragma unroll
+        for (int f = 0; f < FT; f++) out.x[f] = (T)rsat_out(acc[f]);
+        s[p] = out;
+    }
+}
+
+// Write the decisions (and posteriors) of the frames in `mask`.
+template <int MODE, int FT>
+__device__ __forceinline__ void emit(const ResArgs& a, const Idx& ix,
+                                     const VecR<typename RT<MODE>::T, FT>* s, int fbase,
+                                     uint32_t mask, int iters, uint32_t okm) {
+    using A = typename RT<MODE>::A;
+    const int N = a.N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const auto v = s[ix.col_pos[j]];
+#pragma unroll
+        for (int f = 0; f < FT; f++) {
+            if (!((mask >> f) & 1u)) continue;
+            const size_t o = (size_t)(fbase + f) * N + j;
+            const A x = (A)v.x[f];
+            a.out_bits[o] = (uint8_t)rslice(x, a.paper);
+            if (a.out_soft) a.out_soft[o] = (MODE == kModeFP32) ? (float)x : (float)x * 0.25f;
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < FT; f++)
+        if (threadIdx.x == f && ((mask >> f) & 1u)) {
+            a.out_iters[fbase + f] = iters;
+            if (a.out_ok) a.out_ok[fbase + f] = (okm >> f) & 1u;
+        }
+}
+
+template <typename T>
+__device__ __forceinline__ void copy_to_smem(T* dst, const T* src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+template <int MODE, int FT, bool IDX_SMEM, bool PAPER>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
+    using T = typename RT<MODE>::T;
+    using VT = VecR<T, FT>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* eta = reinterpret_cast<T*>(smem_raw);
-    T* sv = eta + (size_t)FT * a.E_pad;
-    __shared__ int unsat[2][FT];
+    __shared__ uint32_t unsat_w[2];
     __shared__ int tile_sh;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int E_pad = a.E_pad, N = a.N, N_pad = a.N_pad;
+    const ResLayout lay = res_layout((int)sizeof(T), FT, a.E_pad, a.Ec_pad, a.n_rsl, a.n_csl, a.N,
+                                     IDX_SMEM);
+    VT* eta = reinterpret_cast<VT*>(smem_raw + lay.eta);
+    VT* s = reinterpret_cast<VT*>(smem_raw + lay.s);
+    VT* r = reinterpret_cast<VT*>(smem_raw + lay.r);
+    Idx ix;
+    if (IDX_SMEM) {
+        uint16_t* rpos = reinterpret_cast<uint16_t*>(smem_raw + lay.rpos);
+        uint16_t* cslot = reinterpret_cast<uint16_t*>(smem_raw + lay.cslot);
+        uint16_t* cpos = reinterpret_cast<uint16_t*>(smem_raw + lay.cpos);
+        uint8_t* rdeg = smem_raw + lay.rdeg;
+        uint8_t* cdeg = smem_raw + lay.cdeg;
+        int32_t* rbase = reinterpret_cast<int32_t*>(smem_raw + lay.rbase);
+        int32_t* cbase = reinterpret_cast<int32_t*>(smem_raw + lay.cbase);
+        copy_to_smem(rpos, a.r_slot_pos, a.E_pad);
+        copy_to_smem(cslot, a.c_slot, a.Ec_pad);
+        copy_to_smem(cpos, a.col_pos, a.N);
+        copy_to_smem(rdeg, a.r_deg, a.n_rsl * 32);
+        copy_to_smem(cdeg, a.c_deg, a.n_csl * 32);
+        copy_to_smem(rbase, a.r_base, a.n_rsl + 1);
+        copy_to_smem(cbase, a.c_base, a.n_csl + 1);
+        ix = Idx{rbase, rdeg, rpos, cbase, cdeg, cslot, cpos};
+    } else {
+        ix = Idx{a.r_base, a.r_deg, a.r_slot_pos, a.c_base, a.c_deg, a.c_slot, a.col_pos};
+    }
+    const int N = a.N, n_rtasks = a.n_rsl * 32;
 
     for (;;) {
-        if (tid == 0) tile_sh = atomicAdd(a.tile_counter, 1);
-        if (tid < 2 * FT) unsat[tid / FT][tid % FT] = 0;
+        if (threadIdx.x == 0) {
+            tile_sh = atomicAdd(a.tile_counter, 1);
+            unsat_w[0] = 0;
+            unsat_w[1] = 0;
+        }
         __syncthreads();
         const int tile = tile_sh;
         if (tile >= a.n_tiles) break;
         const int fbase = tile * FT;
         const int nf = min(FT, a.frames - fbase);
-        for (int f = 0; f < nf; f++)
-            for (int j = tid; j < N; j += nth) sv[f * N_pad + j] = (T)chan<MODE>(a, (size_t)(fbase + f) * N + j);
-        uint32_t active = (1u << nf) - 1u, okm = 0;
-        int its[FT];
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            VT v;
 #pragma unroll
-        for (int f = 0; f < FT; f++) its[f] = a.L;
+            for (int f = 0; f < FT; f++)  // "+ 0" turns -0.0 into +0.0 and changes no other value
+                v.x[f] = f < nf ? (T)(chan<MODE>(a, (size_t)(fbase + f) * N + j) + 0) : T(0);
+            const int p = ix.col_pos[j];
+            s[p] = v;
+            r[p] = v;
+        }
+        uint32_t active = (1u << nf) - 1u;
         __syncthreads();
 
         for (int k = 0;; k++) {
             const int par = k & 1;
             const bool last = (k == a.L);
             const bool syn = last || (a.early_stop && (k % a.check_every == 0));
-            const bool first = (k == 0);
-            // ---------------- phase A: check nodes (and syndrome of the current s)
-            for (int task = tid; task < a.n_tasks; task += nth) {
-                const int d = a.row_deg[task];
-                if (d == 0) continue;
-                const int base = a.slice_base[task >> 5] + (task & 31);
-                A min0[FT], min1[FT];
-                int loc[FT];
-                uint32_t msk[FT];
-                uint32_t neg = 0, z = 0;
-#pragma unroll
-                for (int f = 0; f < FT; f++) {
-                    min0[f] = rbig(A());
-                    min1[f] = rbig(A());
-                    loc[f] = 0;
-                    msk[f] = 0;
-                }
-                const bool longrow = d > 32;
-                for (int t = 0; t < d; t++) {
-                    const int slot = base + 32 * t;
-                    const int col = __ldg(a.slot_col + slot);
-#pragma unroll
-                    for (int f = 0; f < FT; f++) {
-                        if (!((active >> f) & 1u)) continue;
-                        const A s_ = (A)sv[f * N_pad + col];
-                        if (syn) z ^= rslice(s_, a.paper) << f;
-                        if (!last) {
-                            const A lam = first ? s_ : rlam(s_, (A)eta[f * E_pad + slot]);
-                            const A m = rabs(lam);
-                            const uint32_t sg = lam < A(0);
-                            if (m < min0[f]) {
-                                min1[f] = min0[f];
-                                min0[f] = m;
-                                loc[f] = t;
-                            } else if (m < min1[f]) {
-                                min1[f] = m;
-                            }
-                            neg ^= sg << f;
-                            msk[f] |= sg << (t & 31);
-                            if (longrow) eta[f * E_pad + slot] = (T)lam;
-                        }
-                    }
-                }
-                if (syn && (z & active)) {
-#pragma unroll
-                    for (int f = 0; f < FT; f++)
-                        if (((z & active) >> f) & 1u) unsat[par][f] = 1;
-                }
-                if (!last) {
-                    for (int t = 0; t < d; t++) {
-                        const int slot = base + 32 * t;
-#pragma unroll
-                        for (int f = 0; f < FT; f++) {
-                            if (!((active >> f) & 1u)) continue;
-                            const uint32_t sg = longrow ? (uint32_t)((A)eta[f * E_pad + slot] < A(0))
-                                                        : ((msk[f] >> t) & 1u);
-                            const A m = (t == loc[f]) ? min1[f] : min0[f];
-                            eta[f * E_pad + slot] = (T)((((neg >> f) ^ sg) & 1u) ? -m : m);
-                        }
-                    }
-                }
+            uint32_t* uw = &unsat_w[par];
+            if (k == 0) {
+                if (last) phase_a<MODE, FT, true, true, false, PAPER>(ix, eta, s, n_rtasks, uw);
+                else if (syn) phase_a<MODE, FT, true, true, true, PAPER>(ix, eta, s, n_rtasks, uw);
+                else phase_a<MODE, FT, true, false, true, PAPER>(ix, eta, s, n_rtasks, uw);
+            } else {
+                if (last) phase_a<MODE, FT, false, true, false, PAPER>(ix, eta, s, n_rtasks, uw);
+                else if (syn) phase_a<MODE, FT, false, true, true, PAPER>(ix, eta, s, n_rtasks, uw);
+                else phase_a<MODE, FT, false, false, true, PAPER>(ix, eta, s, n_rtasks, uw);
             }
             __syncthreads();
             if (syn) {
-                uint32_t zm = 0;
-#pragma unroll
-                for (int f = 0; f < FT; f++) zm |= (uint32_t)(unsat[par][f] != 0) << f;
-                const uint32_t conv = active & ~zm;
-                okm |= conv;
-                if (last) break;
-#pragma unroll
-                for (int f = 0; f < FT; f++)
-                    if ((conv >> f) & 1u) its[f] = k;
-                active &= ~conv;
-                if (!active) break;
-            }
-            // ---------------- phase B: bit nodes
-            for (int j = tid; j < N; j += nth) {
-                const int t0 = __ldg(a.col_ptr + j), t1 = __ldg(a.col_ptr + j + 1);
-                A acc[FT];
-#pragma unroll
-                for (int f = 0; f < FT; f++)
-                    if ((active >> f) & 1u) acc[f] = chan<MODE>(a, (size_t)(fbase + f) * N + j);
-                for (int t = t0; t < t1; t++) {
-                    const int slot = a.col_slot16 ? (int)__ldg(a.col_slot16 + t) : __ldg(a.col_slot32 + t);
-#pragma unroll
-                    for (int f = 0; f < FT; f++)
-                        if ((active >> f) & 1u) acc[f] = acc[f] + (A)eta[f * E_pad + slot];
+                const uint32_t conv = active & ~unsat_w[par];
+                if (last) {
+                    emit<MODE, FT>(a, ix, s, fbase, active, a.L, conv);
+                    break;
                 }
-#pragma unroll
-                for (int f = 0; f < FT; f++)
-                    if ((active >> f) & 1u)
-                        sv[f * N_pad + j] = (MODE == kModeFP32) ? (T)acc[f] : (T)rsat16((int32_t)acc[f]);
+                if (conv) {
+                    emit<MODE, FT>(a, ix, s, fbase, conv, k, conv);
+                    active &= ~conv;
+                    if (!active) break;
+                    __syncthreads();  // the emitted posteriors are read before phase B rewrites them
+                }
             }
-            if (tid < FT) unsat[par ^ 1][tid] = 0;
+            phase_b<MODE, FT>(ix, eta, s, r, N);
+            if (threadIdx.x == 0) unsat_w[par ^ 1] = 0;
             __syncthreads();
         }
-        // ---------------- output of the tile
-        for (int f = 0; f < nf; f++) {
-            const size_t row = (size_t)(fbase + f) * N;
-            for (int j = tid; j < N; j += nth) {
-                const A s_ = (A)sv[f * N_pad + j];
-                a.out_bits[row + j] = (uint8_t)rslice(s_, a.paper);
-                if (a.out_soft) a.out_soft[row + j] = (MODE == kModeFP32) ? (float)s_ : (float)s_ * 0.25f;
-            }
-        }
-#pragma unroll
-        for (int f = 0; f < FT; f++)
-            if (tid == f && f < nf) {
-                a.out_iters[fbase + f] = its[f];
-                if (a.out_ok) a.out_ok[fbase + f] = (okm >> f) & 1u;
-            }
         __syncthreads();
     }
 }
 
-template <int MODE, int FT>
-int launch(const ResArgs& ra, const ResidentPlan& p, int grid, cudaStream_t st) {
-    // the opt-in shared-memory size is a per-function attribute: set it for this plan
-    if (cudaFuncSetAttribute(k_resident<MODE, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)p.smem) != cudaSuccess)
+template <int MODE, int FT, bool IDX, bool PAPER>
+int launch(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
+    auto kern = k_resident<MODE, FT, IDX, PAPER>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
-    k_resident<MODE, FT><<<grid, p.threads, p.smem, st>>>(ra);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, p.threads, p.smem) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    if (per_sm < 1) return LDPC_ERR_UNSUPPORTED;
+    const int grid = std::max(1, std::min(ra.n_tiles, num_sms * per_sm));
+    kern<<<grid, p.threads, p.smem, st>>>(ra);
     return cudaGetLastError() == cudaSuccess ? 1 : LDPC_ERR_CUDA;
 }
 
-template <int MODE>
-int dispatch(const ResArgs& ra, const ResidentPlan& p, int grid, cudaStream_t st) {
-    switch (p.FT) {
-        case 1: return launch<MODE, 1>(ra, p, grid, st);
-        case 2: return launch<MODE, 2>(ra, p, grid, st);
-        case 3: return launch<MODE, 3>(ra, p, grid, st);
-        case 4: return launch<MODE, 4>(ra, p, grid, st);
-        case 6: return launch<MODE, 6>(ra, p, grid, st);
-        case 8: return launch<MODE, 8>(ra, p, grid, st);
+template <int MODE, bool PAPER>
+int dispatch(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
+    if (p.idx_smem) {
+        switch (p.FT) {
+            case 1: return launch<MODE, 1, true, PAPER>(ra, p, num_sms, st);
+            case 2: return launch<MODE, 2, true, PAPER>(ra, p, num_sms, st);
+            case 4: return launch<MODE, 4, true, PAPER>(ra, p, num_sms, st);
+        }
+    } else {
+        switch (p.FT) {
+            case 1: return launch<MODE, 1, false, PAPER>(ra, p, num_sms, st);
+            case 2: return launch<MODE, 2, false, PAPER>(ra, p, num_sms, st);
+        }
     }
     return LDPC_ERR_INVALID_ARG;
 }
 
 }  // namespace
 
-static size_t frame_bytes(int mode, int32_t E_pad, int32_t N_pad) {
-    const size_t tb = mode == kModeFP32 ? 4 : 2;
-    return tb * ((size_t)E_pad + (size_t)N_pad);
-}
-
-ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t M, int32_t N, int device) {
+ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device) {
     ResidentPlan p;
-    (void)M;
-    if (N > 65535 || dg.n_slices == 0) return p;
-    int optin = 0, per_sm = 0;
+    if (!dg.sliced) return p;
+    int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
-    const int32_t N_pad = (N + 7) & ~7;
-    const size_t fb = frame_bytes(mode, dg.E_pad, N_pad);
-    const size_t reserve = 1024 + 256;  // per-CTA system reserve + static shared memory
-    if (fb + reserve > (size_t)optin) return p;
-    static const int kFT[] = {8, 6, 4, 3, 2, 1};
-    for (int ft : kFT)
-        if (ft * fb + reserve <= (size_t)optin) {
-            p.FT = ft;
-            break;
+    const int tb = mode == kModeFP32 ? 4 : 2;
+    const size_t budget = (size_t)std::max(0, optin - 256);  // static shared memory
+    // up to four interleaved frames (registers); index arrays in shared memory preferred
+    const int fts[] = {4, 2, 1};
+    for (int idx = 1; idx >= 0 && !p.ok; idx--)
+        for (int ft : fts) {
+            if (ft * tb > 16 || (!idx && ft > 2)) continue;
+            const ResLayout L = res_layout(tb, ft, dg.E_pad, dg.Ec_pad, dg.n_rslices, dg.n_cslices, N, idx);
+            if (L.total <= budget) {
+                p.ok = 1;
+                p.FT = ft;
+                p.idx_smem = idx;
+                p.smem = L.total;
+                break;
+            }
         }
-    // threads: minimise padded work of both phases; prefer more threads on ties
-    const int tasks = dg.n_slices * 32;
+    if (!p.ok) return p;
+    // threads: minimise the padded work of both phases (rows weigh twice: two sweeps)
+    const int rt = dg.n_rslices * 32;
     long best = -1;
     for (int t = 256; t <= kMaxThreads; t += 32) {
-        const long cost = (long)((tasks + t - 1) / t) * t * 2 + (long)((N + t - 1) / t) * t;
+        const long cost = (long)((rt + t - 1) / t) * t * 2 + (long)((N + t - 1) / t) * t;
         if (best < 0 || cost <= best) {  // ascending t: ties go to the larger CTA
             best = cost;
             p.threads = t;
         }
     }
-    p.smem = p.FT * fb;
-    p.ctas_per_sm = std::max(1, std::min((int)(per_sm / (p.smem + reserve)), 2048 / p.threads));
-    p.ok = 1;
     return p;
 }
 
 int resident_decode(int mode, const DevGraph& dg, const ResidentPlan& p, const DecodeArgs& a,
                     int32_t* tile_counter, int num_sms, cudaStream_t st) {
     ResArgs ra;
-    ra.slice_base = dg.s_slice_base;
-    ra.row_deg = dg.s_row_deg;
-    ra.slot_col = dg.s_slot_col;
-    ra.col_ptr = dg.s_col_ptr;
-    ra.col_slot16 = dg.s_col_slot16;
-    ra.col_slot32 = dg.s_col_slot32;
-    ra.n_tasks = dg.n_slices * 32;
+    ra.r_base = dg.r_base;
+    ra.r_deg = dg.r_deg;
+    ra.r_slot_pos = dg.r_slot_pos;
+    ra.c_base = dg.c_base;
+    ra.c_deg = dg.c_deg;
+    ra.c_slot = dg.c_slot;
+    ra.col_pos = dg.col_pos;
+    ra.n_rsl = dg.n_rslices;
+    ra.n_csl = dg.n_cslices;
     ra.E_pad = dg.E_pad;
+    ra.Ec_pad = dg.Ec_pad;
     ra.N = a.N;
-    ra.N_pad = (a.N + 7) & ~7;
     ra.llr = a.llr;
     ra.llr_i8 = a.llr_is_i8;
     ra.frames = a.frames;
@@ -319,8 +494,9 @@ int resident_decode(int mode, const DevGraph& dg, const ResidentPlan& p, const D
     ra.out_soft = a.out_soft;
     ra.tile_counter = tile_counter;
     if (cudaMemsetAsync(tile_counter, 0, sizeof(int32_t), st) != cudaSuccess) return LDPC_ERR_CUDA;
-    const int grid = std::max(1, std::min(ra.n_tiles, num_sms * p.ctas_per_sm));
-    return mode == kModeFP32 ? dispatch<kModeFP32>(ra, p, grid, st) : dispatch<kModeFixed>(ra, p, grid, st);
+    if (mode == kModeFP32)
+        return ra.paper ? dispatch<kModeFP32, true>(ra, p, num_sms, st) : dispatch<kModeFP32, false>(ra, p, num_sms, st);
+    return ra.paper ? dispatch<kModeFixed, true>(ra, p, num_sms, st) : dispatch<kModeFixed, false>(ra, p, num_sms, st);
 }
 
 }  // namespace ldpc_impl

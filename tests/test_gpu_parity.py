@@ -155,6 +155,19 @@ def test_long_rows_and_empty_rows_columns(torch_cuda, mode, variant):
     assert_parity(got, oracle_decode(code, llr, 15, mode), mode, "long rows")
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_ties_and_signed_zeros(torch_cuda, mode, variant):
+    """LLRs drawn from {-2, -1, -0.0, +0.0, 1, 2}: ties in every row, zero messages of both
+    signs, zero posteriors; decisions, iteration counts and values must still agree."""
+    code = inputs.qc_code(4, 8, 32, 0.7, 4)
+    rng = np.random.default_rng(17)
+    llr = rng.choice(np.array([-2.0, -1.0, -0.0, 0.0, 1.0, 2.0], np.float32), size=(199, code.N))
+    for es in (True, False):
+        got = gpu_decode(torch_cuda, code, llr, 12, mode, variant, early_stop=es)
+        assert_parity(got, oracle_decode(code, llr, 12, mode, early_stop=es), mode, "ties/zeros")
+
+
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_int8_input_and_saturation(torch_cuda, variant):
     rng = np.random.default_rng(2)
