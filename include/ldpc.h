@@ -128,6 +128,33 @@ int ldpc_decode_host(ldpc_t *h, const void *llr_host, int32_t llr_dtype, int32_t
                      int32_t max_iter, int32_t early_stop, int32_t check_every,
                      uint8_t *bits_host, int32_t *iters_host, uint8_t *ok_host, float *soft_host);
 
+/*
+ * ldpc_decode_noalloc: ldpc_decode_ex without any device allocation. The paper has no
+ * counterpart; this is a service entry point of this library.
+ *
+ * For callers that cannot allocate device memory while they decode: a serving loop that
+ * must not stall on the allocator (cudaMalloc/cudaFree may synchronise the device), a
+ * process whose device memory is already held by another allocator, or an embedding
+ * that forbids allocation after start-up. It runs the streaming kernels with their
+ * scratch taken from one static device array of LDPC_NOALLOC_SCRATCH_BYTES (32 MiB),
+ * which every GPU that loads the library keeps until the process exits.
+ *
+ * Arguments and results are those of ldpc_decode_ex (device pointers). The scratch
+ * needed is about frames_padded * (E*m + N*(m + r) + max_iter + 7) bytes, with
+ * frames_padded = frames rounded up to 256, m = 4 (FP32) or 2 (fixed) and r = 4 or 1;
+ * a larger request returns LDPC_ERR_INVALID_ARG without launching anything. The current
+ * device must be the handle's device (else LDPC_ERR_INVALID_ARG).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Every call uses the same array and each clears what must start from zero; calls whose
+ * work overlaps on the GPU (other streams, or other handles) race on it and must be
+ * serialised by the caller. It does not set ldpc_last_error().
+ */
+#define LDPC_NOALLOC_SCRATCH_BYTES (32u << 20)
+int ldpc_decode_noalloc(ldpc_t *h, const void *llr, int32_t llr_dtype, int32_t frames,
+                        int32_t max_iter, int32_t early_stop, int32_t check_every,
+                        uint8_t *out_bits, int32_t *out_iters, uint8_t *out_ok, float *out_soft);
+
 /* ldpc_set_stream: decode on this cudaStream_t (NULL = legacy default stream). */
 int ldpc_set_stream(ldpc_t *h, void *cuda_stream);
 

@@ -213,6 +213,12 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
     return h;
 }
 
+int ldpc_impl::handle_view(ldpc_t* h, HandleView* v) {
+    if (!h || !v) return LDPC_ERR_BAD_POINTER;
+    *v = HandleView{h->device, h->mode, h->flags, h->M, h->N, h->E, &h->dg, h->stream, &h->last_launches};
+    return LDPC_OK;
+}
+
 extern "C" {
 
 ldpc_t* ldpc_create_ex(int32_t M, int32_t N, int32_t h_format, const void* h_a, const void* h_b,

@@ -6,6 +6,8 @@
 
 #include <vector>
 
+#include "../../include/ldpc.h"
+
 namespace ldpc_impl {
 
 constexpr int kModeFP32 = 0;
@@ -122,5 +124,16 @@ struct ResidentPlan {
 ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device);
 int resident_decode(int mode, const DevGraph& dg, const ResidentPlan& p, const DecodeArgs& a,
                     int32_t* tile_counter, int num_sms, cudaStream_t st);
+
+// Read access to a handle's graph and settings for entry points outside api.cu.
+struct HandleView {
+    int device, mode, flags;
+    int32_t M, N;
+    int64_t E;
+    const DevGraph* dg;
+    cudaStream_t stream;
+    int32_t* last_launches;
+};
+int handle_view(::ldpc_t* h, HandleView* v);
 
 }  // namespace ldpc_impl

@@ -33,6 +33,7 @@ LDPC_FLAG_PAPER_SLICER = 1
 LDPC_VARIANT_AUTO = 0
 LDPC_VARIANT_STREAM = 1
 LDPC_VARIANT_RESIDENT = 2
+LDPC_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 # name -> (restype, argtypes), exactly the declarations of include/ldpc.h
 P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
@@ -44,6 +45,7 @@ SIGNATURES = {
     "ldpc_decode_i8": (ctypes.c_int, [P, P, I32, I32, P, P]),
     "ldpc_decode_ex": (ctypes.c_int, [P, P, I32, I32, I32, I32, I32, P, P, P, P]),
     "ldpc_decode_host": (ctypes.c_int, [P, P, I32, I32, I32, I32, I32, P, P, P, P]),
+    "ldpc_decode_noalloc": (ctypes.c_int, [P, P, I32, I32, I32, I32, I32, P, P, P, P]),
     "ldpc_set_stream": (ctypes.c_int, [P, P]),
     "ldpc_set_mode": (ctypes.c_int, [P, I32]),
     "ldpc_set_variant": (ctypes.c_int, [P, I32]),
@@ -119,6 +121,13 @@ def ldpc_decode_host(h, llr_ptr, llr_dtype, frames, max_iter, early_stop, check_
                      iters_ptr, ok_ptr, soft_ptr):
     return load().ldpc_decode_host(h, llr_ptr, llr_dtype, frames, max_iter, early_stop, check_every,
                                    bits_ptr, iters_ptr, ok_ptr, soft_ptr)
+
+
+def ldpc_decode_noalloc(h, llr_ptr, llr_dtype, frames, max_iter, early_stop, check_every, bits_ptr,
+                        iters_ptr, ok_ptr, soft_ptr):
+    """Decode with scratch from the library's static device array (no allocation)."""
+    return load().ldpc_decode_noalloc(h, llr_ptr, llr_dtype, frames, max_iter, early_stop,
+                                      check_every, bits_ptr, iters_ptr, ok_ptr, soft_ptr)
 
 
 def ldpc_set_stream(h, stream_ptr):
