@@ -262,7 +262,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2507_10424_gb300 import build
+    from paper_2507_10424_gb300 import build, shard
     build.build()
     from paper_2507_10424_gb300.ldpc import Decoder
 
@@ -279,15 +279,11 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return shard.max_over_ranks(x, device="cuda")
 
     code = make_code()
     F, L, mode = args.frames, args.iters, args.mode
-    cw, llr, bounds = make_llr(code, F, 1000 + rank)
+    cw, llr, bounds = make_llr(code, F, shard.rank_seed(1000, rank))
     dec = Decoder.from_code(code, mode=mode)
     dec.set_variant(args.variant)
     variant = dec.variant()
