@@ -165,7 +165,7 @@ def measured_peak_hbm():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("resident_kernels.cu", "stream_kernels.cu", "ldpc_internal.h"):
+    for f in ("resident.cuh", "resident.cu", "stream_kernels.cu", "ldpc_internal.h"):
         with open(os.path.join(ROOT, "paper_2507_10424_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -287,6 +287,7 @@ def main():
     dec = Decoder.from_code(code, mode=mode)
     dec.set_variant(args.variant)
     variant = dec.variant()
+    tuned_ms = dec.autotune(F, L) if variant == "resident" else None  # launch shape for this code
     x = torch.from_numpy(llr).cuda()
     bits = torch.empty((F, code.N), dtype=torch.uint8, device="cuda")
     iters = torch.empty(F, dtype=torch.int32, device="cuda")
@@ -349,6 +350,8 @@ def main():
         "dtype": "f32" if mode == "fp32" else "i16", "data": "synthetic",
         "config": {"workload": workload_name(code, F, L), "frames_per_gpu": F, "iters": L,
                    "early_stop": False, "mode": mode, "variant": variant,
+                   "tuning": ({"frames_per_tile": dec.tuning()[0], "threads": dec.tuning()[1]}
+                              if variant == "resident" else None),
                    "l2": f"inputs larger than L2 ({llr.nbytes / 1e6:.0f} MB of LLRs per step)"},
         "roofline": roofline,
         "gpu_launches": per_step_kernels * args.steps,
@@ -379,6 +382,8 @@ def main():
         for m2, v2 in (("fixed" if mode == "fp32" else "fp32", "auto"), (mode, "stream")):
             d2 = Decoder.from_code(code, mode=m2)
             d2.set_variant(v2)
+            if d2.variant() == "resident":
+                d2.autotune(F, L)
             o2 = (torch.empty_like(bits), torch.empty_like(iters), None, None)
             f2 = lambda: d2.decode(x, L, early_stop=False, out=o2)
             ms2 = timed(f2, max(5, args.steps // 5), 3)

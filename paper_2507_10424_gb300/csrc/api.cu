@@ -48,6 +48,7 @@ struct ldpc {
     int64_t E = 0;
     DevGraph dg;
     ResidentPlan plan[2];
+    ResidentTuning tuning;
     cudaStream_t stream = nullptr;
     // streaming workspace
     StreamWork sw;
@@ -204,6 +205,7 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
             (rc = upload(&d.col_pos, sg.col_pos.data(), sg.col_pos.size())))
             return bail(rc);
         d.sliced = 1;
+        d.max_dc = hg.max_dc;
         h->plan[kModeFP32] = resident_plan(kModeFP32, d, hg.N, h->device);
         h->plan[kModeFixed] = resident_plan(kModeFixed, d, hg.N, h->device);
     }
@@ -395,6 +397,110 @@ int ldpc_set_mode(ldpc_t* h, int32_t mode) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
     if (mode != LDPC_MODE_FP32 && mode != LDPC_MODE_FIXED) return fail(LDPC_ERR_INVALID_ARG);
     h->mode = mode;
+    return LDPC_OK;
+}
+
+int ldpc_set_tuning(ldpc_t* h, int32_t frames_per_tile, int32_t threads) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if ((frames_per_tile != 0 && frames_per_tile != 1 && frames_per_tile != 2 && frames_per_tile != 4) ||
+        threads < 0 || threads % 32)
+        return fail(LDPC_ERR_INVALID_ARG);
+    if (!h->dg.sliced) return fail(LDPC_ERR_UNSUPPORTED);
+    ResidentTuning t;
+    t.FT = frames_per_tile;
+    t.threads = threads;
+    const ResidentPlan p = resident_plan(h->mode, h->dg, h->N, h->device, t);
+    if (!p.ok) return fail(LDPC_ERR_UNSUPPORTED);
+    h->tuning = t;
+    h->plan[kModeFP32] = resident_plan(kModeFP32, h->dg, h->N, h->device, t);
+    h->plan[kModeFixed] = resident_plan(kModeFixed, h->dg, h->N, h->device, t);
+    return LDPC_OK;
+}
+
+int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (frames <= 0 || max_iter < 0) return fail(LDPC_ERR_INVALID_ARG);
+    if (!h->dg.sliced || !h->plan[h->mode].ok) return fail(LDPC_ERR_UNSUPPORTED);
+    const int32_t F = std::min<int32_t>(frames, 16384);
+    void* llr = nullptr;
+    uint8_t* bits = nullptr;
+    int32_t* iters = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (llr) cudaFree(llr);
+        if (bits) cudaFree(bits);
+        if (iters) cudaFree(iters);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&llr, (size_t)F * h->N * 4) != cudaSuccess ||
+        cudaMalloc((void**)&bits, (size_t)F * h->N) != cudaSuccess ||
+        cudaMalloc((void**)&iters, (size_t)F * 4) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return fail(LDPC_ERR_OOM);
+    }
+    // without early stop the work does not depend on the LLR values
+    if (cudaMemsetAsync(llr, 0, (size_t)F * h->N * 4, h->stream) != cudaSuccess) {
+        cleanup();
+        return fail(LDPC_ERR_CUDA);
+    }
+    DecodeArgs a;
+    a.M = h->M;
+    a.N = h->N;
+    a.E = (int32_t)h->E;
+    a.frames = F;
+    a.L = max_iter;
+    a.early_stop = 0;
+    a.check_every = 1;
+    a.paper_slicer = (h->flags & LDPC_FLAG_PAPER_SLICER) ? 1 : 0;
+    a.llr_is_i8 = 0;
+    a.llr = llr;
+    a.out_bits = bits;
+    a.out_iters = iters;
+    a.out_ok = nullptr;
+    a.out_soft = nullptr;
+    float best = -1.0f;
+    ResidentTuning best_t = h->tuning;
+    for (int ft : {1, 2, 4}) {
+        for (int th = 0; th <= 1024; th += (th == 0 ? 256 : 64)) {
+            ResidentTuning t;
+            t.FT = ft;
+            t.threads = th;
+            const ResidentPlan p = resident_plan(h->mode, h->dg, h->N, h->device, t);
+            if (!p.ok) continue;
+            float ms = 0.0f;
+            bool bad = resident_decode(h->mode, h->dg, p, a, h->counters, h->num_sms, h->stream) < 0;
+            bad = bad || cudaEventRecord(e0, h->stream) != cudaSuccess;
+            for (int r = 0; r < 2 && !bad; r++)
+                bad = resident_decode(h->mode, h->dg, p, a, h->counters, h->num_sms, h->stream) < 0;
+            bad = bad || cudaEventRecord(e1, h->stream) != cudaSuccess ||
+                  cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess;
+            if (bad) {
+                cudaGetLastError();
+                continue;  // a shape the device cannot run is skipped
+            }
+            if (best < 0.0f || ms < best) {
+                best = ms;
+                best_t = t;
+            }
+        }
+    }
+    cleanup();
+    if (best < 0.0f) return fail(LDPC_ERR_UNSUPPORTED);
+    h->tuning = best_t;
+    h->plan[h->mode] = resident_plan(h->mode, h->dg, h->N, h->device, best_t);
+    if (best_ms) *best_ms = best / 2.0f;
+    return LDPC_OK;
+}
+
+int ldpc_get_tuning(const ldpc_t* h, int32_t* frames_per_tile, int32_t* threads) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    const ResidentPlan& p = h->plan[h->mode];
+    if (!p.ok) return fail(LDPC_ERR_UNSUPPORTED);
+    if (frames_per_tile) *frames_per_tile = p.FT;
+    if (threads) *threads = p.threads;
     return LDPC_OK;
 }
 

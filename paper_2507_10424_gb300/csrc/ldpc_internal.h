@@ -76,6 +76,7 @@ struct DevGraph {
     uint16_t* col_pos = nullptr;
     int32_t n_rslices = 0, n_cslices = 0, E_pad = 0, Ec_pad = 0;
     int32_t sliced = 0;  // the sliced layout exists
+    int32_t max_dc = 0;  // longest row
 };
 
 // ---------------------------------------------------------------------------------------
@@ -121,7 +122,12 @@ struct ResidentPlan {
     int ctas_per_sm = 0;
     size_t smem = 0;      // dynamic shared memory per CTA
 };
-ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device);
+// Requested plan parameters; 0 = chosen automatically.
+struct ResidentTuning {
+    int FT = 0, threads = 0;
+};
+ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device,
+                           const ResidentTuning& tune = ResidentTuning());
 int resident_decode(int mode, const DevGraph& dg, const ResidentPlan& p, const DecodeArgs& a,
                     int32_t* tile_counter, int num_sms, cudaStream_t st);
 

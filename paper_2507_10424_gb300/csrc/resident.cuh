@@ -22,15 +22,17 @@
 // A frame whose syndrome is zero is written out at once (iterations = k); it keeps being
 // computed with its tile (no per-frame branches in the inner loops) but is never written
 // again. The tile ends when all its frames are out or after max_iter iterations.
+#pragma once
+
 #include <algorithm>
 
 #include "../../include/ldpc.h"
 #include "ldpc_internal.h"
 
 namespace ldpc_impl {
-namespace {
+namespace resident {
 
-constexpr int kMaxThreads = 768;  // 85 registers per thread at one CTA per SM
+constexpr int kMaxThreads = 1024;
 
 template <int MODE>
 struct RT;
@@ -51,8 +53,6 @@ struct alignas(sizeof(T) * V) VecR {
 };
 
 __device__ __forceinline__ int32_t rsat16(int32_t v) { return max(-kSat, min(kSat, v)); }
-__device__ __forceinline__ float rlam(float s, float e) { return s - e; }
-__device__ __forceinline__ int32_t rlam(int32_t s, int32_t e) { return rsat16(s - e); }
 __device__ __forceinline__ float rabs(float x) { return fabsf(x); }
 __device__ __forceinline__ int32_t rabs(int32_t x) { return abs(x); }
 __device__ __forceinline__ float rbig(float) { return __int_as_float(0x7f800000); }
@@ -242,6 +242,25 @@ __device__ __forceinline__ void phase_a(const Idx& ix, VecR<typename RT<MODE>::T
     }
 }
 
+// One phase A of the iteration, specialised on (first, syndrome, update).
+template <int MODE, int FT, bool PAPER>
+__device__ __forceinline__ void phase_a_any(bool first, bool syn, bool upd, const Idx& ix,
+                                            VecR<typename RT<MODE>::T, FT>* eta,
+                                            const VecR<typename RT<MODE>::T, FT>* s, int n_rtasks,
+                                            uint32_t* uw) {
+#define LDPC_PHASE_A(F, S, U) phase_a<MODE, FT, F, S, U, PAPER>(ix, eta, s, n_rtasks, uw)
+    if (first) {
+        if (!upd) LDPC_PHASE_A(true, true, false);
+        else if (syn) LDPC_PHASE_A(true, true, true);
+        else LDPC_PHASE_A(true, false, true);
+    } else {
+        if (!upd) LDPC_PHASE_A(false, true, false);
+        else if (syn) LDPC_PHASE_A(false, true, true);
+        else LDPC_PHASE_A(false, false, true);
+    }
+#undef LDPC_PHASE_A
+}
+
 // Phase B for every column position of the tile.
 template <int MODE, int FT>
 __device__ __forceinline__ void phase_b(const Idx& ix, const VecR<typename RT<MODE>::T, FT>* eta,
@@ -366,15 +385,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
             const bool last = (k == a.L);
             const bool syn = last || (a.early_stop && (k % a.check_every == 0));
             uint32_t* uw = &unsat_w[par];
-            if (k == 0) {
-                if (last) phase_a<MODE, FT, true, true, false, PAPER>(ix, eta, s, n_rtasks, uw);
-                else if (syn) phase_a<MODE, FT, true, true, true, PAPER>(ix, eta, s, n_rtasks, uw);
-                else phase_a<MODE, FT, true, false, true, PAPER>(ix, eta, s, n_rtasks, uw);
-            } else {
-                if (last) phase_a<MODE, FT, false, true, false, PAPER>(ix, eta, s, n_rtasks, uw);
-                else if (syn) phase_a<MODE, FT, false, true, true, PAPER>(ix, eta, s, n_rtasks, uw);
-                else phase_a<MODE, FT, false, false, true, PAPER>(ix, eta, s, n_rtasks, uw);
-            }
+            phase_a_any<MODE, FT, PAPER>(k == 0, syn, !last, ix, eta, s, n_rtasks, uw);
             __syncthreads();
             if (syn) {
                 const uint32_t conv = active & ~unsat_w[par];
@@ -411,92 +422,29 @@ int launch(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t s
     return cudaGetLastError() == cudaSuccess ? 1 : LDPC_ERR_CUDA;
 }
 
-template <int MODE, bool PAPER>
-int dispatch(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
-    if (p.idx_smem) {
-        switch (p.FT) {
-            case 1: return launch<MODE, 1, true, PAPER>(ra, p, num_sms, st);
-            case 2: return launch<MODE, 2, true, PAPER>(ra, p, num_sms, st);
-            case 4: return launch<MODE, 4, true, PAPER>(ra, p, num_sms, st);
-        }
-    } else {
-        switch (p.FT) {
-            case 1: return launch<MODE, 1, false, PAPER>(ra, p, num_sms, st);
-            case 2: return launch<MODE, 2, false, PAPER>(ra, p, num_sms, st);
-        }
+// Instantiations: index arrays in shared memory with FT in {1, 2, 4}; in global memory
+// with FT in {1, 2}; each with the standard and the paper's slicer.
+template <int MODE, bool IDX, bool PAPER>
+int launch_ft(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
+    switch (p.FT) {
+        case 1: return launch<MODE, 1, IDX, PAPER>(ra, p, num_sms, st);
+        case 2: return launch<MODE, 2, IDX, PAPER>(ra, p, num_sms, st);
+        case 4:
+            if constexpr (IDX) return launch<MODE, 4, IDX, PAPER>(ra, p, num_sms, st);
+            break;
     }
     return LDPC_ERR_INVALID_ARG;
 }
 
-}  // namespace
-
-ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device) {
-    ResidentPlan p;
-    if (!dg.sliced) return p;
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    const int tb = mode == kModeFP32 ? 4 : 2;
-    const size_t budget = (size_t)std::max(0, optin - 256);  // static shared memory
-    // up to four interleaved frames (registers); index arrays in shared memory preferred
-    const int fts[] = {4, 2, 1};
-    for (int idx = 1; idx >= 0 && !p.ok; idx--)
-        for (int ft : fts) {
-            if (ft * tb > 16 || (!idx && ft > 2)) continue;
-            const ResLayout L = res_layout(tb, ft, dg.E_pad, dg.Ec_pad, dg.n_rslices, dg.n_cslices, N, idx);
-            if (L.total <= budget) {
-                p.ok = 1;
-                p.FT = ft;
-                p.idx_smem = idx;
-                p.smem = L.total;
-                break;
-            }
-        }
-    if (!p.ok) return p;
-    // threads: minimise the padded work of both phases (rows weigh twice: two sweeps)
-    const int rt = dg.n_rslices * 32;
-    long best = -1;
-    for (int t = 256; t <= kMaxThreads; t += 32) {
-        const long cost = (long)((rt + t - 1) / t) * t * 2 + (long)((N + t - 1) / t) * t;
-        if (best < 0 || cost <= best) {  // ascending t: ties go to the larger CTA
-            best = cost;
-            p.threads = t;
-        }
-    }
-    return p;
+template <int MODE>
+int dispatch(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
+    if (p.idx_smem)
+        return ra.paper ? launch_ft<MODE, true, true>(ra, p, num_sms, st) : launch_ft<MODE, true, false>(ra, p, num_sms, st);
+    return ra.paper ? launch_ft<MODE, false, true>(ra, p, num_sms, st) : launch_ft<MODE, false, false>(ra, p, num_sms, st);
 }
 
-int resident_decode(int mode, const DevGraph& dg, const ResidentPlan& p, const DecodeArgs& a,
-                    int32_t* tile_counter, int num_sms, cudaStream_t st) {
-    ResArgs ra;
-    ra.r_base = dg.r_base;
-    ra.r_deg = dg.r_deg;
-    ra.r_slot_pos = dg.r_slot_pos;
-    ra.c_base = dg.c_base;
-    ra.c_deg = dg.c_deg;
-    ra.c_slot = dg.c_slot;
-    ra.col_pos = dg.col_pos;
-    ra.n_rsl = dg.n_rslices;
-    ra.n_csl = dg.n_cslices;
-    ra.E_pad = dg.E_pad;
-    ra.Ec_pad = dg.Ec_pad;
-    ra.N = a.N;
-    ra.llr = a.llr;
-    ra.llr_i8 = a.llr_is_i8;
-    ra.frames = a.frames;
-    ra.n_tiles = (a.frames + p.FT - 1) / p.FT;
-    ra.L = a.L;
-    ra.early_stop = a.early_stop;
-    ra.check_every = a.check_every;
-    ra.paper = a.paper_slicer;
-    ra.out_bits = a.out_bits;
-    ra.out_iters = a.out_iters;
-    ra.out_ok = a.out_ok;
-    ra.out_soft = a.out_soft;
-    ra.tile_counter = tile_counter;
-    if (cudaMemsetAsync(tile_counter, 0, sizeof(int32_t), st) != cudaSuccess) return LDPC_ERR_CUDA;
-    if (mode == kModeFP32)
-        return ra.paper ? dispatch<kModeFP32, true>(ra, p, num_sms, st) : dispatch<kModeFP32, false>(ra, p, num_sms, st);
-    return ra.paper ? dispatch<kModeFixed, true>(ra, p, num_sms, st) : dispatch<kModeFixed, false>(ra, p, num_sms, st);
-}
+int dispatch_fp32(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st);
+int dispatch_fixed(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st);
 
+}  // namespace resident
 }  // namespace ldpc_impl

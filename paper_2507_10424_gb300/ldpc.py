@@ -49,6 +49,9 @@ SIGNATURES = {
     "ldpc_set_stream": (ctypes.c_int, [P, P]),
     "ldpc_set_mode": (ctypes.c_int, [P, I32]),
     "ldpc_set_variant": (ctypes.c_int, [P, I32]),
+    "ldpc_set_tuning": (ctypes.c_int, [P, I32, I32]),
+    "ldpc_get_tuning": (ctypes.c_int, [P, PI32, PI32]),
+    "ldpc_autotune": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(ctypes.c_float)]),
     "ldpc_get_variant": (ctypes.c_int, [P, PI32]),
     "ldpc_reserve": (ctypes.c_int, [P, I32]),
     "ldpc_info": (ctypes.c_int, [P, PI32, PI32, PI64, PI32, PI32]),
@@ -140,6 +143,22 @@ def ldpc_set_mode(h, mode):
 
 def ldpc_set_variant(h, variant):
     return load().ldpc_set_variant(h, variant)
+
+
+def ldpc_set_tuning(h, frames_per_tile, threads):
+    return load().ldpc_set_tuning(h, frames_per_tile, threads)
+
+
+def ldpc_get_tuning(h):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().ldpc_get_tuning(h, ctypes.byref(a), ctypes.byref(b)), "ldpc_get_tuning")
+    return a.value, b.value
+
+
+def ldpc_autotune(h, frames, max_iter):
+    ms = ctypes.c_float()
+    _check(load().ldpc_autotune(h, frames, max_iter, ctypes.byref(ms)), "ldpc_autotune")
+    return ms.value
 
 
 def ldpc_get_variant(h):
@@ -241,6 +260,19 @@ class Decoder:
         v = {"auto": LDPC_VARIANT_AUTO, "stream": LDPC_VARIANT_STREAM,
              "resident": LDPC_VARIANT_RESIDENT}[variant]
         _check(load().ldpc_set_variant(self.h, v), "ldpc_set_variant")
+
+    def set_tuning(self, frames_per_tile=0, threads=0):
+        _check(load().ldpc_set_tuning(self.h, frames_per_tile, threads), "ldpc_set_tuning")
+
+    def tuning(self):
+        return ldpc_get_tuning(self.h)
+
+    def autotune(self, frames: int, max_iter: int) -> float:
+        """Pick the fastest resident launch shape on this device; returns its time (ms)."""
+        import torch
+        _check(load().ldpc_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+               "ldpc_set_stream")
+        return ldpc_autotune(self.h, frames, max_iter)
 
     def variant(self) -> str:
         return {LDPC_VARIANT_STREAM: "stream", LDPC_VARIANT_RESIDENT: "resident"}[ldpc_get_variant(self.h)]

@@ -206,6 +206,50 @@ def test_edge_cases(torch_cuda, mode, variant):
     assert b.shape == (0, code.N) and it.shape == (0,)
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_every_resident_launch_shape(torch_cuda, mode):
+    """Results must not depend on the launch shape: frames per tile and CTA size."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
+    code = inputs.cfg_qc_2304()
+    cw = inputs.Encoder(code).random_codewords(67, 5)
+    llr = inputs.bpsk_awgn_llr(cw, 2.5, code.design_rate, 6)
+    want = oracle_decode(code, llr, 8, mode)
+    x = torch.from_numpy(llr).cuda()
+    tried = 0
+    for ft in (1, 2, 4):
+        for th in (0, 96, 256, 640, 1024):
+            dec = Decoder.from_code(code, mode=mode)
+            dec.set_variant("resident")
+            try:
+                dec.set_tuning(ft, th)
+            except LdpcError:
+                continue
+            b, it, ok, sf = dec.decode(x, 8, want_ok=True, want_soft=True)
+            torch.cuda.synchronize()
+            got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
+            assert_parity(got, want, mode, f"FT={ft} threads={th}")
+            tried += 1
+            dec.close()
+    assert tried >= 8
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_autotune_keeps_results(torch_cuda, mode):
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder
+    code = inputs.cfg_regular_576()
+    llr = inputs.all_zero_awgn_llr(500, code.N, 2.0, code.design_rate, 91)
+    dec = Decoder.from_code(code, mode=mode)
+    ms = dec.autotune(4096, 10)
+    ft, th = dec.tuning()
+    assert ms > 0 and ft in (1, 2, 4) and th % 32 == 0 and 64 <= th <= 1024
+    b, it, ok, sf = dec.decode(torch.from_numpy(llr).cuda(), 20, want_ok=True, want_soft=True)
+    torch.cuda.synchronize()
+    got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
+    assert_parity(got, oracle_decode(code, llr, 20, mode), mode, "after autotune")
+
+
 def test_errors_on_device_arguments(torch_cuda):
     torch = torch_cuda
     import ctypes
