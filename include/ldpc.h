@@ -95,7 +95,8 @@ ldpc_t *ldpc_create_ex(int32_t M, int32_t N, int32_t h_format, const void *h_a, 
  * out_bits [frames][N], values 0/1) and the iteration count per frame (device int32
  * out_iters [frames]: 0 if the input already satisfies H, else the iteration after which
  * the syndrome was zero, else max_iter). In fixed mode the LLRs are quantised first.
- * frames == 0 is a no-op; frames < 0 or max_iter < 0 give LDPC_ERR_INVALID_ARG.
+ * frames == 0 is a no-op; frames < 0 or max_iter < 0 give LDPC_ERR_INVALID_ARG, and so
+ * does a streaming-variant call with more than 2,097,120 frames (split larger batches).
  */
 int ldpc_decode(ldpc_t *h, const float *llr, int32_t frames, int32_t max_iter, uint8_t *out_bits,
                 int32_t *out_iters);

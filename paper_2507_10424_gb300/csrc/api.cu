@@ -82,7 +82,11 @@ static void free_stream_work(ldpc_t* h) {
     h->sw_cap_L = -1;
 }
 
+// Largest batch of one streaming decode (its grids put frame blocks on the y dimension).
+constexpr int32_t kMaxStreamFrames = 65535 * 32;
+
 static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L) {
+    if (frames > kMaxStreamFrames) return fail(LDPC_ERR_INVALID_ARG);
     const int32_t Fp = (frames + 255) & ~255;
     if (Fp > h->sw_cap) {
         if (h->sw_big) {

@@ -71,6 +71,7 @@ extern "C" int ldpc_decode_noalloc(ldpc_t* h, const void* llr, int32_t llr_dtype
         (out_ok && !is_device(out_ok)) || (out_soft && !is_device(out_soft)))
         return LDPC_ERR_BAD_POINTER;
     // the scratch this request needs, laid out as the streaming workspace
+    if (frames > (int32_t)(kScratchBytes / 8)) return LDPC_ERR_INVALID_ARG;  // cannot fit
     const int32_t Fp = (frames + 255) & ~255;
     const size_t tb = v.mode == kModeFP32 ? 4 : 2, rb = v.mode == kModeFP32 ? 4 : 1;
     const size_t o_eta = 0;

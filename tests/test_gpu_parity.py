@@ -275,6 +275,26 @@ def test_errors_on_device_arguments(torch_cuda):
         d2.set_variant("resident")
 
 
+def test_workspace_too_large_is_an_error_not_a_crash(torch_cuda):
+    """A streaming decode whose workspace cannot be allocated returns LDPC_ERR_OOM before
+    anything is launched (the LLR buffer is never read), and the handle stays usable."""
+    torch = torch_cuda
+    import ctypes
+    from paper_2507_10424_gb300 import ldpc
+    code = inputs.cfg_irregular_64800()
+    dec = ldpc.Decoder.from_code(code)
+    x = torch.zeros((8, code.N), device="cuda")
+    bits = torch.zeros((8, code.N), dtype=torch.uint8, device="cuda")
+    it = torch.zeros(8, dtype=torch.int32, device="cuda")
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    huge = 2_000_000  # frames: about 1.6 TB of edge messages, more than the device holds
+    assert ldpc.ldpc_decode(dec.h, P(x), huge, 5, P(bits), P(it)) == ldpc.LDPC_ERR_OOM
+    assert ldpc.ldpc_reserve(dec.h, huge) == ldpc.LDPC_ERR_OOM
+    assert ldpc.ldpc_decode(dec.h, P(x), 8, 5, P(bits), P(it)) == ldpc.LDPC_OK
+    torch.cuda.synchronize()
+    assert (it.cpu().numpy() >= 0).all()
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_host_buffer_pipeline_matches_device_path(torch_cuda, mode):
     torch = torch_cuda
