@@ -16,6 +16,12 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                                error bound, fixed/float cross-mode identity.
 * ``decode_dense_f32``      -- pinned: identical to the graph form (Algorithms 1 and 2).
 * ``quantize``              -- pinned: closed-form table of the rounding/clamping rule.
+* ``decode_weighted_f32/f64`` (normalised/offset Min-Sum with learned weights, an
+  extension of eq. eta_update) -- pinned: unit weights equal plain Min-Sum bit for bit,
+  single-check closed form, a silencing offset, reuse of the last table row, agreement
+  of the binary64 C and PyTorch implementations (tests/test_learned_oracle.py).
+* ``learned_ref`` (PyTorch, autograd) -- pinned: its forward against the C oracle in
+  binary64, its gradient against central finite differences.
 """
 from __future__ import annotations
 
@@ -68,6 +74,9 @@ def lib():
         for name in ("orc_trace_f32", "orc_trace_fixed"):
             getattr(L, name).argtypes = [P, P, i32, i32, i32, i32, i32, P, P, P, P, P]
         L.orc_decode_dense_f32.argtypes = [i32, i32, P, P, i32, i32, i32, P, P, P, P]
+        L.orc_decode_weighted_f32.argtypes = [P, P, i64, i32, i32, i32, i32, P, i32, i32, P, P,
+                                              P, P, P, P]
+        L.orc_decode_weighted_f64.argtypes = [P, P, i64, i32, P, i32, i32, P, P, P]
         _lib = L
     return _lib
 
@@ -192,6 +201,48 @@ def trace_fixed(g, q, L, early_stop=False, check_every=1, variant=CHECK_TWOMIN, 
                                _p(bits), ctypes.byref(it), ctypes.byref(ok), _p(eta), _p(s))
     assert rc == 0
     return bits, it.value, ok.value, eta, s
+
+
+def column_classes(code):
+    """Class of each bit for learned weights: index of its column weight among the sorted
+    distinct column weights (a single class for a regular code)."""
+    w = code.col_weights()
+    degrees = np.unique(w)
+    return np.searchsorted(degrees, w).astype(np.int32), degrees
+
+
+def decode_weighted_f32(g, llr, L, col_class, alpha, beta, early_stop=True, check_every=1,
+                        flags=0):
+    """Normalised/offset Min-Sum: magnitudes max(fma(alpha, m, -beta), 0); tables [n_w][C]."""
+    r = np.ascontiguousarray(np.atleast_2d(llr), dtype=np.float32)
+    F = r.shape[0]
+    cc = np.ascontiguousarray(col_class, dtype=np.int32)
+    a = np.ascontiguousarray(alpha, dtype=np.float32)
+    b = np.ascontiguousarray(beta, dtype=np.float32)
+    n_w, C = (a.shape if a.ndim == 2 else (0, int(cc.max()) + 1))
+    bits = np.zeros((F, g.N), np.uint8)
+    iters = np.zeros(F, np.int32)
+    ok = np.zeros(F, np.uint8)
+    soft = np.zeros((F, g.N), np.float32)
+    rc = lib().orc_decode_weighted_f32(g.h, _p(r), F, L, int(early_stop), check_every, flags,
+                                       _p(cc), C, n_w, _p(a), _p(b), _p(bits), _p(iters), _p(ok),
+                                       _p(soft))
+    assert rc == 0
+    return bits, iters, ok, soft
+
+
+def decode_weighted_f64(g, llr, L, col_class, alpha, beta):
+    """Binary64, exactly L iterations; returns the posteriors [F][N]."""
+    r = np.ascontiguousarray(np.atleast_2d(llr), dtype=np.float64)
+    F = r.shape[0]
+    cc = np.ascontiguousarray(col_class, dtype=np.int32)
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    soft = np.zeros((F, g.N), np.float64)
+    rc = lib().orc_decode_weighted_f64(g.h, _p(r), F, L, _p(cc), a.shape[1], a.shape[0], _p(a),
+                                       _p(b), _p(soft))
+    assert rc == 0
+    return soft
 
 
 def decode_dense_f32(H: np.ndarray, llr: np.ndarray, L: int, early_stop=True, flags=0):

@@ -706,3 +706,148 @@ int orc_decode_dense_f32(int32_t m, int32_t n, const uint8_t *H, const float *r,
     free(lam); free(eta); free(s); free(min0); free(min1); free(loc); free(sgn); free(zi);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Normalised / offset Min-Sum with learned weights (an extension of eq.      */
+/* (eta_update); not in the paper). Every check-to-bit magnitude m is replaced */
+/* by max(alpha * m - beta, 0), computed as one fused multiply-add, with alpha */
+/* and beta chosen by the iteration k (row min(k, n_w) - 1 of the tables) and */
+/* by the class of the edge's bit (col_class[j] in [0, n_classes)). With      */
+/* alpha = 1 and beta = 0 this is plain Min-Sum. FP32 and binary64.           */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    const int32_t *col_class;
+    int32_t n_classes, n_w;
+    const float *alpha, *beta;   /* [n_w][n_classes] */
+    const double *alpha64, *beta64;
+} orc_weights;
+
+static inline float weigh_f32(const orc_weights *w, int32_t k, int32_t j, float m) {
+    if (!w || w->n_w <= 0) return m;
+    int32_t row = (k < w->n_w ? k : w->n_w) - 1;
+    int32_t c = w->col_class[j];
+    float a = fmaf(w->alpha[row * w->n_classes + c], m, -w->beta[row * w->n_classes + c]);
+    return a > 0.0f ? a : 0.0f;
+}
+
+static inline double weigh_f64(const orc_weights *w, int32_t k, int32_t j, double m) {
+    if (!w || w->n_w <= 0) return m;
+    int32_t row = (k < w->n_w ? k : w->n_w) - 1;
+    int32_t c = w->col_class[j];
+    double a = fma(w->alpha64[row * w->n_classes + c], m, -w->beta64[row * w->n_classes + c]);
+    return a > 0.0 ? a : 0.0;
+}
+
+/* One frame; the check update through Observations 1 and 2, magnitudes weighted. */
+static int decode_frame_w_f32(const orc_graph *g, const orc_opts *o, const orc_weights *w,
+                              const float *r, uint8_t *b, int32_t *iters, uint8_t *ok, float *soft,
+                              float *eta, float *s, float *lam) {
+    const int32_t M = g->M, N = g->N;
+    const int64_t E = g->E;
+    for (int32_t j = 0; j < N; j++) s[j] = r[j];
+    for (int64_t e = 0; e < E; e++) eta[e] = 0.0f;
+    for (int32_t j = 0; j < N; j++) b[j] = slice_f32(s[j], o->flags);
+    int32_t k = 0;
+    int done = test_now(o, 0) && orc_syndrome(g, b, NULL) == 0;
+    while (!done && k < o->L) {
+        for (int32_t i = 0; i < M; i++) {
+            int64_t e0 = g->row_ptr[i], d = g->row_ptr[i + 1] - e0;
+            float min0 = INFINITY, min1 = INFINITY;
+            int64_t loc = -1;
+            int neg = 0;
+            for (int64_t t = 0; t < d; t++) {
+                lam[t] = s[g->col_of[e0 + t]] - eta[e0 + t];
+                float a = fabsf(lam[t]);
+                if (a < min0) { min1 = min0; min0 = a; loc = t; }
+                else if (a < min1) { min1 = a; }
+                if (lam[t] < 0.0f) neg ^= 1;
+            }
+            for (int64_t t = 0; t < d; t++) {
+                float m = weigh_f32(w, k + 1, g->col_of[e0 + t], t == loc ? min1 : min0);
+                eta[e0 + t] = (neg ^ (lam[t] < 0.0f)) ? -m : m;
+            }
+        }
+        for (int32_t j = 0; j < N; j++) {
+            float acc = r[j];
+            for (int64_t t = g->col_ptr[j]; t < g->col_ptr[j + 1]; t++) acc = acc + eta[g->edge_of[t]];
+            s[j] = acc;
+        }
+        k++;
+        for (int32_t j = 0; j < N; j++) b[j] = slice_f32(s[j], o->flags);
+        if (test_now(o, k) && orc_syndrome(g, b, NULL) == 0) done = 1;
+    }
+    *iters = k;
+    *ok = (uint8_t)(orc_syndrome(g, b, NULL) == 0);
+    if (soft) memcpy(soft, s, sizeof(float) * (size_t)N);
+    return ORC_OK;
+}
+
+static int decode_frame_w_f64(const orc_graph *g, const orc_opts *o, const orc_weights *w,
+                              const double *r, double *soft, double *eta, double *s, double *lam) {
+    const int32_t M = g->M, N = g->N;
+    for (int32_t j = 0; j < N; j++) s[j] = r[j];
+    for (int64_t e = 0; e < g->E; e++) eta[e] = 0.0;
+    for (int32_t k = 0; k < o->L; k++) {
+        for (int32_t i = 0; i < M; i++) {
+            int64_t e0 = g->row_ptr[i], d = g->row_ptr[i + 1] - e0;
+            double min0 = INFINITY, min1 = INFINITY;
+            int64_t loc = -1;
+            int neg = 0;
+            for (int64_t t = 0; t < d; t++) {
+                lam[t] = s[g->col_of[e0 + t]] - eta[e0 + t];
+                double a = fabs(lam[t]);
+                if (a < min0) { min1 = min0; min0 = a; loc = t; }
+                else if (a < min1) { min1 = a; }
+                if (lam[t] < 0.0) neg ^= 1;
+            }
+            for (int64_t t = 0; t < d; t++) {
+                double m = weigh_f64(w, k + 1, g->col_of[e0 + t], t == loc ? min1 : min0);
+                eta[e0 + t] = (neg ^ (lam[t] < 0.0)) ? -m : m;
+            }
+        }
+        for (int32_t j = 0; j < N; j++) {
+            double acc = r[j];
+            for (int64_t t = g->col_ptr[j]; t < g->col_ptr[j + 1]; t++) acc = acc + eta[g->edge_of[t]];
+            s[j] = acc;
+        }
+    }
+    memcpy(soft, s, sizeof(double) * (size_t)N);
+    return ORC_OK;
+}
+
+/* Batch of FP32 frames with early stop options, like orc_decode_f32. */
+int orc_decode_weighted_f32(const orc_graph *g, const float *r, int64_t F, int32_t L,
+                            int32_t early_stop, int32_t check_every, int32_t flags,
+                            const int32_t *col_class, int32_t n_classes, int32_t n_w,
+                            const float *alpha, const float *beta, uint8_t *bits, int32_t *iters,
+                            uint8_t *ok, float *soft) {
+    if (!g || F < 0 || L < 0 || n_classes < 1 || n_w < 0) return ORC_ERR_ARG;
+    for (int32_t j = 0; j < g->N; j++)
+        if (col_class[j] < 0 || col_class[j] >= n_classes) return ORC_ERR_ARG;
+    orc_opts o = {L, early_stop, check_every, ORC_CHECK_TWOMIN, flags};
+    orc_weights w = {col_class, n_classes, n_w, alpha, beta, NULL, NULL};
+    const int64_t D = max_row_degree(g);
+    float *eta = malloc(sizeof(float) * (size_t)(g->E > 0 ? g->E : 1));
+    float *s = malloc(sizeof(float) * (size_t)g->N), *lam = malloc(sizeof(float) * (size_t)D);
+    for (int64_t f = 0; f < F; f++)
+        decode_frame_w_f32(g, &o, &w, r + f * g->N, bits + f * g->N, iters + f, ok + f,
+                           soft ? soft + f * g->N : NULL, eta, s, lam);
+    free(eta); free(s); free(lam);
+    return ORC_OK;
+}
+
+/* Batch of binary64 frames, exactly L iterations (no early stop): the posteriors only. */
+int orc_decode_weighted_f64(const orc_graph *g, const double *r, int64_t F, int32_t L,
+                            const int32_t *col_class, int32_t n_classes, int32_t n_w,
+                            const double *alpha, const double *beta, double *soft) {
+    if (!g || F < 0 || L < 0 || n_classes < 1 || n_w < 0) return ORC_ERR_ARG;
+    orc_opts o = {L, 0, 1, ORC_CHECK_TWOMIN, 0};
+    orc_weights w = {col_class, n_classes, n_w, NULL, NULL, alpha, beta};
+    const int64_t D = max_row_degree(g);
+    double *eta = malloc(sizeof(double) * (size_t)(g->E > 0 ? g->E : 1));
+    double *s = malloc(sizeof(double) * (size_t)g->N), *lam = malloc(sizeof(double) * (size_t)D);
+    for (int64_t f = 0; f < F; f++) decode_frame_w_f64(g, &o, &w, r + f * g->N, soft + f * g->N, eta, s, lam);
+    free(eta); free(s); free(lam);
+    return ORC_OK;
+}
