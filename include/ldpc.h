@@ -156,6 +156,48 @@ int ldpc_decode_noalloc(ldpc_t *h, const void *llr, int32_t llr_dtype, int32_t f
                         int32_t max_iter, int32_t early_stop, int32_t check_every,
                         uint8_t *out_bits, int32_t *out_iters, uint8_t *out_ok, float *out_soft);
 
+/*
+ * Learned normalised / offset Min-Sum (an extension of eq. eta_update; the paper has
+ * plain Min-Sum only). Each extrinsic magnitude m of the check update becomes
+ * max(fma(alpha, m, -beta), 0) in binary32, with (alpha, beta) chosen by the iteration t
+ * and by the class of the edge's bit: classes are the distinct column weights of H in
+ * ascending order (one class for a regular code). alpha = 1, beta = 0 is plain Min-Sum,
+ * bit for bit.
+ *
+ * ldpc_classes: number of classes and (degrees, nullable) the column weight of each.
+ */
+int ldpc_classes(const ldpc_t *h, int32_t *n_classes, int32_t *degrees);
+
+/* ldpc_set_weights: decode with learned weights from now on (FP32 mode; decodes in fixed
+ * mode then return LDPC_ERR_UNSUPPORTED). alpha, beta: host [n_rows][n_classes]; iteration
+ * t uses row min(t, n_rows) - 1. n_rows = 0 returns to plain Min-Sum. */
+int ldpc_set_weights(ldpc_t *h, int32_t n_rows, const float *alpha, const float *beta);
+
+/* ldpc_train_workspace_size: device bytes that ldpc_train_forward/backward need for
+ * `frames` frames and `iters` unrolled iterations (about frames x (16 N + 8 E + iters x
+ * (E + 12 M)) bytes). */
+int ldpc_train_workspace_size(ldpc_t *h, int32_t frames, int32_t iters, uint64_t *bytes);
+
+/* ldpc_train_forward: `iters` flooding iterations (no early stop) of the learned decoder
+ * on FP32 LLRs (device [frames][N]); alpha, beta: device [iters][n_classes]. Writes the
+ * posteriors to device float `soft`: [frames][N] after the last iteration (soft_every = 0;
+ * equal to ldpc_decode_ex's out_soft with the same weights and early_stop = 0), or
+ * [iters][frames][N] after every iteration (soft_every = 1). Keeps, in `work` (device,
+ * caller-owned), the per-iteration compressed check state the backward pass needs. */
+int ldpc_train_forward(ldpc_t *h, const float *llr, int32_t frames, int32_t iters,
+                       const float *alpha, const float *beta, float *soft, int32_t soft_every,
+                       void *work, uint64_t work_bytes);
+
+/* ldpc_train_backward: adjoint of the preceding ldpc_train_forward (same frames, iters,
+ * weights, soft_every and work): from grad_soft (device, shaped like that call's `soft`:
+ * the loss gradient w.r.t. the posteriors) computes grad_alpha and grad_beta (device
+ * [iters][n_classes], overwritten). Messages are rebuilt per iteration from the saved
+ * state; the gradient follows the edge attaining each minimum (a subgradient) and treats
+ * signs as constant. */
+int ldpc_train_backward(ldpc_t *h, int32_t frames, int32_t iters, const float *alpha,
+                        const float *beta, const float *grad_soft, int32_t soft_every,
+                        float *grad_alpha, float *grad_beta, void *work, uint64_t work_bytes);
+
 /* ldpc_set_stream: decode on this cudaStream_t (NULL = legacy default stream). */
 int ldpc_set_stream(ldpc_t *h, void *cuda_stream);
 

@@ -49,6 +49,11 @@ struct ldpc {
     DevGraph dg;
     ResidentPlan plan[2];
     ResidentTuning tuning;
+    std::vector<int32_t> class_degree;
+    // learned weights (FP32 mode)
+    int32_t w_rows = 0;
+    float* w_alpha = nullptr;  // device [w_rows][n_classes], then beta
+    // training scratch: accumulators of the weight gradients are the caller's
     cudaStream_t stream = nullptr;
     // streaming workspace
     StreamWork sw;
@@ -66,7 +71,8 @@ struct ldpc {
 
 static void free_graph(DevGraph& g) {
     void* ptrs[] = {g.row_ptr, g.col_idx, g.col_ptr, g.col_edge, g.packed, g.r_base,
-                    g.r_deg, g.r_slot_pos, g.c_base, g.c_deg, g.c_slot, g.col_pos};
+                    g.r_deg, g.r_slot_pos, g.c_base, g.c_deg, g.c_slot, g.col_pos,
+                    g.col_class, g.r_slot_cls};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     g = DevGraph();
@@ -136,6 +142,14 @@ static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L) {
     return LDPC_OK;
 }
 
+// Resident plans for both modes under the current tuning and weights.
+static void replan(ldpc_t* h) {
+    if (!h->dg.sliced) return;
+    const int we = h->w_rows * h->dg.n_classes;
+    h->plan[kModeFP32] = resident_plan(kModeFP32, h->dg, h->N, h->device, h->tuning, we);
+    h->plan[kModeFixed] = resident_plan(kModeFixed, h->dg, h->N, h->device, h->tuning, 0);
+}
+
 static int resolved_variant(const ldpc_t* h) {
     if (h->variant == LDPC_VARIANT_STREAM) return LDPC_VARIANT_STREAM;
     if (h->variant == LDPC_VARIANT_RESIDENT) return LDPC_VARIANT_RESIDENT;
@@ -183,6 +197,12 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
         (rc = upload(&h->dg.col_ptr, hg.col_ptr.data(), hg.col_ptr.size())) ||
         (rc = upload(&h->dg.col_edge, hg.col_edge.data(), hg.col_edge.size())))
         return bail(rc);
+    h->dg.max_dc = hg.max_dc;
+    // edge classes (learned weights)
+    h->class_degree = hg.class_degree;
+    h->dg.n_classes = (int32_t)hg.class_degree.size();
+    if (h->dg.n_classes > 255) h->dg.n_classes = 0;  // weights unsupported for such codes
+    if ((rc = upload(&h->dg.col_class, hg.col_class.data(), hg.col_class.size()))) return bail(rc);
     // bit-packed rows
     {
         const int64_t W = (hg.N + 31) / 32;
@@ -206,10 +226,10 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
             (rc = upload(&d.c_base, sg.c_base.data(), sg.c_base.size())) ||
             (rc = upload(&d.c_deg, sg.c_deg.data(), sg.c_deg.size())) ||
             (rc = upload(&d.c_slot, sg.c_slot.data(), sg.c_slot.size())) ||
-            (rc = upload(&d.col_pos, sg.col_pos.data(), sg.col_pos.size())))
+            (rc = upload(&d.col_pos, sg.col_pos.data(), sg.col_pos.size())) ||
+            (rc = upload(&d.r_slot_cls, sg.r_slot_cls.data(), sg.r_slot_cls.size())))
             return bail(rc);
         d.sliced = 1;
-        d.max_dc = hg.max_dc;
         h->plan[kModeFP32] = resident_plan(kModeFP32, d, hg.N, h->device);
         h->plan[kModeFixed] = resident_plan(kModeFixed, d, hg.N, h->device);
     }
@@ -221,7 +241,8 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
 
 int ldpc_impl::handle_view(ldpc_t* h, HandleView* v) {
     if (!h || !v) return LDPC_ERR_BAD_POINTER;
-    *v = HandleView{h->device, h->mode, h->flags, h->M, h->N, h->E, &h->dg, h->stream, &h->last_launches};
+    *v = HandleView{h->device, h->mode, h->flags, h->M, h->N, h->E, &h->dg, h->stream,
+                    &h->last_launches, h->w_rows, h->w_alpha};
     return LDPC_OK;
 }
 
@@ -267,6 +288,7 @@ int ldpc_decode_ex(ldpc_t* h, const void* llr, int32_t llr_dtype, int32_t frames
     if (frames < 0 || max_iter < 0 || check_every < 1) return fail(LDPC_ERR_INVALID_ARG);
     if (llr_dtype != LDPC_LLR_F32 && llr_dtype != LDPC_LLR_I8) return fail(LDPC_ERR_INVALID_ARG);
     if (llr_dtype == LDPC_LLR_I8 && h->mode != kModeFixed) return fail(LDPC_ERR_INVALID_ARG);
+    if (h->w_rows > 0 && h->mode != kModeFP32) return fail(LDPC_ERR_UNSUPPORTED);
     h->last_launches = 0;
     if (frames == 0) return LDPC_OK;
     if (!is_device_ptr(llr) || !is_device_ptr(out_bits) || !is_device_ptr(out_iters) ||
@@ -287,6 +309,12 @@ int ldpc_decode_ex(ldpc_t* h, const void* llr, int32_t llr_dtype, int32_t frames
     a.out_iters = out_iters;
     a.out_ok = out_ok;
     a.out_soft = out_soft;
+    if (h->w_rows > 0 && h->mode == kModeFP32) {
+        a.w_rows = h->w_rows;
+        a.n_classes = h->dg.n_classes;
+        a.w_alpha = h->w_alpha;
+        a.w_beta = h->w_alpha + (size_t)h->w_rows * h->dg.n_classes;
+    }
     int n;
     if (resolved_variant(h) == LDPC_VARIANT_RESIDENT) {
         if (!h->plan[h->mode].ok) return fail(LDPC_ERR_UNSUPPORTED);
@@ -413,11 +441,11 @@ int ldpc_set_tuning(ldpc_t* h, int32_t frames_per_tile, int32_t threads) {
     ResidentTuning t;
     t.FT = frames_per_tile;
     t.threads = threads;
-    const ResidentPlan p = resident_plan(h->mode, h->dg, h->N, h->device, t);
+    const ResidentPlan p = resident_plan(h->mode, h->dg, h->N, h->device, t,
+                                         h->mode == kModeFP32 ? h->w_rows * h->dg.n_classes : 0);
     if (!p.ok) return fail(LDPC_ERR_UNSUPPORTED);
     h->tuning = t;
-    h->plan[kModeFP32] = resident_plan(kModeFP32, h->dg, h->N, h->device, t);
-    h->plan[kModeFixed] = resident_plan(kModeFixed, h->dg, h->N, h->device, t);
+    replan(h);
     return LDPC_OK;
 }
 
@@ -465,6 +493,12 @@ int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
     a.out_iters = iters;
     a.out_ok = nullptr;
     a.out_soft = nullptr;
+    if (h->w_rows > 0 && h->mode == kModeFP32) {
+        a.w_rows = h->w_rows;
+        a.n_classes = h->dg.n_classes;
+        a.w_alpha = h->w_alpha;
+        a.w_beta = h->w_alpha + (size_t)h->w_rows * h->dg.n_classes;
+    }
     float best = -1.0f;
     ResidentTuning best_t = h->tuning;
     for (int ft : {1, 2, 4}) {
@@ -472,7 +506,8 @@ int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
             ResidentTuning t;
             t.FT = ft;
             t.threads = th;
-            const ResidentPlan p = resident_plan(h->mode, h->dg, h->N, h->device, t);
+            const ResidentPlan p = resident_plan(h->mode, h->dg, h->N, h->device, t,
+                                                 h->mode == kModeFP32 ? h->w_rows * h->dg.n_classes : 0);
             if (!p.ok) continue;
             float ms = 0.0f;
             bool bad = resident_decode(h->mode, h->dg, p, a, h->counters, h->num_sms, h->stream) < 0;
@@ -494,7 +529,7 @@ int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
     cleanup();
     if (best < 0.0f) return fail(LDPC_ERR_UNSUPPORTED);
     h->tuning = best_t;
-    h->plan[h->mode] = resident_plan(h->mode, h->dg, h->N, h->device, best_t);
+    replan(h);
     if (best_ms) *best_ms = best / 2.0f;
     return LDPC_OK;
 }
@@ -505,6 +540,38 @@ int ldpc_get_tuning(const ldpc_t* h, int32_t* frames_per_tile, int32_t* threads)
     if (!p.ok) return fail(LDPC_ERR_UNSUPPORTED);
     if (frames_per_tile) *frames_per_tile = p.FT;
     if (threads) *threads = p.threads;
+    return LDPC_OK;
+}
+
+int ldpc_classes(const ldpc_t* h, int32_t* n_classes, int32_t* degrees) {
+    if (!h || !n_classes) return fail(LDPC_ERR_BAD_POINTER);
+    *n_classes = h->dg.n_classes;
+    if (degrees)
+        for (int32_t c = 0; c < h->dg.n_classes; c++) degrees[c] = h->class_degree[c];
+    return LDPC_OK;
+}
+
+int ldpc_set_weights(ldpc_t* h, int32_t n_rows, const float* alpha, const float* beta) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (n_rows < 0 || n_rows > 4096) return fail(LDPC_ERR_INVALID_ARG);
+    if (n_rows > 0 && (!alpha || !beta)) return fail(LDPC_ERR_BAD_POINTER);
+    if (n_rows > 0 && h->dg.n_classes == 0) return fail(LDPC_ERR_UNSUPPORTED);
+    cudaStreamSynchronize(h->stream);
+    if (h->w_alpha) cudaFree(h->w_alpha);
+    h->w_alpha = nullptr;
+    h->w_rows = 0;
+    if (n_rows == 0) {
+        replan(h);
+        return LDPC_OK;
+    }
+    const size_t n = (size_t)n_rows * h->dg.n_classes;
+    std::vector<float> tab(2 * n);
+    std::copy(alpha, alpha + n, tab.begin());
+    std::copy(beta, beta + n, tab.begin() + n);
+    int rc = upload(&h->w_alpha, tab.data(), tab.size());
+    if (rc != LDPC_OK) return rc;
+    h->w_rows = n_rows;
+    replan(h);
     return LDPC_OK;
 }
 
@@ -580,6 +647,7 @@ void ldpc_destroy(ldpc_t* h) {
     free_stream_work(h);
     free_graph(h->dg);
     if (h->counters) cudaFree(h->counters);
+    if (h->w_alpha) cudaFree(h->w_alpha);
     delete h;
 }
 

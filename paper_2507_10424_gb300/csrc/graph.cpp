@@ -27,7 +27,20 @@ static int finish_graph(HostGraph& g) {
         for (int32_t e = g.row_ptr[i]; e < g.row_ptr[i + 1]; e++) g.col_edge[fill[g.col_idx[e]]++] = e;
     g.max_dv = 0;
     for (int32_t j = 0; j < N; j++) g.max_dv = std::max(g.max_dv, g.col_ptr[j + 1] - g.col_ptr[j]);
+    assign_classes(g);
     return LDPC_OK;
+}
+
+void assign_classes(HostGraph& g) {
+    g.class_degree.clear();
+    for (int32_t j = 0; j < g.N; j++) g.class_degree.push_back(g.col_ptr[j + 1] - g.col_ptr[j]);
+    std::sort(g.class_degree.begin(), g.class_degree.end());
+    g.class_degree.erase(std::unique(g.class_degree.begin(), g.class_degree.end()), g.class_degree.end());
+    g.col_class.assign(g.N, 0);
+    for (int32_t j = 0; j < g.N; j++)
+        g.col_class[j] = (uint8_t)(std::lower_bound(g.class_degree.begin(), g.class_degree.end(),
+                                                    g.col_ptr[j + 1] - g.col_ptr[j]) -
+                                   g.class_degree.begin());
 }
 
 int graph_from_dense(int32_t M, int32_t N, const uint8_t* H, HostGraph& g) {
@@ -148,12 +161,14 @@ bool build_sliced(const HostGraph& g, SlicedGraph& sg) {
     // row side: slot of every edge, and the sorted column position it reads
     std::vector<int32_t> slot_of_edge(g.E);
     sg.r_slot_pos.assign(sg.E_pad, 0);
+    sg.r_slot_cls.assign(sg.E_pad, 0);
     for (int32_t s = 0; s < sg.n_rslices; s++)
         for (int32_t l = 0; l < 32 && s * 32 + l < g.M; l++) {
             const int32_t i = rorder[s * 32 + l];
             for (int32_t k = 0; k < g.row_ptr[i + 1] - g.row_ptr[i]; k++) {
                 const int32_t slot = sg.r_base[s] + 32 * k + l, e = g.row_ptr[i] + k;
                 sg.r_slot_pos[slot] = sg.col_pos[g.col_idx[e]];
+                sg.r_slot_cls[slot] = g.col_class.empty() ? 0 : g.col_class[g.col_idx[e]];
                 slot_of_edge[e] = slot;
             }
         }

@@ -26,7 +26,12 @@ struct HostGraph {
     std::vector<int32_t> col_ptr;   // N+1
     std::vector<int32_t> col_edge;  // E: CSR edge ids of column j, ascending row
     int32_t max_dc = 0, max_dv = 0;
+    // edge classes for learned weights: class of bit j = index of its column weight among
+    // the sorted distinct column weights
+    std::vector<int32_t> class_degree;  // n_classes
+    std::vector<uint8_t> col_class;     // N
 };
+void assign_classes(HostGraph& g);
 
 // Each returns LDPC_OK or an LDPC_ERR_* status.
 int graph_from_dense(int32_t M, int32_t N, const uint8_t* H, HostGraph& g);
@@ -53,6 +58,7 @@ struct SlicedGraph {
     std::vector<uint8_t> c_deg;         // 32 * n_cslices (0 for missing columns)
     std::vector<uint16_t> c_slot;       // Ec_pad
     std::vector<uint16_t> col_pos;      // N
+    std::vector<uint8_t> r_slot_cls;    // E_pad: class of the edge's bit (0 for padding)
 };
 // Returns false when the code cannot use 16-bit slot ids or 8-bit degrees.
 bool build_sliced(const HostGraph& g, SlicedGraph& sg);
@@ -66,6 +72,8 @@ struct DevGraph {
     int32_t* col_edge = nullptr;
     // bit-packed rows, uint32 [M][ceil(N/32)]
     uint32_t* packed = nullptr;
+    uint8_t* col_class = nullptr;  // N
+    int32_t n_classes = 0;
     // sliced layout (resident kernel)
     int32_t* r_base = nullptr;
     uint8_t* r_deg = nullptr;
@@ -74,9 +82,10 @@ struct DevGraph {
     uint8_t* c_deg = nullptr;
     uint16_t* c_slot = nullptr;
     uint16_t* col_pos = nullptr;
+    uint8_t* r_slot_cls = nullptr;
     int32_t n_rslices = 0, n_cslices = 0, E_pad = 0, Ec_pad = 0;
     int32_t sliced = 0;  // the sliced layout exists
-    int32_t max_dc = 0;  // longest row
+    int32_t max_dc = 0;  // longest row (set for every code)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -95,6 +104,11 @@ struct DecodeArgs {
     int32_t* out_iters;   // [frames]
     uint8_t* out_ok;      // nullable
     float* out_soft;      // nullable
+    // learned weights (FP32 mode): w_rows > 0 -> magnitudes max(fma(alpha, m, -beta), 0),
+    // row min(iteration, w_rows) - 1 of the [w_rows][n_classes] device tables
+    int32_t w_rows = 0, n_classes = 0;
+    const float* w_alpha = nullptr;
+    const float* w_beta = nullptr;
 };
 
 // Streaming variant workspace (frame-interleaved, frame stride Fp).
@@ -127,7 +141,7 @@ struct ResidentTuning {
     int FT = 0, threads = 0;
 };
 ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device,
-                           const ResidentTuning& tune = ResidentTuning());
+                           const ResidentTuning& tune = ResidentTuning(), int w_entries = 0);
 int resident_decode(int mode, const DevGraph& dg, const ResidentPlan& p, const DecodeArgs& a,
                     int32_t* tile_counter, int num_sms, cudaStream_t st);
 
@@ -139,6 +153,8 @@ struct HandleView {
     const DevGraph* dg;
     cudaStream_t stream;
     int32_t* last_launches;
+    int32_t w_rows;          // learned weights in force (FP32 mode), 0 if none
+    const float* w_alpha;    // device [w_rows][n_classes], beta follows
 };
 int handle_view(::ldpc_t* h, HandleView* v);
 

@@ -62,6 +62,7 @@ extern "C" int ldpc_decode_noalloc(ldpc_t* h, const void* llr, int32_t llr_dtype
     if (frames < 0 || max_iter < 0 || check_every < 1) return LDPC_ERR_INVALID_ARG;
     if (llr_dtype != LDPC_LLR_F32 && llr_dtype != LDPC_LLR_I8) return LDPC_ERR_INVALID_ARG;
     if (llr_dtype == LDPC_LLR_I8 && v.mode != kModeFixed) return LDPC_ERR_INVALID_ARG;
+    if (v.w_rows > 0 && v.mode != kModeFP32) return LDPC_ERR_UNSUPPORTED;
     *v.last_launches = 0;
     if (frames == 0) return LDPC_OK;
     int device = -1;
@@ -110,6 +111,12 @@ extern "C" int ldpc_decode_noalloc(ldpc_t* h, const void* llr, int32_t llr_dtype
     a.out_iters = out_iters;
     a.out_ok = out_ok;
     a.out_soft = out_soft;
+    if (v.w_rows > 0) {  // learned weights set on the handle
+        a.w_rows = v.w_rows;
+        a.n_classes = v.dg->n_classes;
+        a.w_alpha = v.w_alpha;
+        a.w_beta = v.w_alpha + (size_t)v.w_rows * v.dg->n_classes;
+    }
     // the kernels clear the done counter and the syndrome flags and set the frame state
     const int n = stream_decode(v.mode, *v.dg, a, w, v.stream);
     if (n < 0) return n;

@@ -6,7 +6,7 @@ namespace ldpc_impl {
 using namespace resident;
 
 ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device,
-                           const ResidentTuning& tune) {
+                           const ResidentTuning& tune, int w_entries) {
     ResidentPlan p;
     if (!dg.sliced) return p;
     int optin = 0;
@@ -19,7 +19,8 @@ ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device,
         for (int ft : fts) {
             if (ft * tb > 16 || (!idx && ft > 2)) continue;
             if (tune.FT && ft != tune.FT) continue;
-            const ResLayout L = res_layout(tb, ft, dg.E_pad, dg.Ec_pad, dg.n_rslices, dg.n_cslices, N, idx);
+            const ResLayout L = res_layout(tb, ft, dg.E_pad, dg.Ec_pad, dg.n_rslices, dg.n_cslices, N, idx,
+                                           mode == kModeFP32 ? w_entries : 0);
             if (L.total <= budget) {
                 p.ok = 1;
                 p.FT = ft;
@@ -65,6 +66,11 @@ int resident_decode(int mode, const DevGraph& dg, const ResidentPlan& p, const D
     ra.c_deg = dg.c_deg;
     ra.c_slot = dg.c_slot;
     ra.col_pos = dg.col_pos;
+    ra.r_slot_cls = dg.r_slot_cls;
+    ra.w_rows = mode == kModeFP32 ? a.w_rows : 0;
+    ra.n_classes = a.n_classes;
+    ra.w_alpha = a.w_alpha;
+    ra.w_beta = a.w_beta;
     ra.n_rsl = dg.n_rslices;
     ra.n_csl = dg.n_cslices;
     ra.E_pad = dg.E_pad;

@@ -72,11 +72,11 @@ __device__ __forceinline__ int8_t rquant(float x) {
 
 // Byte offsets of the shared-memory regions (host and device agree on them).
 struct ResLayout {
-    uint32_t eta, s, r, rpos, cslot, cpos, rdeg, cdeg, rbase, cbase, total;
+    uint32_t eta, s, r, rpos, cslot, cpos, rdeg, cdeg, rbase, cbase, wcls, wtab, total;
 };
 __host__ __device__ inline uint32_t al16(uint32_t x) { return (x + 15u) & ~15u; }
 __host__ __device__ inline ResLayout res_layout(int tb, int FT, int E_pad, int Ec_pad, int n_rsl,
-                                                int n_csl, int N, bool idx) {
+                                                int n_csl, int N, bool idx, int w_entries = 0) {
     ResLayout L{};
     uint32_t o = 0;
     L.eta = o;
@@ -100,6 +100,12 @@ __host__ __device__ inline ResLayout res_layout(int tb, int FT, int E_pad, int E
         o = al16(o + (uint32_t)(n_rsl + 1) * 4);
         L.cbase = o;
         o = al16(o + (uint32_t)(n_csl + 1) * 4);
+        if (w_entries > 0) {  // learned weights: class of each row slot, alpha and beta tables
+            L.wcls = o;
+            o = al16(o + (uint32_t)E_pad);
+            L.wtab = o;
+            o = al16(o + (uint32_t)w_entries * 2 * 4);
+        }
     }
     L.total = o;
     return L;
@@ -113,7 +119,11 @@ struct ResArgs {
     const uint8_t* c_deg;
     const uint16_t* c_slot;
     const uint16_t* col_pos;
+    const uint8_t* r_slot_cls;
     int32_t n_rsl, n_csl, E_pad, Ec_pad, N;
+    int32_t w_rows, n_classes;  // learned weights (FP32), w_rows = 0: plain Min-Sum
+    const float* w_alpha;       // [w_rows][n_classes]
+    const float* w_beta;
     const void* llr;
     int32_t llr_i8;
     int32_t frames, n_tiles, L, early_stop, check_every, paper;
@@ -132,6 +142,9 @@ struct Idx {
     const uint8_t* c_deg;
     const uint16_t* c_slot;
     const uint16_t* col_pos;
+    const uint8_t* wcls;   // class of each row slot (learned weights)
+    const float* walpha;   // alpha row of the current iteration
+    const float* wbeta;    // beta row of the current iteration
 };
 
 // Channel value of (frame, bit) in the arithmetic of the mode.
@@ -170,7 +183,7 @@ __device__ __forceinline__ int snake(int k, int nth) {
 // stashes lambda in the edge's slot; sweep 2 turns each stashed lambda into the new
 // message: magnitude min1 where |lambda| = min0 (on a tie min1 = min0, so the first
 // location needs no tracking), else min0; sign = total sign x own sign.
-template <int MODE, int FT, bool FIRST, bool SYN, bool UPD, bool PAPER>
+template <int MODE, int FT, bool FIRST, bool SYN, bool UPD, bool PAPER, bool W>
 __device__ __forceinline__ void phase_a(const Idx& ix, VecR<typename RT<MODE>::T, FT>* eta,
                                         const VecR<typename RT<MODE>::T, FT>* s, int n_rtasks,
                                         uint32_t* unsat_w) {
@@ -229,11 +242,21 @@ __device__ __forceinline__ void phase_a(const Idx& ix, VecR<typename RT<MODE>::T
             for (int t = 0; t < d; t++) {
                 const int slot = base + 32 * t;
                 const VT lv = eta[slot];
+                float wa = 1.0f, wb = 0.0f;
+                if constexpr (W) {
+                    const int c = ix.wcls[slot];
+                    wa = ix.walpha[c];
+                    wb = ix.wbeta[c];
+                }
                 VT out;
 #pragma unroll
                 for (int f = 0; f < FT; f++) {
                     const A lam = (A)lv.x[f];
-                    const A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
+                    A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
+                    if constexpr (W) {  // max(fma(alpha, m, -beta), 0)
+                        const float x = __fmaf_rn(wa, (float)m, -wb);
+                        m = (A)(x > 0.0f ? x : 0.0f);
+                    }
                     out.x[f] = (T)with_sign(m, bits_of(lam) ^ sx[f]);
                 }
                 eta[slot] = out;
@@ -243,12 +266,12 @@ __device__ __forceinline__ void phase_a(const Idx& ix, VecR<typename RT<MODE>::T
 }
 
 // One phase A of the iteration, specialised on (first, syndrome, update).
-template <int MODE, int FT, bool PAPER>
+template <int MODE, int FT, bool PAPER, bool W>
 __device__ __forceinline__ void phase_a_any(bool first, bool syn, bool upd, const Idx& ix,
                                             VecR<typename RT<MODE>::T, FT>* eta,
                                             const VecR<typename RT<MODE>::T, FT>* s, int n_rtasks,
                                             uint32_t* uw) {
-#define LDPC_PHASE_A(F, S, U) phase_a<MODE, FT, F, S, U, PAPER>(ix, eta, s, n_rtasks, uw)
+#define LDPC_PHASE_A(F, S, U) phase_a<MODE, FT, F, S, U, PAPER, W>(ix, eta, s, n_rtasks, uw)
     if (first) {
         if (!upd) LDPC_PHASE_A(true, true, false);
         else if (syn) LDPC_PHASE_A(true, true, true);
@@ -323,15 +346,16 @@ __device__ __forceinline__ void copy_to_smem(T* dst, const T* src, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
-template <int MODE, int FT, bool IDX_SMEM, bool PAPER>
+template <int MODE, int FT, bool IDX_SMEM, bool PAPER, bool W>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
     using T = typename RT<MODE>::T;
     using VT = VecR<T, FT>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t unsat_w[2];
     __shared__ int tile_sh;
+    const int w_entries = W ? a.w_rows * a.n_classes : 0;
     const ResLayout lay = res_layout((int)sizeof(T), FT, a.E_pad, a.Ec_pad, a.n_rsl, a.n_csl, a.N,
-                                     IDX_SMEM);
+                                     IDX_SMEM, w_entries);
     VT* eta = reinterpret_cast<VT*>(smem_raw + lay.eta);
     VT* s = reinterpret_cast<VT*>(smem_raw + lay.s);
     VT* r = reinterpret_cast<VT*>(smem_raw + lay.r);
@@ -351,10 +375,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
         copy_to_smem(cdeg, a.c_deg, a.n_csl * 32);
         copy_to_smem(rbase, a.r_base, a.n_rsl + 1);
         copy_to_smem(cbase, a.c_base, a.n_csl + 1);
-        ix = Idx{rbase, rdeg, rpos, cbase, cdeg, cslot, cpos};
+        ix = Idx{rbase, rdeg, rpos, cbase, cdeg, cslot, cpos, nullptr, nullptr, nullptr};
+        if (W) {
+            uint8_t* wcls = smem_raw + lay.wcls;
+            float* wtab = reinterpret_cast<float*>(smem_raw + lay.wtab);
+            copy_to_smem(wcls, a.r_slot_cls, a.E_pad);
+            copy_to_smem(wtab, a.w_alpha, w_entries);
+            copy_to_smem(wtab + w_entries, a.w_beta, w_entries);
+            ix.wcls = wcls;
+            ix.walpha = wtab;
+            ix.wbeta = wtab + w_entries;
+        }
     } else {
-        ix = Idx{a.r_base, a.r_deg, a.r_slot_pos, a.c_base, a.c_deg, a.c_slot, a.col_pos};
+        ix = Idx{a.r_base, a.r_deg, a.r_slot_pos, a.c_base, a.c_deg, a.c_slot, a.col_pos,
+                 a.r_slot_cls, a.w_alpha, a.w_beta};
     }
+    const float* walpha0 = ix.walpha;
+    const float* wbeta0 = ix.wbeta;
     const int N = a.N, n_rtasks = a.n_rsl * 32;
 
     for (;;) {
@@ -385,7 +422,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
             const bool last = (k == a.L);
             const bool syn = last || (a.early_stop && (k % a.check_every == 0));
             uint32_t* uw = &unsat_w[par];
-            phase_a_any<MODE, FT, PAPER>(k == 0, syn, !last, ix, eta, s, n_rtasks, uw);
+            if (W) {  // weights of iteration k + 1 (the last row serves the later iterations)
+                const int row = min(k + 1, a.w_rows) - 1;
+                ix.walpha = walpha0 + row * a.n_classes;
+                ix.wbeta = wbeta0 + row * a.n_classes;
+            }
+            phase_a_any<MODE, FT, PAPER, W>(k == 0, syn, !last, ix, eta, s, n_rtasks, uw);
             __syncthreads();
             if (syn) {
                 const uint32_t conv = active & ~unsat_w[par];
@@ -408,9 +450,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
     }
 }
 
-template <int MODE, int FT, bool IDX, bool PAPER>
+template <int MODE, int FT, bool IDX, bool PAPER, bool W>
 int launch(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
-    auto kern = k_resident<MODE, FT, IDX, PAPER>;
+    auto kern = k_resident<MODE, FT, IDX, PAPER, W>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
     int per_sm = 0;
@@ -424,23 +466,33 @@ int launch(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t s
 
 // Instantiations: index arrays in shared memory with FT in {1, 2, 4}; in global memory
 // with FT in {1, 2}; each with the standard and the paper's slicer.
-template <int MODE, bool IDX, bool PAPER>
+template <int MODE, bool IDX, bool PAPER, bool W>
 int launch_ft(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
     switch (p.FT) {
-        case 1: return launch<MODE, 1, IDX, PAPER>(ra, p, num_sms, st);
-        case 2: return launch<MODE, 2, IDX, PAPER>(ra, p, num_sms, st);
+        case 1: return launch<MODE, 1, IDX, PAPER, W>(ra, p, num_sms, st);
+        case 2: return launch<MODE, 2, IDX, PAPER, W>(ra, p, num_sms, st);
         case 4:
-            if constexpr (IDX) return launch<MODE, 4, IDX, PAPER>(ra, p, num_sms, st);
+            if constexpr (IDX) return launch<MODE, 4, IDX, PAPER, W>(ra, p, num_sms, st);
             break;
     }
     return LDPC_ERR_INVALID_ARG;
 }
 
+template <int MODE, bool W>
+int dispatch_w(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
+    if (p.idx_smem)
+        return ra.paper ? launch_ft<MODE, true, true, W>(ra, p, num_sms, st)
+                        : launch_ft<MODE, true, false, W>(ra, p, num_sms, st);
+    return ra.paper ? launch_ft<MODE, false, true, W>(ra, p, num_sms, st)
+                    : launch_ft<MODE, false, false, W>(ra, p, num_sms, st);
+}
+
+// Learned weights exist in FP32 mode only.
 template <int MODE>
 int dispatch(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
-    if (p.idx_smem)
-        return ra.paper ? launch_ft<MODE, true, true>(ra, p, num_sms, st) : launch_ft<MODE, true, false>(ra, p, num_sms, st);
-    return ra.paper ? launch_ft<MODE, false, true>(ra, p, num_sms, st) : launch_ft<MODE, false, false>(ra, p, num_sms, st);
+    if constexpr (MODE == kModeFP32)
+        if (ra.w_rows > 0) return dispatch_w<MODE, true>(ra, p, num_sms, st);
+    return dispatch_w<MODE, false>(ra, p, num_sms, st);
 }
 
 int dispatch_fp32(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st);

@@ -110,14 +110,22 @@ __global__ void k_load(const void* llr, int llr_i8, int frames, int N, typename 
 // Check-node pass. Block = 4 warps = 4 rows; lane = one frame vector (V frames).
 // MODE_SYN: syndrome only (final status pass), no message update.
 // ------------------------------------------------------------------------------------
-template <int MODE, bool FIRST, bool SYN_ONLY>
+// Learned weights of one iteration: magnitude m of an edge whose bit has class c becomes
+// max(fma(alpha[c], m, -beta[c]), 0).
+struct IterWeights {
+    const uint8_t* col_class;
+    const float* alpha;
+    const float* beta;
+};
+
+template <int MODE, bool FIRST, bool SYN_ONLY, bool W = false>
 __global__ void __launch_bounds__(128) k_check(const int32_t* __restrict__ row_ptr,
                                                const int32_t* __restrict__ col_idx, int M,
                                                const typename Tr<MODE>::T* __restrict__ s,
                                                typename Tr<MODE>::T* eta, int Fp,
                                                const uint8_t* __restrict__ state, uint8_t* unsat,
                                                int do_syn, const int* n_done, int frames,
-                                               int paper) {
+                                               int paper, IterWeights wt = IterWeights()) {
     using T = typename Tr<MODE>::T;
     using A = typename Tr<MODE>::A;
     constexpr int V = Tr<MODE>::V;
@@ -189,11 +197,21 @@ __global__ void __launch_bounds__(128) k_check(const int32_t* __restrict__ row_p
         T* ep = eta + (size_t)(e0 + t) * Fp + f0;
         VT lv;
         if (longrow) lv = *reinterpret_cast<const VT*>(ep);
+        float wa = 1.0f, wb = 0.0f;
+        if constexpr (W) {
+            const int c = __ldg(wt.col_class + __ldg(col_idx + e0 + t));
+            wa = __ldg(wt.alpha + c);
+            wb = __ldg(wt.beta + c);
+        }
         VT out;
 #pragma unroll
         for (int v = 0; v < V; v++) {
             const uint32_t sg = longrow ? (uint32_t)((A)lv.x[v] < A(0)) : ((msk[v] >> t) & 1u);
-            const A m = (t == loc[v]) ? min1[v] : min0[v];
+            A m = (t == loc[v]) ? min1[v] : min0[v];
+            if constexpr (W) {
+                const float x = __fmaf_rn(wa, (float)m, -wb);
+                m = (A)(x > 0.0f ? x : 0.0f);
+            }
             out.x[v] = (T)((((neg >> v) ^ sg) & 1u) ? -m : m);
         }
         *reinterpret_cast<VT*>(ep) = out;
@@ -333,7 +351,19 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
     for (int k = 1; k <= a.L; k++) {
         const int test_prev = a.early_stop && ((k - 1) % a.check_every == 0);
         uint8_t* un = w.unsat + (size_t)k * Fp;
-        if (k == 1)
+        if (MODE == kModeFP32 && a.w_rows > 0) {
+            const int row = (k < a.w_rows ? k : a.w_rows) - 1;
+            const IterWeights wt{g.col_class, a.w_alpha + (size_t)row * a.n_classes,
+                                 a.w_beta + (size_t)row * a.n_classes};
+            if (k == 1)
+                k_check<MODE, true, false, true><<<gc, 128, 0, st>>>(
+                    g.row_ptr, g.col_idx, a.M, s, eta, Fp, state, un, test_prev, w.n_done, a.frames,
+                    a.paper_slicer, wt);
+            else
+                k_check<MODE, false, false, true><<<gc, 128, 0, st>>>(
+                    g.row_ptr, g.col_idx, a.M, s, eta, Fp, state, un, test_prev, w.n_done, a.frames,
+                    a.paper_slicer, wt);
+        } else if (k == 1)
             k_check<MODE, true, false><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp,
                                                            state, un, test_prev, w.n_done,
                                                            a.frames, a.paper_slicer);

@@ -52,6 +52,11 @@ SIGNATURES = {
     "ldpc_set_tuning": (ctypes.c_int, [P, I32, I32]),
     "ldpc_get_tuning": (ctypes.c_int, [P, PI32, PI32]),
     "ldpc_autotune": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(ctypes.c_float)]),
+    "ldpc_classes": (ctypes.c_int, [P, PI32, PI32]),
+    "ldpc_set_weights": (ctypes.c_int, [P, I32, P, P]),
+    "ldpc_train_workspace_size": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(ctypes.c_uint64)]),
+    "ldpc_train_forward": (ctypes.c_int, [P, P, I32, I32, P, P, P, I32, P, ctypes.c_uint64]),
+    "ldpc_train_backward": (ctypes.c_int, [P, I32, I32, P, P, P, I32, P, P, P, ctypes.c_uint64]),
     "ldpc_get_variant": (ctypes.c_int, [P, PI32]),
     "ldpc_reserve": (ctypes.c_int, [P, I32]),
     "ldpc_info": (ctypes.c_int, [P, PI32, PI32, PI64, PI32, PI32]),
@@ -161,6 +166,38 @@ def ldpc_autotune(h, frames, max_iter):
     return ms.value
 
 
+def ldpc_classes(h):
+    n = ctypes.c_int32()
+    _check(load().ldpc_classes(h, ctypes.byref(n), None), "ldpc_classes")
+    deg = (ctypes.c_int32 * max(n.value, 1))()
+    _check(load().ldpc_classes(h, ctypes.byref(n), deg), "ldpc_classes")
+    return [deg[i] for i in range(n.value)]
+
+
+def ldpc_set_weights(h, n_rows, alpha_ptr, beta_ptr):
+    return load().ldpc_set_weights(h, n_rows, alpha_ptr, beta_ptr)
+
+
+def ldpc_train_workspace_size(h, frames, iters):
+    b = ctypes.c_uint64()
+    _check(load().ldpc_train_workspace_size(h, frames, iters, ctypes.byref(b)),
+           "ldpc_train_workspace_size")
+    return b.value
+
+
+def ldpc_train_forward(h, llr_ptr, frames, iters, alpha_ptr, beta_ptr, soft_ptr, soft_every,
+                       work_ptr, work_bytes):
+    return load().ldpc_train_forward(h, llr_ptr, frames, iters, alpha_ptr, beta_ptr, soft_ptr,
+                                     soft_every, work_ptr, work_bytes)
+
+
+def ldpc_train_backward(h, frames, iters, alpha_ptr, beta_ptr, grad_soft_ptr, soft_every,
+                        grad_alpha_ptr, grad_beta_ptr, work_ptr, work_bytes):
+    return load().ldpc_train_backward(h, frames, iters, alpha_ptr, beta_ptr, grad_soft_ptr,
+                                      soft_every, grad_alpha_ptr, grad_beta_ptr, work_ptr,
+                                      work_bytes)
+
+
 def ldpc_get_variant(h):
     v = ctypes.c_int32()
     _check(load().ldpc_get_variant(h, ctypes.byref(v)), "ldpc_get_variant")
@@ -266,6 +303,21 @@ class Decoder:
 
     def tuning(self):
         return ldpc_get_tuning(self.h)
+
+    def classes(self):
+        """Column weight of each learned-weight class (distinct column weights, ascending)."""
+        return ldpc_classes(self.h)
+
+    def set_weights(self, alpha=None, beta=None):
+        """Learned weights [rows][classes] (numpy or CPU tensors); None clears them."""
+        if alpha is None:
+            _check(load().ldpc_set_weights(self.h, 0, None, None), "ldpc_set_weights")
+            return
+        a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float32))
+        b = np.ascontiguousarray(np.asarray(beta, dtype=np.float32))
+        if a.shape != b.shape or a.ndim != 2 or a.shape[1] != len(self.classes()):
+            raise ValueError("alpha and beta must be [rows][n_classes]")
+        _check(load().ldpc_set_weights(self.h, a.shape[0], _host(a), _host(b)), "ldpc_set_weights")
 
     def autotune(self, frames: int, max_iter: int) -> float:
         """Pick the fastest resident launch shape on this device; returns its time (ms)."""
