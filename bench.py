@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=65536)
     ap.add_argument("--iters", type=int, default=10)
     ap.add_argument("--variant", choices=["auto", "resident", "stream"], default="auto")
+    ap.add_argument("--tuning", default="auto",
+                    help="resident launch shape 'FT,threads[,index placement]' instead of the autotuner")
     ap.add_argument("--quick", action="store_true", help="skip the extra measurements")
     return ap.parse_args()
 
@@ -163,12 +165,13 @@ def measured_peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
-    h = hashlib.sha256()
-    for f in ("resident.cuh", "resident.cu", "stream_kernels.cu", "ldpc_internal.h"):
-        with open(os.path.join(ROOT, "paper_2507_10424_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+KERNEL_SOURCES = {"k_resident": "resident.cuh", "k_check": "stream_kernels.cu"}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the file holding a kernel's device code (the traffic record goes stale with it)."""
+    with open(os.path.join(ROOT, "paper_2507_10424_gb300", "csrc", KERNEL_SOURCES[kernel]), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
 def ncu_traffic(kernel, mode, F):
@@ -180,7 +183,7 @@ def ncu_traffic(kernel, mode, F):
     except Exception:
         return None
     e = t.get(f"{kernel}:{mode}")
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return e["dram_bytes_per_launch"] * F / e["frames"]
 
@@ -207,6 +210,47 @@ def oracle_rate(code, llr, L, mode, budget_s=10.0, threads=None):
     run(llr[:n])
     dt = time.perf_counter() - t
     return n * code.N / dt / 1e9, n, dt
+
+
+# ------------------------------------------------------------------ learned decoder
+
+def learned_vs_plain(timed):
+    """Learned normalised/offset Min-Sum on the (3,6)-regular N=576 code: trained here
+    (10 unrolled iterations, 4096-frame batches at Eb/N0 uniform in [1, 4] dB), then the
+    iteration limit at which it matches plain Min-Sum's frame error rate, and decoded Gbit/s
+    of both at equal FER (early stop, 65536 frames at 2.5 dB)."""
+    import torch
+    from paper_2507_10424_gb300 import inputs, learn
+    from paper_2507_10424_gb300.ldpc import Decoder
+    code = inputs.cfg_regular_576()
+    dec = Decoder.from_code(code)
+    t = time.perf_counter()
+    alpha, beta, losses = learn.train_weights(dec, code, iters=10, steps=400, batch=4096, lr=0.02,
+                                              seed=1, every=True)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t
+    rows = learn.compare(dec, code, (alpha, beta), ebn0_points=(2.0, 2.5, 3.0), frames=20000)
+    match = {f"{e:.1f}dB": {f"plain@{p}": learn.iterations_to_match(rows, e, p) for p in (10, 20)}
+             for e in (2.0, 2.5, 3.0)}
+    # throughput at equal FER: plain at 20 iterations vs learned at its matching limit
+    L_l = match["2.5dB"]["plain@20"] or 20
+    src = learn.FrameSource(code, seed=11)
+    llr, bits = src.batch(65536, 2.5)
+    out = (torch.empty_like(bits), torch.empty(65536, dtype=torch.int32, device="cuda"), None, None)
+    res = {}
+    for name, w, L in (("plain", None, 20), ("learned", (alpha, beta), L_l)):
+        dec.set_weights(*(w if w else (None,)))
+        dec.autotune(65536, L)
+        ms = timed(lambda: dec.decode(llr, L, early_stop=True, out=out), 10, 3)
+        fer = float((out[0] != bits).any(dim=1).float().mean().item())
+        res[name] = {"max_iter": L, "ms_per_step": ms, "Gbit/s": 65536 * code.N / (ms * 1e-3) / 1e9,
+                     "fer": fer, "mean_iter": float(out[1].float().mean().item())}
+    dec.set_weights(None)
+    return {"code": "(3,6)-regular N=576 M=288", "train_steps": 400, "train_s": train_s,
+            "loss_first_last": [float(np.mean(losses[:10])), float(np.mean(losses[-10:]))],
+            "alpha": alpha[:, 0].round(4).tolist(), "beta": beta[:, 0].round(4).tolist(),
+            "iterations_to_match_plain_fer": match, "equal_fer_throughput_2.5dB": res,
+            "fer_table": rows}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -287,7 +331,11 @@ def main():
     dec = Decoder.from_code(code, mode=mode)
     dec.set_variant(args.variant)
     variant = dec.variant()
-    tuned_ms = dec.autotune(F, L) if variant == "resident" else None  # launch shape for this code
+    if variant == "resident":  # launch shape for this code on this GPU
+        if args.tuning == "auto":
+            dec.autotune(F, L)
+        else:
+            dec.set_tuning(*[int(v) for v in args.tuning.split(",")])
     x = torch.from_numpy(llr).cuda()
     bits = torch.empty((F, code.N), dtype=torch.uint8, device="cuda")
     iters = torch.empty(F, dtype=torch.int32, device="cuda")
@@ -350,7 +398,7 @@ def main():
         "dtype": "f32" if mode == "fp32" else "i16", "data": "synthetic",
         "config": {"workload": workload_name(code, F, L), "frames_per_gpu": F, "iters": L,
                    "early_stop": False, "mode": mode, "variant": variant,
-                   "tuning": ({"frames_per_tile": dec.tuning()[0], "threads": dec.tuning()[1]}
+                   "tuning": (dict(zip(("frames_per_tile", "threads", "index_placement"), dec.tuning()))
                               if variant == "resident" else None),
                    "l2": f"inputs larger than L2 ({llr.nbytes / 1e6:.0f} MB of LLRs per step)"},
         "roofline": roofline,
@@ -394,6 +442,8 @@ def main():
                 "hbm_edge_message_GBs": ach2, "frac": ach2 / peak}
             d2.close()
         result["other_paths"] = others
+        if rank == 0:
+            result["learned"] = learned_vs_plain(timed)
         if world == 1 and rank == 0:
             val, n, dt = oracle_rate(code, llr, L, mode)
             result["cpu_baseline"] = {"value": val, "unit": "Gbit/s", "cores": cpu_threads(),

@@ -211,16 +211,19 @@ int ldpc_set_variant(ldpc_t *h, int32_t variant);
 /*
  * ldpc_set_tuning: launch shape of the resident kernel (0 = automatic for each field).
  * frames_per_tile in {0, 1, 2, 4}: frames interleaved per CTA tile; threads: CTA size
- * (a multiple of 32, at most 1024). Results do not depend on the tuning.
+ * (a multiple of 32, at most 1024); index_placement: 1 = the code's index arrays are copied
+ * to shared memory, 2 = read from global memory (leaves room for more CTAs per SM).
+ * Results do not depend on the tuning.
  * LDPC_ERR_UNSUPPORTED when the requested shape does not fit this code (the previous
  * tuning stays in force), LDPC_ERR_INVALID_ARG for values outside these sets. (The paper
  * tunes blocks and threads per kernel by hand, Section IV; this is the knob the
  * autotuner turns.)
  */
-int ldpc_set_tuning(ldpc_t *h, int32_t frames_per_tile, int32_t threads);
+int ldpc_set_tuning(ldpc_t *h, int32_t frames_per_tile, int32_t threads, int32_t index_placement);
 
 /*
- * ldpc_autotune: time the resident kernel's launch shapes (frames per tile x CTA size)
+ * ldpc_autotune: time the resident kernel's launch shapes (frames per tile x index
+ * placement x CTA size)
  * on this device for this code and mode, on min(frames, 16384) frames of max_iter
  * iterations without early stop, and keep the fastest (as ldpc_set_tuning would).
  * Allocates and frees its own temporary device buffers; synchronises the handle's
@@ -230,7 +233,8 @@ int ldpc_set_tuning(ldpc_t *h, int32_t frames_per_tile, int32_t threads);
 int ldpc_autotune(ldpc_t *h, int32_t frames, int32_t max_iter, float *best_ms);
 
 /* ldpc_get_tuning: the resident launch shape in force for the current mode. */
-int ldpc_get_tuning(const ldpc_t *h, int32_t *frames_per_tile, int32_t *threads);
+int ldpc_get_tuning(const ldpc_t *h, int32_t *frames_per_tile, int32_t *threads,
+                    int32_t *index_placement);
 
 /* ldpc_get_variant: the variant the next decode will run (AUTO resolved). */
 int ldpc_get_variant(const ldpc_t *h, int32_t *variant);

@@ -22,6 +22,13 @@ int cuda_fail(cudaError_t e) {
     g_last_cuda = (int)e;
     return fail(LDPC_ERR_CUDA);
 }
+// A failed allocation: clear the runtime's pending error (else the next successful call
+// would report it) and map it to a status.
+int alloc_fail(cudaError_t e) {
+    cudaGetLastError();
+    g_last_cuda = (int)e;
+    return fail(e == cudaErrorMemoryAllocation ? LDPC_ERR_OOM : LDPC_ERR_CUDA);
+}
 #define CK(call)                                   \
     do {                                           \
         cudaError_t e_ = (call);                   \
@@ -32,7 +39,10 @@ template <typename T>
 int upload(T** dst, const T* src, size_t n) {
     *dst = nullptr;
     cudaError_t e = cudaMalloc((void**)dst, (n ? n : 1) * sizeof(T));  // never a null array
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(LDPC_ERR_OOM) : cuda_fail(e);
+    if (e != cudaSuccess) {
+        *dst = nullptr;
+        return alloc_fail(e);
+    }
     if (src && n) {
         e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -108,7 +118,7 @@ static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L) {
         if (e != cudaSuccess) {
             h->sw_big = nullptr;
             h->sw_cap = 0;
-            return e == cudaErrorMemoryAllocation ? fail(LDPC_ERR_OOM) : cuda_fail(e);
+            return alloc_fail(e);
         }
         char* p = (char*)h->sw_big;
         h->sw.eta = p;
@@ -131,8 +141,9 @@ static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L) {
         }
         cudaError_t e = cudaMalloc((void**)&h->sw_unsat, (size_t)(L + 2) * h->sw_cap);
         if (e != cudaSuccess) {
+            h->sw_unsat = nullptr;
             h->sw_cap_L = -1;
-            return e == cudaErrorMemoryAllocation ? fail(LDPC_ERR_OOM) : cuda_fail(e);
+            return alloc_fail(e);
         }
         h->sw_cap_L = L;
     }
@@ -234,7 +245,7 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
         h->plan[kModeFixed] = resident_plan(kModeFixed, d, hg.N, h->device);
     }
     e = cudaMalloc((void**)&h->counters, 4 * sizeof(int32_t));
-    if (e != cudaSuccess) return bail(cuda_fail(e));
+    if (e != cudaSuccess) return bail(alloc_fail(e));
     g_last_error = LDPC_OK;
     return h;
 }
@@ -378,8 +389,9 @@ int ldpc_decode_host(ldpc_t* h, const void* llr_host, int32_t llr_dtype, int32_t
             }
             cudaError_t e = cudaMalloc(&h->stage[s], need);
             if (e != cudaSuccess) {
+                h->stage[s] = nullptr;
                 h->stage_bytes = 0;
-                return e == cudaErrorMemoryAllocation ? fail(LDPC_ERR_OOM) : cuda_fail(e);
+                return alloc_fail(e);
             }
         }
         h->stage_bytes = need;
@@ -432,15 +444,16 @@ int ldpc_set_mode(ldpc_t* h, int32_t mode) {
     return LDPC_OK;
 }
 
-int ldpc_set_tuning(ldpc_t* h, int32_t frames_per_tile, int32_t threads) {
+int ldpc_set_tuning(ldpc_t* h, int32_t frames_per_tile, int32_t threads, int32_t index_placement) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
     if ((frames_per_tile != 0 && frames_per_tile != 1 && frames_per_tile != 2 && frames_per_tile != 4) ||
-        threads < 0 || threads % 32)
+        threads < 0 || threads % 32 || index_placement < 0 || index_placement > 2)
         return fail(LDPC_ERR_INVALID_ARG);
     if (!h->dg.sliced) return fail(LDPC_ERR_UNSUPPORTED);
     ResidentTuning t;
     t.FT = frames_per_tile;
     t.threads = threads;
+    t.idx = index_placement;
     const ResidentPlan p = resident_plan(h->mode, h->dg, h->N, h->device, t,
                                          h->mode == kModeFP32 ? h->w_rows * h->dg.n_classes : 0);
     if (!p.ok) return fail(LDPC_ERR_UNSUPPORTED);
@@ -501,11 +514,13 @@ int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
     }
     float best = -1.0f;
     ResidentTuning best_t = h->tuning;
-    for (int ft : {1, 2, 4}) {
+    for (int ft : {1, 2, 4})
+    for (int ip : {1, 2})
         for (int th = 0; th <= 1024; th += (th == 0 ? 256 : 64)) {
             ResidentTuning t;
             t.FT = ft;
             t.threads = th;
+            t.idx = ip;
             const ResidentPlan p = resident_plan(h->mode, h->dg, h->N, h->device, t,
                                                  h->mode == kModeFP32 ? h->w_rows * h->dg.n_classes : 0);
             if (!p.ok) continue;
@@ -525,7 +540,6 @@ int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
                 best_t = t;
             }
         }
-    }
     cleanup();
     if (best < 0.0f) return fail(LDPC_ERR_UNSUPPORTED);
     h->tuning = best_t;
@@ -534,12 +548,14 @@ int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
     return LDPC_OK;
 }
 
-int ldpc_get_tuning(const ldpc_t* h, int32_t* frames_per_tile, int32_t* threads) {
+int ldpc_get_tuning(const ldpc_t* h, int32_t* frames_per_tile, int32_t* threads,
+                    int32_t* index_placement) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
     const ResidentPlan& p = h->plan[h->mode];
     if (!p.ok) return fail(LDPC_ERR_UNSUPPORTED);
     if (frames_per_tile) *frames_per_tile = p.FT;
     if (threads) *threads = p.threads;
+    if (index_placement) *index_placement = p.idx_smem ? 1 : 2;
     return LDPC_OK;
 }
 

@@ -139,6 +139,7 @@ struct ResidentPlan {
 // Requested plan parameters; 0 = chosen automatically.
 struct ResidentTuning {
     int FT = 0, threads = 0;
+    int idx = 0;  // index arrays: 0 automatic, 1 shared memory, 2 global memory
 };
 ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device,
                            const ResidentTuning& tune = ResidentTuning(), int w_entries = 0);

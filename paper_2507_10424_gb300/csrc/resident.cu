@@ -17,6 +17,7 @@ ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device,
     const int fts[] = {4, 2, 1};
     for (int idx = 1; idx >= 0 && !p.ok; idx--)
         for (int ft : fts) {
+            if ((tune.idx == 1 && !idx) || (tune.idx == 2 && idx)) continue;
             if (ft * tb > 16 || (!idx && ft > 2)) continue;
             if (tune.FT && ft != tune.FT) continue;
             const ResLayout L = res_layout(tb, ft, dg.E_pad, dg.Ec_pad, dg.n_rslices, dg.n_cslices, N, idx,

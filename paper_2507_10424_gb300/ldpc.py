@@ -49,8 +49,8 @@ SIGNATURES = {
     "ldpc_set_stream": (ctypes.c_int, [P, P]),
     "ldpc_set_mode": (ctypes.c_int, [P, I32]),
     "ldpc_set_variant": (ctypes.c_int, [P, I32]),
-    "ldpc_set_tuning": (ctypes.c_int, [P, I32, I32]),
-    "ldpc_get_tuning": (ctypes.c_int, [P, PI32, PI32]),
+    "ldpc_set_tuning": (ctypes.c_int, [P, I32, I32, I32]),
+    "ldpc_get_tuning": (ctypes.c_int, [P, PI32, PI32, PI32]),
     "ldpc_autotune": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(ctypes.c_float)]),
     "ldpc_classes": (ctypes.c_int, [P, PI32, PI32]),
     "ldpc_set_weights": (ctypes.c_int, [P, I32, P, P]),
@@ -150,14 +150,15 @@ def ldpc_set_variant(h, variant):
     return load().ldpc_set_variant(h, variant)
 
 
-def ldpc_set_tuning(h, frames_per_tile, threads):
-    return load().ldpc_set_tuning(h, frames_per_tile, threads)
+def ldpc_set_tuning(h, frames_per_tile, threads, index_placement=0):
+    return load().ldpc_set_tuning(h, frames_per_tile, threads, index_placement)
 
 
 def ldpc_get_tuning(h):
-    a, b = ctypes.c_int32(), ctypes.c_int32()
-    _check(load().ldpc_get_tuning(h, ctypes.byref(a), ctypes.byref(b)), "ldpc_get_tuning")
-    return a.value, b.value
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().ldpc_get_tuning(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "ldpc_get_tuning")
+    return a.value, b.value, c.value
 
 
 def ldpc_autotune(h, frames, max_iter):
@@ -298,8 +299,9 @@ class Decoder:
              "resident": LDPC_VARIANT_RESIDENT}[variant]
         _check(load().ldpc_set_variant(self.h, v), "ldpc_set_variant")
 
-    def set_tuning(self, frames_per_tile=0, threads=0):
-        _check(load().ldpc_set_tuning(self.h, frames_per_tile, threads), "ldpc_set_tuning")
+    def set_tuning(self, frames_per_tile=0, threads=0, index_placement=0):
+        _check(load().ldpc_set_tuning(self.h, frames_per_tile, threads, index_placement),
+               "ldpc_set_tuning")
 
     def tuning(self):
         return ldpc_get_tuning(self.h)

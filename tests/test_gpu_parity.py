@@ -219,19 +219,21 @@ def test_every_resident_launch_shape(torch_cuda, mode):
     tried = 0
     for ft in (1, 2, 4):
         for th in (0, 96, 256, 640, 1024):
-            dec = Decoder.from_code(code, mode=mode)
-            dec.set_variant("resident")
-            try:
-                dec.set_tuning(ft, th)
-            except LdpcError:
-                continue
-            b, it, ok, sf = dec.decode(x, 8, want_ok=True, want_soft=True)
-            torch.cuda.synchronize()
-            got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
-            assert_parity(got, want, mode, f"FT={ft} threads={th}")
-            tried += 1
-            dec.close()
-    assert tried >= 8
+            for ip in (1, 2):
+                dec = Decoder.from_code(code, mode=mode)
+                dec.set_variant("resident")
+                try:
+                    dec.set_tuning(ft, th, ip)
+                except LdpcError:
+                    continue
+                assert dec.tuning()[2] == ip
+                b, it, ok, sf = dec.decode(x, 8, want_ok=True, want_soft=True)
+                torch.cuda.synchronize()
+                got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
+                assert_parity(got, want, mode, f"FT={ft} threads={th} index={ip}")
+                tried += 1
+                dec.close()
+    assert tried >= 12
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -242,8 +244,8 @@ def test_autotune_keeps_results(torch_cuda, mode):
     llr = inputs.all_zero_awgn_llr(500, code.N, 2.0, code.design_rate, 91)
     dec = Decoder.from_code(code, mode=mode)
     ms = dec.autotune(4096, 10)
-    ft, th = dec.tuning()
-    assert ms > 0 and ft in (1, 2, 4) and th % 32 == 0 and 64 <= th <= 1024
+    ft, th, ip = dec.tuning()
+    assert ms > 0 and ft in (1, 2, 4) and th % 32 == 0 and 64 <= th <= 1024 and ip in (1, 2)
     b, it, ok, sf = dec.decode(torch.from_numpy(llr).cuda(), 20, want_ok=True, want_soft=True)
     torch.cuda.synchronize()
     got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
