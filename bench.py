@@ -253,6 +253,59 @@ def learned_vs_plain(timed):
             "fer_table": rows}
 
 
+# ------------------------------------------------------------------ mixed codes, one launch
+
+def mixed_codes(timed):
+    """Eight irregular codes (N 256..16200, rates 1/2..5/6, column weights {2,3,4,8}),
+    frames per code drawn from [64, 8192], all-zero codeword at Eb/N0 = 2.0 dB, FP32, at
+    most 25 iterations with early stop: decoded as one persistent launch replayed from a
+    CUDA graph, and, for comparison, one decode call per code (each autotuned)."""
+    import torch
+    from paper_2507_10424_gb300 import inputs
+    from paper_2507_10424_gb300.ldpc import Batch, Decoder
+    codes, frames = inputs.cfg_mixed_codes()
+    L = 25
+    decs = [Decoder.from_code(c) for c in codes]
+    batch = Batch(decs)
+    xs = []
+    for k, (c, F) in enumerate(zip(codes, frames)):
+        x = torch.from_numpy(inputs.all_zero_awgn_llr(F, c.N, 2.0, c.design_rate, 300 + k)).cuda()
+        xs.append(x)
+        batch.set_io(k, x)
+    threads, _ = batch.autotune(L)
+    batch.prepare(L)
+    batch.capture()
+    stream = batch.stream
+
+    def one_launch():
+        batch.replay()
+
+    ms_graph = timed(one_launch, 20, 3, st=stream)
+    bits_total = sum(c.N * F for c, F in zip(codes, frames))
+    outs = []
+    for d, c, F, x in zip(decs, codes, frames, xs):
+        if d.variant() == "resident":
+            d.autotune(F, L)
+        outs.append((torch.empty((F, c.N), dtype=torch.uint8, device="cuda"),
+                     torch.empty(F, dtype=torch.int32, device="cuda"), None, None))
+
+    def per_code():
+        for d, x, o in zip(decs, xs, outs):
+            d.decode(x, L, early_stop=True, out=o)
+
+    ms_seq = timed(per_code, 20, 3)
+    same = all(bool((batch._keep[k][1] == outs[k][0]).all()) for k in range(len(codes)))
+    info = batch.info()
+    batch.close()
+    return {"codes": [{"N": c.N, "M": c.M, "E": c.E, "frames": F} for c, F in zip(codes, frames)],
+            "max_iter": L, "ebn0_db": 2.0, "frames_total": int(sum(frames)),
+            "one_launch_graph": {"ms": ms_graph, "Gbit/s": bits_total / (ms_graph * 1e-3) / 1e9,
+                                 "threads": threads, "codes_in_shared_memory": info["codes_in_shared_memory"]},
+            "per_code_calls": {"ms": ms_seq, "Gbit/s": bits_total / (ms_seq * 1e-3) / 1e9,
+                               "launches": sum(d.last_kernel_count() for d in decs)},
+            "identical_bits": same}
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args):
@@ -345,7 +398,10 @@ def main():
     def step():
         dec.decode(x, L, early_stop=False, out=out)
 
-    def timed(fn, K, W, sampler=None):
+    def timed(fn, K, W, sampler=None, st=None):
+        """Mean ms per call of fn over K calls after W warm-up calls, CUDA events on the
+        stream the work is launched on (st, else the current stream)."""
+        st = st or stream
         for _ in range(W):
             fn()
         torch.cuda.synchronize()
@@ -354,10 +410,10 @@ def main():
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if sampler:
             sampler.mark("t0")
-        e0.record(stream)
+        e0.record(st)
         for _ in range(K):
             fn()
-        e1.record(stream)
+        e1.record(st)
         torch.cuda.synchronize()
         if sampler:
             sampler.mark("t1")
@@ -444,6 +500,7 @@ def main():
         result["other_paths"] = others
         if rank == 0:
             result["learned"] = learned_vs_plain(timed)
+            result["mixed_codes"] = mixed_codes(timed)
         if world == 1 and rank == 0:
             val, n, dt = oracle_rate(code, llr, L, mode)
             result["cpu_baseline"] = {"value": val, "unit": "Gbit/s", "cores": cpu_threads(),

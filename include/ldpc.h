@@ -198,6 +198,59 @@ int ldpc_train_backward(ldpc_t *h, int32_t frames, int32_t iters, const float *a
                         const float *beta, const float *grad_soft, int32_t soft_every,
                         float *grad_alpha, float *grad_beta, void *work, uint64_t work_bytes);
 
+/*
+ * Batched decoding of several codes of uneven size in ONE persistent launch (FP32 mode).
+ * The paper decodes one frame of one code at a time; this batches frames of many codes.
+ * The batch refers to existing handles (which must outlive it; all on the current
+ * device, all with or all without LDPC_FLAG_PAPER_SLICER, each small enough for the
+ * resident variant's sliced layout). Its kernel takes (code, frame) tiles from one work
+ * counter, largest codes first; a code whose frame fits in shared memory keeps its
+ * messages there, a larger one uses a per-CTA slot of the batch's global scratch.
+ * Results equal ldpc_decode_ex with check_every = 1 on each code.
+ *
+ * ldpc_batch_create: NULL on failure (bad handle, mixed slicers, device mismatch, OOM).
+ */
+typedef struct ldpc_batch ldpc_batch_t;
+ldpc_batch_t *ldpc_batch_create(int32_t n_codes, ldpc_t *const *codes);
+
+/* ldpc_batch_set_stream: stream of the batch's launches (a non-default stream is needed
+ * for ldpc_batch_capture). */
+int ldpc_batch_set_stream(ldpc_batch_t *b, void *cuda_stream);
+
+/* ldpc_batch_set_io: device buffers of code `code` for the next prepare: llr [frames][N],
+ * out_bits [frames][N], out_iters [frames], out_ok / out_soft nullable. frames may be 0. */
+int ldpc_batch_set_io(ldpc_batch_t *b, int32_t code, const float *llr, int32_t frames,
+                      uint8_t *out_bits, int32_t *out_iters, uint8_t *out_ok, float *out_soft);
+
+/* ldpc_batch_prepare: upload the per-code descriptors and the tile list for max_iter and
+ * early_stop (synchronous; waits for the batch's stream). */
+int ldpc_batch_prepare(ldpc_batch_t *b, int32_t max_iter, int32_t early_stop);
+
+/* ldpc_batch_launch: enqueue the prepared decode (a counter reset and one kernel). */
+int ldpc_batch_launch(ldpc_batch_t *b);
+
+/* ldpc_batch_decode: ldpc_batch_prepare then ldpc_batch_launch. */
+int ldpc_batch_decode(ldpc_batch_t *b, int32_t max_iter, int32_t early_stop);
+
+/* ldpc_batch_capture: record the prepared launch in a CUDA graph (on the batch's stream);
+ * ldpc_batch_replay launches that graph. Prepare and capture again after changing the
+ * buffers, the iteration limit or the CTA size. */
+int ldpc_batch_capture(ldpc_batch_t *b);
+int ldpc_batch_replay(ldpc_batch_t *b);
+
+/* ldpc_batch_set_threads / ldpc_batch_autotune: CTA size of the batch kernel, given or
+ * chosen by timing the prepared decode (prepares it for max_iter / early_stop first). */
+int ldpc_batch_set_threads(ldpc_batch_t *b, int32_t threads);
+int ldpc_batch_autotune(ldpc_batch_t *b, int32_t max_iter, int32_t early_stop,
+                        int32_t *best_threads, float *best_ms);
+
+/* ldpc_batch_info: codes, prepared tiles, CTA size, codes kept in shared memory. */
+int ldpc_batch_info(const ldpc_batch_t *b, int32_t *n_codes, int32_t *n_tiles, int32_t *threads,
+                    int32_t *codes_in_shared_memory);
+
+/* ldpc_batch_destroy: waits for the batch's stream, frees it (not the handles). */
+void ldpc_batch_destroy(ldpc_batch_t *b);
+
 /* ldpc_set_stream: decode on this cudaStream_t (NULL = legacy default stream). */
 int ldpc_set_stream(ldpc_t *h, void *cuda_stream);
 

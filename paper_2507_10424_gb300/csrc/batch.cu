@@ -1,0 +1,402 @@
+// Batched decoding of several codes of uneven size in one persistent launch.
+//
+// One kernel decodes the frames of every code in the batch: its CTAs take tiles (code,
+// frame) from a single atomic work counter, largest codes first, and run every flooding
+// iteration of the tile with the resident variant's tile body (decode_tile). A code whose
+// frame fits the launch's shared memory keeps eta, s and r there; a larger one keeps them
+// in the CTA's own slot of a global scratch buffer (which stays in L2 at these sizes).
+// The index arrays of every code are read from global memory. FP32 mode.
+//
+// The launch (a memset of the work counter and the kernel) touches only buffers fixed when
+// the batch's inputs and outputs are set, so it can be recorded once in a CUDA graph and
+// replayed (ldpc_batch_capture / ldpc_batch_replay).
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "resident.cuh"
+
+namespace ldpc_impl {
+namespace resident {
+namespace {
+
+struct CodeDesc {
+    ResArgs a;        // graph, sizes, inputs and outputs of this code for the call
+    int32_t in_smem;  // eta, s, r of a tile in shared memory (else in the CTA's scratch slot)
+    int32_t ft;       // frames interleaved per tile: 1, 2 or 4
+};
+
+struct Tile {
+    int32_t code, f0;
+};
+
+// The tile body for FT interleaved frames at `base` (shared memory or a scratch slot).
+template <int FT, bool PAPER>
+__device__ __forceinline__ void multi_tile(const ResArgs& a, const Idx& ix, char* base,
+                                           uint32_t* unsat_w, int f0) {
+    using VT = VecR<float, FT>;
+    VT* eta = reinterpret_cast<VT*>(base);
+    VT* s = eta + a.E_pad;
+    VT* r = s + a.n_csl * 32;
+    decode_tile<kModeFP32, FT, PAPER, false>(a, ix, eta, s, r, unsat_w, f0, min(FT, a.frames - f0),
+                                             nullptr, nullptr, a.n_rsl * 32);
+}
+
+template <bool PAPER>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_multi(const CodeDesc* codes, const Tile* tiles,
+                                                          int n_tiles, int32_t* counter,
+                                                          char* scratch, size_t slot_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t unsat_w[2];
+    __shared__ int tile_sh;
+    __shared__ CodeDesc cd;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            tile_sh = atomicAdd(counter, 1);
+            unsat_w[0] = 0;
+            unsat_w[1] = 0;
+        }
+        __syncthreads();
+        const int t = tile_sh;
+        if (t >= n_tiles) break;
+        const Tile tl = tiles[t];
+        if (threadIdx.x == 0) cd = codes[tl.code];
+        __syncthreads();
+        const ResArgs& a = cd.a;
+        const Idx ix{a.r_base, a.r_deg, a.r_slot_pos, a.c_base, a.c_deg, a.c_slot, a.col_pos,
+                     nullptr, nullptr, nullptr};
+        if (cd.in_smem) {
+            char* base = reinterpret_cast<char*>(smem_raw);
+            if (cd.ft == 4) multi_tile<4, PAPER>(a, ix, base, unsat_w, tl.f0);
+            else if (cd.ft == 2) multi_tile<2, PAPER>(a, ix, base, unsat_w, tl.f0);
+            else multi_tile<1, PAPER>(a, ix, base, unsat_w, tl.f0);
+        } else {
+            char* base = scratch + (size_t)blockIdx.x * slot_bytes;
+            if (cd.ft == 2) multi_tile<2, PAPER>(a, ix, base, unsat_w, tl.f0);
+            else multi_tile<1, PAPER>(a, ix, base, unsat_w, tl.f0);
+        }
+        __syncthreads();
+    }
+}
+
+size_t frame_bytes(const DevGraph& g) { return ((size_t)g.E_pad + 2 * (size_t)g.n_cslices * 32) * 4; }
+
+}  // namespace
+}  // namespace resident
+}  // namespace ldpc_impl
+
+using namespace ldpc_impl;
+using namespace ldpc_impl::resident;
+
+struct ldpc_batch {
+    int device = 0, num_sms = 0;
+    std::vector<ldpc_t*> codes;
+    std::vector<HandleView> views;
+    std::vector<CodeDesc> desc;  // host copies
+    std::vector<int32_t> frames;
+    int paper = 0;
+    CodeDesc* d_desc = nullptr;
+    Tile* d_tiles = nullptr;
+    int32_t n_tiles = 0, tiles_cap = 0;
+    int32_t* d_counter = nullptr;
+    char* d_scratch = nullptr;
+    size_t slot_bytes = 0, smem = 0;
+    int threads = 512, grid = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t last_launches = 0;
+};
+
+static void batch_free(ldpc_batch_t* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_counter) cudaFree(b->d_counter);
+    if (b->d_scratch) cudaFree(b->d_scratch);
+    delete b;
+}
+
+static int batch_occupancy(ldpc_batch_t* b, int threads, int* grid) {
+    auto kern = b->paper ? k_multi<true> : k_multi<false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, b->smem) != cudaSuccess ||
+        per_sm < 1)
+        return LDPC_ERR_UNSUPPORTED;
+    *grid = b->num_sms * per_sm;
+    return LDPC_OK;
+}
+
+// Enqueue the launch (capturable): reset the work counter, run the kernel.
+static int batch_enqueue(ldpc_batch_t* b) {
+    if (cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), b->stream) != cudaSuccess) return LDPC_ERR_CUDA;
+    if (b->n_tiles == 0) return LDPC_OK;
+    const int grid = std::min(b->grid, b->n_tiles);
+    if (b->paper)
+        k_multi<true><<<grid, b->threads, b->smem, b->stream>>>(b->d_desc, b->d_tiles, b->n_tiles,
+                                                                b->d_counter, b->d_scratch, b->slot_bytes);
+    else
+        k_multi<false><<<grid, b->threads, b->smem, b->stream>>>(b->d_desc, b->d_tiles, b->n_tiles,
+                                                                 b->d_counter, b->d_scratch, b->slot_bytes);
+    return cudaGetLastError() == cudaSuccess ? LDPC_OK : LDPC_ERR_CUDA;
+}
+
+extern "C" {
+
+ldpc_batch_t* ldpc_batch_create(int32_t n_codes, ldpc_t* const* codes) {
+    if (n_codes <= 0 || n_codes > 4096 || !codes) return nullptr;
+    ldpc_batch_t* b = new (std::nothrow) ldpc_batch();
+    if (!b) return nullptr;
+    int optin = 0;
+    if (cudaGetDevice(&b->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return nullptr;
+    }
+    const size_t budget = (size_t)std::max(0, optin - 1024);
+    size_t slot = 0;
+    constexpr int kScratchFT = 2;  // frames per tile of the codes kept in global scratch
+    for (int32_t c = 0; c < n_codes; c++) {
+        HandleView v;
+        if (handle_view(codes[c], &v) != LDPC_OK || !v.dg->sliced || v.device != b->device) {
+            delete b;
+            return nullptr;
+        }
+        if (c == 0) b->paper = (v.flags & LDPC_FLAG_PAPER_SLICER) ? 1 : 0;
+        if (b->paper != ((v.flags & LDPC_FLAG_PAPER_SLICER) ? 1 : 0)) {  // one slicer per batch
+            delete b;
+            return nullptr;
+        }
+        b->codes.push_back(codes[c]);
+        b->views.push_back(v);
+        const size_t fb = frame_bytes(*v.dg);
+        CodeDesc d{};
+        d.in_smem = fb <= budget;
+        d.ft = 1;
+        if (d.in_smem) {
+            d.ft = 4 * fb <= budget ? 4 : (2 * fb <= budget ? 2 : 1);
+            b->smem = std::max(b->smem, (size_t)d.ft * fb);
+        } else {
+            d.ft = kScratchFT;
+            slot = std::max(slot, (size_t)kScratchFT * fb);
+        }
+        b->desc.push_back(d);
+        b->frames.push_back(0);
+    }
+    b->slot_bytes = (slot + 255) & ~(size_t)255;
+    cudaError_t e = cudaMalloc((void**)&b->d_desc, sizeof(CodeDesc) * n_codes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int32_t));
+    if (e == cudaSuccess && batch_occupancy(b, b->threads, &b->grid) != LDPC_OK) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess && b->slot_bytes) e = cudaMalloc((void**)&b->d_scratch, b->slot_bytes * b->grid);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        return nullptr;
+    }
+    return b;
+}
+
+int ldpc_batch_set_stream(ldpc_batch_t* b, void* stream) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    b->stream = (cudaStream_t)stream;
+    return LDPC_OK;
+}
+
+int ldpc_batch_set_io(ldpc_batch_t* b, int32_t code, const float* llr, int32_t frames,
+                      uint8_t* out_bits, int32_t* out_iters, uint8_t* out_ok, float* out_soft) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    if (code < 0 || code >= (int32_t)b->codes.size() || frames < 0) return LDPC_ERR_INVALID_ARG;
+    if (frames > 0 && (!llr || !out_bits || !out_iters)) return LDPC_ERR_BAD_POINTER;
+    const HandleView& v = b->views[code];
+    const DevGraph& g = *v.dg;
+    ResArgs& a = b->desc[code].a;
+    a = ResArgs{};
+    a.r_base = g.r_base;
+    a.r_deg = g.r_deg;
+    a.r_slot_pos = g.r_slot_pos;
+    a.c_base = g.c_base;
+    a.c_deg = g.c_deg;
+    a.c_slot = g.c_slot;
+    a.col_pos = g.col_pos;
+    a.r_slot_cls = g.r_slot_cls;
+    a.n_rsl = g.n_rslices;
+    a.n_csl = g.n_cslices;
+    a.E_pad = g.E_pad;
+    a.Ec_pad = g.Ec_pad;
+    a.N = v.N;
+    a.llr = llr;
+    a.frames = frames;
+    a.paper = b->paper;
+    a.out_bits = out_bits;
+    a.out_iters = out_iters;
+    a.out_ok = out_ok;
+    a.out_soft = out_soft;
+    b->frames[code] = frames;
+    return LDPC_OK;
+}
+
+// Upload the descriptors and the tile list for max_iter / early_stop (synchronous).
+int ldpc_batch_prepare(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    if (max_iter < 0) return LDPC_ERR_INVALID_ARG;
+    std::vector<int32_t> order(b->codes.size());
+    for (size_t c = 0; c < order.size(); c++) {
+        order[c] = (int32_t)c;
+        ResArgs& a = b->desc[c].a;
+        a.L = max_iter;
+        a.early_stop = early_stop ? 1 : 0;
+        a.check_every = 1;
+    }
+    // largest frames first: the last tiles to start are the short ones
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return b->views[x].E > b->views[y].E;
+    });
+    std::vector<Tile> tiles;
+    for (int32_t c : order)
+        for (int32_t f = 0; f < b->frames[c]; f += b->desc[c].ft) tiles.push_back(Tile{c, f});
+    if ((int32_t)tiles.size() > b->tiles_cap) {
+        if (b->d_tiles) cudaFree(b->d_tiles);
+        b->d_tiles = nullptr;
+        if (cudaMalloc((void**)&b->d_tiles, sizeof(Tile) * tiles.size()) != cudaSuccess) {
+            cudaGetLastError();
+            b->tiles_cap = 0;
+            return LDPC_ERR_OOM;
+        }
+        b->tiles_cap = (int32_t)tiles.size();
+    }
+    b->n_tiles = (int32_t)tiles.size();
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
+        cudaMemcpy(b->d_desc, b->desc.data(), sizeof(CodeDesc) * b->desc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (b->n_tiles && cudaMemcpy(b->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+        return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+
+int ldpc_batch_launch(ldpc_batch_t* b) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    const int rc = batch_enqueue(b);
+    b->last_launches = b->n_tiles ? 1 : 0;
+    return rc;
+}
+
+int ldpc_batch_decode(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
+    const int rc = ldpc_batch_prepare(b, max_iter, early_stop);
+    return rc != LDPC_OK ? rc : ldpc_batch_launch(b);
+}
+
+int ldpc_batch_capture(ldpc_batch_t* b) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    if (!b->stream) return LDPC_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LDPC_ERR_CUDA;
+    const int rc = batch_enqueue(b);
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (rc != LDPC_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return LDPC_ERR_CUDA;
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        b->exec = nullptr;
+        cudaGetLastError();
+        return LDPC_ERR_CUDA;
+    }
+    return LDPC_OK;
+}
+
+int ldpc_batch_replay(ldpc_batch_t* b) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    if (!b->exec) return LDPC_ERR_INVALID_ARG;
+    b->last_launches = b->n_tiles ? 1 : 0;
+    return cudaGraphLaunch(b->exec, b->stream) == cudaSuccess ? LDPC_OK : LDPC_ERR_CUDA;
+}
+
+int ldpc_batch_set_threads(ldpc_batch_t* b, int32_t threads) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    if (threads < 64 || threads > kMaxThreads || threads % 32) return LDPC_ERR_INVALID_ARG;
+    int grid = 0;
+    const int rc = batch_occupancy(b, threads, &grid);
+    if (rc != LDPC_OK) return rc;
+    if (grid > b->grid && b->slot_bytes) {  // more CTAs need more scratch slots
+        char* p = nullptr;
+        if (cudaMalloc((void**)&p, b->slot_bytes * grid) != cudaSuccess) {
+            cudaGetLastError();
+            return LDPC_ERR_OOM;
+        }
+        cudaStreamSynchronize(b->stream);
+        cudaFree(b->d_scratch);
+        b->d_scratch = p;
+    }
+    b->threads = threads;
+    b->grid = grid;
+    if (b->exec) {  // a recorded launch keeps its old shape: record again
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    return LDPC_OK;
+}
+
+int ldpc_batch_autotune(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop, int32_t* best_threads,
+                        float* best_ms) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    int rc = ldpc_batch_prepare(b, max_iter, early_stop);
+    if (rc != LDPC_OK) return rc;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LDPC_ERR_CUDA;
+    float best = -1.0f;
+    int best_t = b->threads;
+    for (int th = 256; th <= kMaxThreads; th += 128) {
+        if (ldpc_batch_set_threads(b, th) != LDPC_OK) continue;
+        float ms = 0.0f;
+        bool bad = batch_enqueue(b) != LDPC_OK || cudaEventRecord(e0, b->stream) != cudaSuccess;
+        for (int r = 0; r < 2 && !bad; r++) bad = batch_enqueue(b) != LDPC_OK;
+        bad = bad || cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess;
+        if (bad) {
+            cudaGetLastError();
+            continue;
+        }
+        if (best < 0.0f || ms < best) {
+            best = ms;
+            best_t = th;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best < 0.0f) return LDPC_ERR_UNSUPPORTED;
+    rc = ldpc_batch_set_threads(b, best_t);
+    if (best_threads) *best_threads = best_t;
+    if (best_ms) *best_ms = best / 2.0f;
+    return rc;
+}
+
+int ldpc_batch_info(const ldpc_batch_t* b, int32_t* n_codes, int32_t* n_tiles, int32_t* threads,
+                    int32_t* codes_in_shared_memory) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    if (n_codes) *n_codes = (int32_t)b->codes.size();
+    if (n_tiles) *n_tiles = b->n_tiles;
+    if (threads) *threads = b->threads;
+    if (codes_in_shared_memory) {
+        int32_t n = 0;
+        for (const auto& d : b->desc) n += d.in_smem;
+        *codes_in_shared_memory = n;
+    }
+    return LDPC_OK;
+}
+
+void ldpc_batch_destroy(ldpc_batch_t* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+}
+
+}  // extern "C"

@@ -346,6 +346,59 @@ __device__ __forceinline__ void copy_to_smem(T* dst, const T* src, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
+// Every iteration of one tile of nf frames (frames fbase .. fbase + nf - 1 of a.llr) with
+// eta, s and r at the given addresses (shared memory, or a CTA's slot of global scratch),
+// ending with the decisions of every frame written out. unsat_w: two words reset to 0.
+template <int MODE, int FT, bool PAPER, bool W, typename VT>
+__device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, VT* s, VT* r,
+                                            uint32_t* unsat_w, int fbase, int nf,
+                                            const float* walpha0, const float* wbeta0,
+                                            int n_rtasks) {
+    using T = typename RT<MODE>::T;
+    const int N = a.N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        VT v;
+#pragma unroll
+        for (int f = 0; f < FT; f++)  // "+ 0" turns -0.0 into +0.0 and changes no other value
+            v.x[f] = f < nf ? (T)(chan<MODE>(a, (size_t)(fbase + f) * N + j) + 0) : T(0);
+        const int p = ix.col_pos[j];
+        s[p] = v;
+        r[p] = v;
+    }
+    uint32_t active = (1u << nf) - 1u;
+    __syncthreads();
+
+    for (int k = 0;; k++) {
+        const int par = k & 1;
+        const bool last = (k == a.L);
+        const bool syn = last || (a.early_stop && (k % a.check_every == 0));
+        uint32_t* uw = &unsat_w[par];
+        if (W) {  // weights of iteration k + 1 (the last row serves the later iterations)
+            const int row = min(k + 1, a.w_rows) - 1;
+            ix.walpha = walpha0 + row * a.n_classes;
+            ix.wbeta = wbeta0 + row * a.n_classes;
+        }
+        phase_a_any<MODE, FT, PAPER, W>(k == 0, syn, !last, ix, eta, s, n_rtasks, uw);
+        __syncthreads();
+        if (syn) {
+            const uint32_t conv = active & ~unsat_w[par];
+            if (last) {
+                emit<MODE, FT>(a, ix, s, fbase, active, a.L, conv);
+                break;
+            }
+            if (conv) {
+                emit<MODE, FT>(a, ix, s, fbase, conv, k, conv);
+                active &= ~conv;
+                if (!active) break;
+                __syncthreads();  // the emitted posteriors are read before phase B rewrites them
+            }
+        }
+        phase_b<MODE, FT>(ix, eta, s, r, N);
+        if (threadIdx.x == 0) unsat_w[par ^ 1] = 0;
+        __syncthreads();
+    }
+}
+
 template <int MODE, int FT, bool IDX_SMEM, bool PAPER, bool W>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
     using T = typename RT<MODE>::T;
@@ -404,48 +457,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
         const int tile = tile_sh;
         if (tile >= a.n_tiles) break;
         const int fbase = tile * FT;
-        const int nf = min(FT, a.frames - fbase);
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            VT v;
-#pragma unroll
-            for (int f = 0; f < FT; f++)  // "+ 0" turns -0.0 into +0.0 and changes no other value
-                v.x[f] = f < nf ? (T)(chan<MODE>(a, (size_t)(fbase + f) * N + j) + 0) : T(0);
-            const int p = ix.col_pos[j];
-            s[p] = v;
-            r[p] = v;
-        }
-        uint32_t active = (1u << nf) - 1u;
-        __syncthreads();
-
-        for (int k = 0;; k++) {
-            const int par = k & 1;
-            const bool last = (k == a.L);
-            const bool syn = last || (a.early_stop && (k % a.check_every == 0));
-            uint32_t* uw = &unsat_w[par];
-            if (W) {  // weights of iteration k + 1 (the last row serves the later iterations)
-                const int row = min(k + 1, a.w_rows) - 1;
-                ix.walpha = walpha0 + row * a.n_classes;
-                ix.wbeta = wbeta0 + row * a.n_classes;
-            }
-            phase_a_any<MODE, FT, PAPER, W>(k == 0, syn, !last, ix, eta, s, n_rtasks, uw);
-            __syncthreads();
-            if (syn) {
-                const uint32_t conv = active & ~unsat_w[par];
-                if (last) {
-                    emit<MODE, FT>(a, ix, s, fbase, active, a.L, conv);
-                    break;
-                }
-                if (conv) {
-                    emit<MODE, FT>(a, ix, s, fbase, conv, k, conv);
-                    active &= ~conv;
-                    if (!active) break;
-                    __syncthreads();  // the emitted posteriors are read before phase B rewrites them
-                }
-            }
-            phase_b<MODE, FT>(ix, eta, s, r, N);
-            if (threadIdx.x == 0) unsat_w[par ^ 1] = 0;
-            __syncthreads();
-        }
+        decode_tile<MODE, FT, PAPER, W>(a, ix, eta, s, r, unsat_w, fbase, min(FT, a.frames - fbase),
+                                        walpha0, wbeta0, n_rtasks);
         __syncthreads();
     }
 }

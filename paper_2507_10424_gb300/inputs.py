@@ -281,3 +281,21 @@ def cfg_qc_2304(seed: int = 2) -> Code:
 def cfg_irregular_64800(seed: int = 5) -> Code:
     """Irregular N=64800, M=32400, column weights {2,3,8} at 0.5/0.375/0.125."""
     return irregular_code(64800, 32400, [2, 3, 8], [0.5, 0.375, 0.125], seed)
+
+
+MIXED_N = (256, 512, 1024, 2048, 4096, 8192, 12288, 16200)
+MIXED_RATES = (1 / 2, 2 / 3, 3 / 4, 5 / 6)
+
+
+def cfg_mixed_codes(seed: int = 3):
+    """Eight irregular codes: column weights {2,3,4,8} at 0.3/0.4/0.2/0.1, N from MIXED_N,
+    rate of code k = MIXED_RATES[k % 4], M = round(N (1 - rate)); frames per code drawn
+    uniformly from [64, 8192]. Returns (codes, frames)."""
+    rng = np.random.default_rng(seed)
+    codes, frames = [], []
+    for k, N in enumerate(MIXED_N):
+        R = MIXED_RATES[k % 4]
+        M = int(round(N * (1 - R)))
+        codes.append(irregular_code(N, M, [2, 3, 4, 8], [0.3, 0.4, 0.2, 0.1], seed * 100 + k))
+        frames.append(int(rng.integers(64, 8193)))
+    return codes, frames

@@ -46,6 +46,18 @@ SIGNATURES = {
     "ldpc_decode_ex": (ctypes.c_int, [P, P, I32, I32, I32, I32, I32, P, P, P, P]),
     "ldpc_decode_host": (ctypes.c_int, [P, P, I32, I32, I32, I32, I32, P, P, P, P]),
     "ldpc_decode_noalloc": (ctypes.c_int, [P, P, I32, I32, I32, I32, I32, P, P, P, P]),
+    "ldpc_batch_create": (P, [I32, P]),
+    "ldpc_batch_set_stream": (ctypes.c_int, [P, P]),
+    "ldpc_batch_set_io": (ctypes.c_int, [P, I32, P, I32, P, P, P, P]),
+    "ldpc_batch_prepare": (ctypes.c_int, [P, I32, I32]),
+    "ldpc_batch_launch": (ctypes.c_int, [P]),
+    "ldpc_batch_decode": (ctypes.c_int, [P, I32, I32]),
+    "ldpc_batch_capture": (ctypes.c_int, [P]),
+    "ldpc_batch_replay": (ctypes.c_int, [P]),
+    "ldpc_batch_set_threads": (ctypes.c_int, [P, I32]),
+    "ldpc_batch_autotune": (ctypes.c_int, [P, I32, I32, PI32, ctypes.POINTER(ctypes.c_float)]),
+    "ldpc_batch_info": (ctypes.c_int, [P, PI32, PI32, PI32, PI32]),
+    "ldpc_batch_destroy": (None, [P]),
     "ldpc_set_stream": (ctypes.c_int, [P, P]),
     "ldpc_set_mode": (ctypes.c_int, [P, I32]),
     "ldpc_set_variant": (ctypes.c_int, [P, I32]),
@@ -401,3 +413,75 @@ class Decoder:
                                   ctypes.c_void_p(soft.data_ptr()) if soft is not None else None)
         _check(st, "ldpc_decode_host")
         return bits, iters, ok, soft
+
+
+class Batch:
+    """Several codes decoded in one persistent launch (and, once captured, one CUDA graph).
+
+    ``decoders``: :class:`Decoder` objects (kept alive by the batch). Buffers are torch CUDA
+    tensors given per code with :meth:`set_io`.
+    """
+
+    def __init__(self, decoders):
+        import torch
+        self.decoders = list(decoders)
+        arr = (ctypes.c_void_p * len(self.decoders))(*[d.h for d in self.decoders])
+        self._arr = arr
+        self.b = load().ldpc_batch_create(len(self.decoders), ctypes.cast(arr, ctypes.c_void_p))
+        if not self.b:
+            raise LdpcError(LDPC_ERR_INVALID_ARG, "ldpc_batch_create")
+        self.stream = torch.cuda.Stream()
+        _check(load().ldpc_batch_set_stream(self.b, ctypes.c_void_p(self.stream.cuda_stream)),
+               "ldpc_batch_set_stream")
+        self._keep = {}
+
+    def set_io(self, code, llr, want_ok=False, want_soft=False):
+        """Allocate the outputs of code `code` for the CUDA tensor `llr` [F][N]; returns them."""
+        import torch
+        F, N = llr.shape
+        bits = torch.empty((F, N), dtype=torch.uint8, device=llr.device)
+        iters = torch.empty(F, dtype=torch.int32, device=llr.device)
+        ok = torch.empty(F, dtype=torch.uint8, device=llr.device) if want_ok else None
+        soft = torch.empty((F, N), dtype=torch.float32, device=llr.device) if want_soft else None
+        P_ = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(load().ldpc_batch_set_io(self.b, code, P_(llr), F, P_(bits), P_(iters), P_(ok), P_(soft)),
+               "ldpc_batch_set_io")
+        self._keep[code] = (llr, bits, iters, ok, soft)
+        return bits, iters, ok, soft
+
+    def prepare(self, max_iter, early_stop=True):
+        _check(load().ldpc_batch_prepare(self.b, max_iter, int(early_stop)), "ldpc_batch_prepare")
+
+    def launch(self):
+        _check(load().ldpc_batch_launch(self.b), "ldpc_batch_launch")
+
+    def decode(self, max_iter, early_stop=True):
+        _check(load().ldpc_batch_decode(self.b, max_iter, int(early_stop)), "ldpc_batch_decode")
+
+    def capture(self):
+        _check(load().ldpc_batch_capture(self.b), "ldpc_batch_capture")
+
+    def replay(self):
+        _check(load().ldpc_batch_replay(self.b), "ldpc_batch_replay")
+
+    def autotune(self, max_iter, early_stop=True):
+        t, ms = ctypes.c_int32(), ctypes.c_float()
+        _check(load().ldpc_batch_autotune(self.b, max_iter, int(early_stop), ctypes.byref(t),
+                                          ctypes.byref(ms)), "ldpc_batch_autotune")
+        return t.value, ms.value
+
+    def info(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(load().ldpc_batch_info(self.b, *[ctypes.byref(x) for x in v]), "ldpc_batch_info")
+        return dict(zip(("n_codes", "n_tiles", "threads", "codes_in_shared_memory"), [x.value for x in v]))
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().ldpc_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
