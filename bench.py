@@ -497,6 +497,19 @@ def main():
                 "value": bits_total / (ms2 * 1e-3) / 1e9, "unit": "Gbit/s", "ms_per_step": ms2,
                 "hbm_edge_message_GBs": ach2, "frac": ach2 / peak}
             d2.close()
+        # the paper's dense m x n map-reduce form (Algorithm 2) as a baseline, on a slice of
+        # the batch (its workspace is 4 M N bytes per frame)
+        Fd = min(F, 2048)
+        dd = Decoder.from_code(code)
+        dd.set_variant("dense")
+        od = (torch.empty((Fd, code.N), dtype=torch.uint8, device="cuda"),
+              torch.empty(Fd, dtype=torch.int32, device="cuda"), None, None)
+        xd = x[:Fd].contiguous()
+        msd = timed(lambda: dd.decode(xd, L, early_stop=False, out=od), 3, 1)
+        others["fp32/dense_baseline"] = {"value": Fd * code.N * world / (msd * 1e-3) / 1e9,
+                                         "unit": "Gbit/s", "ms_per_step": msd, "frames": Fd,
+                                         "identical_bits": bool((od[0] == bits[:Fd]).all())}
+        dd.close()
         result["other_paths"] = others
         if rank == 0:
             result["learned"] = learned_vs_plain(timed)

@@ -71,6 +71,9 @@ typedef struct ldpc ldpc_t; /* opaque handle */
 #define LDPC_VARIANT_AUTO 0     /* resident when a frame fits in shared memory, else streaming */
 #define LDPC_VARIANT_STREAM 1   /* messages in HBM, frame-interleaved, two kernels per iteration */
 #define LDPC_VARIANT_RESIDENT 2 /* one persistent kernel, frames resident in shared memory */
+#define LDPC_VARIANT_DENSE 3    /* the paper's dense m x n map-reduce form (Algorithm 2): a
+                                   baseline; FP32 only, at most 65535 frames per call, and
+                                   4 M N bytes of workspace per frame */
 
 /*
  * ldpc_create: build a decoder for the M x N parity matrix H (host pointer, dense uint8,

@@ -70,6 +70,8 @@ struct ldpc {
     int32_t sw_cap = 0, sw_cap_L = -1;
     void* sw_big = nullptr;
     uint8_t* sw_unsat = nullptr;
+    void* dense_work = nullptr;  // dense variant workspace
+    size_t dense_cap = 0;
     int32_t* counters = nullptr;  // [0] resident tile counter, [1] streaming done count
     int32_t last_launches = 0;
     // host pipeline staging (2 slots)
@@ -162,6 +164,7 @@ static void replan(ldpc_t* h) {
 }
 
 static int resolved_variant(const ldpc_t* h) {
+    if (h->variant == LDPC_VARIANT_DENSE) return LDPC_VARIANT_DENSE;
     if (h->variant == LDPC_VARIANT_STREAM) return LDPC_VARIANT_STREAM;
     if (h->variant == LDPC_VARIANT_RESIDENT) return LDPC_VARIANT_RESIDENT;
     return h->plan[h->mode].ok ? LDPC_VARIANT_RESIDENT : LDPC_VARIANT_STREAM;
@@ -327,7 +330,26 @@ int ldpc_decode_ex(ldpc_t* h, const void* llr, int32_t llr_dtype, int32_t frames
         a.w_beta = h->w_alpha + (size_t)h->w_rows * h->dg.n_classes;
     }
     int n;
-    if (resolved_variant(h) == LDPC_VARIANT_RESIDENT) {
+    if (resolved_variant(h) == LDPC_VARIANT_DENSE) {
+        if (h->mode != kModeFP32 || a.w_rows > 0 || a.llr_is_i8) return fail(LDPC_ERR_UNSUPPORTED);
+        if (frames > 65535) return fail(LDPC_ERR_INVALID_ARG);
+        const size_t need = dense_bytes(h->M, h->N, frames);
+        if (need > h->dense_cap) {
+            if (h->dense_work) {
+                cudaStreamSynchronize(h->stream);
+                cudaFree(h->dense_work);
+                h->dense_work = nullptr;
+                h->dense_cap = 0;
+            }
+            cudaError_t e = cudaMalloc(&h->dense_work, need);
+            if (e != cudaSuccess) {
+                h->dense_work = nullptr;
+                return alloc_fail(e);
+            }
+            h->dense_cap = need;
+        }
+        n = dense_decode(h->dg, a, h->dense_work, h->stream);
+    } else if (resolved_variant(h) == LDPC_VARIANT_RESIDENT) {
         if (!h->plan[h->mode].ok) return fail(LDPC_ERR_UNSUPPORTED);
         n = resident_decode(h->mode, h->dg, h->plan[h->mode], a, h->counters, h->num_sms, h->stream);
     } else {
@@ -593,7 +615,7 @@ int ldpc_set_weights(ldpc_t* h, int32_t n_rows, const float* alpha, const float*
 
 int ldpc_set_variant(ldpc_t* h, int32_t variant) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
-    if (variant < LDPC_VARIANT_AUTO || variant > LDPC_VARIANT_RESIDENT) return fail(LDPC_ERR_INVALID_ARG);
+    if (variant < LDPC_VARIANT_AUTO || variant > LDPC_VARIANT_DENSE) return fail(LDPC_ERR_INVALID_ARG);
     if (variant == LDPC_VARIANT_RESIDENT && !h->plan[h->mode].ok) return fail(LDPC_ERR_UNSUPPORTED);
     h->variant = variant;
     return LDPC_OK;
@@ -664,6 +686,7 @@ void ldpc_destroy(ldpc_t* h) {
     free_graph(h->dg);
     if (h->counters) cudaFree(h->counters);
     if (h->w_alpha) cudaFree(h->w_alpha);
+    if (h->dense_work) cudaFree(h->dense_work);
     delete h;
 }
 

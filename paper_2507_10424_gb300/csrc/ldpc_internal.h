@@ -128,6 +128,10 @@ int stream_decode(int mode, const DevGraph& dg, const DecodeArgs& a, const Strea
                   cudaStream_t st);
 size_t stream_bytes(int mode, int32_t N, int64_t E, int32_t Fp, int32_t L);
 
+// Dense variant (the paper's m x n map-reduce form, a baseline): workspace bytes and launcher.
+size_t dense_bytes(int32_t M, int32_t N, int32_t frames);
+int dense_decode(const DevGraph& g, const DecodeArgs& a, void* work, cudaStream_t st);
+
 struct ResidentPlan {
     int ok = 0;           // the code fits
     int FT = 0;           // frames per tile (interleaved in shared memory)

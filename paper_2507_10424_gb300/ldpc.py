@@ -33,6 +33,7 @@ LDPC_FLAG_PAPER_SLICER = 1
 LDPC_VARIANT_AUTO = 0
 LDPC_VARIANT_STREAM = 1
 LDPC_VARIANT_RESIDENT = 2
+LDPC_VARIANT_DENSE = 3
 LDPC_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 # name -> (restype, argtypes), exactly the declarations of include/ldpc.h
@@ -308,7 +309,7 @@ class Decoder:
 
     def set_variant(self, variant: str):
         v = {"auto": LDPC_VARIANT_AUTO, "stream": LDPC_VARIANT_STREAM,
-             "resident": LDPC_VARIANT_RESIDENT}[variant]
+             "resident": LDPC_VARIANT_RESIDENT, "dense": LDPC_VARIANT_DENSE}[variant]
         _check(load().ldpc_set_variant(self.h, v), "ldpc_set_variant")
 
     def set_tuning(self, frames_per_tile=0, threads=0, index_placement=0):
@@ -341,7 +342,8 @@ class Decoder:
         return ldpc_autotune(self.h, frames, max_iter)
 
     def variant(self) -> str:
-        return {LDPC_VARIANT_STREAM: "stream", LDPC_VARIANT_RESIDENT: "resident"}[ldpc_get_variant(self.h)]
+        return {LDPC_VARIANT_STREAM: "stream", LDPC_VARIANT_RESIDENT: "resident",
+                LDPC_VARIANT_DENSE: "dense"}[ldpc_get_variant(self.h)]
 
     def set_mode(self, mode: str):
         _check(load().ldpc_set_mode(self.h, {"fp32": LDPC_MODE_FP32, "fixed": LDPC_MODE_FIXED}[mode]),

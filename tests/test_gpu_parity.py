@@ -277,6 +277,21 @@ def test_errors_on_device_arguments(torch_cuda):
         d2.set_variant("resident")
 
 
+@pytest.mark.parametrize("early_stop", [True, False])
+def test_dense_map_reduce_variant(torch_cuda, early_stop):
+    """The paper's dense m x n form (Algorithm 2) on the GPU: bit-exact with the oracle."""
+    for code, F, L in ((tanner_code(), 77, 9), (inputs.cfg_regular_576(), 64, 20),
+                       (inputs.qc_code(4, 8, 32, 0.7, 3), 33, 12)):
+        llr = inputs.all_zero_awgn_llr(F, code.N, 2.0, code.design_rate, 7) if code.N > 10 else \
+            (np.random.default_rng(3).standard_normal((F, 10)) * 1.5 + 0.5).astype(np.float32)
+        for ce in (1, 3):
+            got = gpu_decode(torch_cuda, code, llr, L, "fp32", "dense", early_stop=early_stop,
+                             check_every=ce)
+            assert got[4] == "dense"
+            assert_parity(got, oracle_decode(code, llr, L, "fp32", early_stop=early_stop,
+                                             check_every=ce), "fp32", f"dense N={code.N}")
+
+
 def test_workspace_too_large_is_an_error_not_a_crash(torch_cuda):
     """A streaming decode whose workspace cannot be allocated returns LDPC_ERR_OOM before
     anything is launched (the LLR buffer is never read), and the handle stays usable."""
