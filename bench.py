@@ -212,6 +212,39 @@ def oracle_rate(code, llr, L, mode, budget_s=10.0, threads=None):
     return n * code.N / dt / 1e9, n, dt
 
 
+# ------------------------------------------------------------------ the other workloads
+
+def other_workloads(timed):
+    """The configured workloads besides the headline: the (3,6)-regular N=576 code (1024
+    all-zero frames at 2.5 dB, 20 iterations, early stop) and the irregular N=64800 code
+    (4096 all-zero frames at 1.0 dB, 50 iterations, early stop; its frames do not fit in
+    shared memory, so it runs the streaming kernels), FP32 and fixed point."""
+    import torch
+    from paper_2507_10424_gb300 import inputs
+    from paper_2507_10424_gb300.ldpc import Decoder
+    out = {}
+    for name, code, F, e, L in (("regular576", inputs.cfg_regular_576(), 1024, 2.5, 20),
+                                ("irregular64800", inputs.cfg_irregular_64800(), 4096, 1.0, 50)):
+        llr = torch.from_numpy(inputs.all_zero_awgn_llr(F, code.N, e, code.design_rate, 17)).cuda()
+        for mode in ("fp32", "fixed"):
+            dec = Decoder.from_code(code, mode=mode)
+            if dec.variant() == "resident":
+                dec.autotune(F, L)
+            o = (torch.empty((F, code.N), dtype=torch.uint8, device="cuda"),
+                 torch.empty(F, dtype=torch.int32, device="cuda"), None, None)
+            ms = timed(lambda: dec.decode(llr, L, early_stop=True, out=o), 10, 3)
+            it = o[1].float()
+            B = edge_message_bytes(code, mode)
+            out[f"{name}/{mode}"] = {
+                "variant": dec.variant(), "frames": F, "ebn0_db": e, "max_iter": L,
+                "ms_per_call": ms, "Gbit/s": F * code.N / (ms * 1e-3) / 1e9,
+                "mean_iter": float(it.mean().item()),
+                "fer": float((o[0] != 0).any(dim=1).float().mean().item()),
+                "edge_message_GBs_at_mean_iter": F * float(it.mean().item()) * B / (ms * 1e-3) / 1e9}
+            dec.close()
+    return out
+
+
 # ------------------------------------------------------------------ learned decoder
 
 def learned_vs_plain(timed):
@@ -512,6 +545,7 @@ def main():
         dd.close()
         result["other_paths"] = others
         if rank == 0:
+            result["other_workloads"] = other_workloads(timed)
             result["learned"] = learned_vs_plain(timed)
             result["mixed_codes"] = mixed_codes(timed)
         if world == 1 and rank == 0:
