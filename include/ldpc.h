@@ -292,6 +292,15 @@ int ldpc_autotune(ldpc_t *h, int32_t frames, int32_t max_iter, float *best_ms);
 int ldpc_get_tuning(const ldpc_t *h, int32_t *frames_per_tile, int32_t *threads,
                     int32_t *index_placement);
 
+/* ldpc_set_stream_group: frame grouping of the streaming variant. The batch is decoded in
+ * groups of frames, one group after another, each through all its iterations, so that a
+ * group's messages can stay in L2. -1 (default): no groups; 0: groups sized so that a
+ * group's working set (about frames x (E m + N (m + r)) bytes) fits half the L2 cache, when
+ * the whole batch does not; > 0 (a multiple of 32): groups of this many frames. Results do
+ * not depend on the grouping; small groups leave the GPU partly idle, which is why it is
+ * off by default. Returns LDPC_ERR_INVALID_ARG for other values. */
+int ldpc_set_stream_group(ldpc_t *h, int32_t frames_per_group);
+
 /* ldpc_get_variant: the variant the next decode will run (AUTO resolved). */
 int ldpc_get_variant(const ldpc_t *h, int32_t *variant);
 

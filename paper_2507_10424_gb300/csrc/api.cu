@@ -72,6 +72,8 @@ struct ldpc {
     uint8_t* sw_unsat = nullptr;
     void* dense_work = nullptr;  // dense variant workspace
     size_t dense_cap = 0;
+    int32_t stream_group = -1;   // streaming: -1 no frame groups, 0 L2-sized groups, > 0 group size
+    int l2_bytes = 0;
     int32_t* counters = nullptr;  // [0] resident tile counter, [1] streaming done count
     int32_t last_launches = 0;
     // host pipeline staging (2 slots)
@@ -103,9 +105,9 @@ static void free_stream_work(ldpc_t* h) {
 // Largest batch of one streaming decode (its grids put frame blocks on the y dimension).
 constexpr int32_t kMaxStreamFrames = 65535 * 32;
 
-static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L) {
+static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L, int32_t granule = 256) {
     if (frames > kMaxStreamFrames) return fail(LDPC_ERR_INVALID_ARG);
-    const int32_t Fp = (frames + 255) & ~255;
+    const int32_t Fp = (frames + granule - 1) / granule * granule;
     if (Fp > h->sw_cap) {
         if (h->sw_big) {
             cudaStreamSynchronize(h->stream);
@@ -204,6 +206,8 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) return bail(cuda_fail(e));
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e));
+    e = cudaDeviceGetAttribute(&h->l2_bytes, cudaDevAttrL2CacheSize, h->device);
     if (e != cudaSuccess) return bail(cuda_fail(e));
     // CSR / CSC
     if ((rc = upload(&h->dg.row_ptr, hg.row_ptr.data(), hg.row_ptr.size())) ||
@@ -353,9 +357,39 @@ int ldpc_decode_ex(ldpc_t* h, const void* llr, int32_t llr_dtype, int32_t frames
         if (!h->plan[h->mode].ok) return fail(LDPC_ERR_UNSUPPORTED);
         n = resident_decode(h->mode, h->dg, h->plan[h->mode], a, h->counters, h->num_sms, h->stream);
     } else {
-        int rc = ensure_stream_work(h, frames, max_iter);
-        if (rc != LDPC_OK) return rc;
-        n = stream_decode(h->mode, h->dg, a, h->sw, h->stream);
+        // A batch whose streaming working set (messages, posteriors, channel values) would
+        // overflow L2 is decoded in frame groups that fit, one frame per lane, each group
+        // through all its iterations before the next: the messages then live in L2.
+        const size_t tb = h->mode == kModeFP32 ? 4 : 2, rb = h->mode == kModeFP32 ? 4 : 1;
+        const size_t per_frame = (size_t)h->E * tb + (size_t)h->N * (tb + rb);
+        const size_t budget = (size_t)h->l2_bytes / 2;
+        int32_t group = h->stream_group;
+        if (group == 0 && (size_t)frames * per_frame > budget && 32 * per_frame <= budget)
+            group = (int32_t)std::max<size_t>(32, budget / per_frame / 32 * 32);
+        if (group > 0 && group < frames) {
+            // frames per lane: the widest vector (up to 16 bytes) that the group fills
+            int vw = 1;
+            while (vw * 2 <= (h->mode == kModeFP32 ? 4 : 8) && group % (64 * vw) == 0) vw *= 2;
+            int rc = ensure_stream_work(h, group, max_iter, 32 * vw);
+            if (rc != LDPC_OK) return rc;
+            const size_t in_b = a.llr_is_i8 ? 1 : 4;
+            n = 0;
+            for (int32_t f0 = 0; f0 < frames && n >= 0; f0 += group) {
+                DecodeArgs ag = a;
+                ag.frames = std::min(group, frames - f0);
+                ag.llr = (const char*)llr + (size_t)f0 * h->N * in_b;
+                ag.out_bits = out_bits + (size_t)f0 * h->N;
+                ag.out_iters = out_iters + f0;
+                ag.out_ok = out_ok ? out_ok + f0 : nullptr;
+                ag.out_soft = out_soft ? out_soft + (size_t)f0 * h->N : nullptr;
+                const int k = stream_decode(h->mode, h->dg, ag, h->sw, h->stream, vw);
+                n = k < 0 ? k : n + k;
+            }
+        } else {
+            int rc = ensure_stream_work(h, frames, max_iter);
+            if (rc != LDPC_OK) return rc;
+            n = stream_decode(h->mode, h->dg, a, h->sw, h->stream);
+        }
     }
     if (n < 0) {
         cudaError_t e = cudaGetLastError();
@@ -610,6 +644,13 @@ int ldpc_set_weights(ldpc_t* h, int32_t n_rows, const float* alpha, const float*
     if (rc != LDPC_OK) return rc;
     h->w_rows = n_rows;
     replan(h);
+    return LDPC_OK;
+}
+
+int ldpc_set_stream_group(ldpc_t* h, int32_t frames_per_group) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (frames_per_group < -1 || (frames_per_group > 0 && frames_per_group % 32)) return fail(LDPC_ERR_INVALID_ARG);
+    h->stream_group = frames_per_group;
     return LDPC_OK;
 }
 

@@ -124,8 +124,10 @@ struct StreamWork {
 };
 
 // Launchers; return the number of kernels enqueued, or a negative status.
+// vw: frames per lane (0: a 16-byte vector, 4 fp32 / 8 int16; else 1, 2, 4 or 8 with the
+// frame stride w.Fp a multiple of 32 vw)
 int stream_decode(int mode, const DevGraph& dg, const DecodeArgs& a, const StreamWork& w,
-                  cudaStream_t st);
+                  cudaStream_t st, int vw = 0);
 size_t stream_bytes(int mode, int32_t N, int64_t E, int32_t Fp, int32_t L);
 
 // Dense variant (the paper's m x n map-reduce form, a baseline): workspace bytes and launcher.

@@ -118,7 +118,7 @@ struct IterWeights {
     const float* beta;
 };
 
-template <int MODE, bool FIRST, bool SYN_ONLY, bool W = false>
+template <int MODE, bool FIRST, bool SYN_ONLY, bool W = false, int VW = Tr<MODE>::V>
 __global__ void __launch_bounds__(128) k_check(const int32_t* __restrict__ row_ptr,
                                                const int32_t* __restrict__ col_idx, int M,
                                                const typename Tr<MODE>::T* __restrict__ s,
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(128) k_check(const int32_t* __restrict__ row_p
                                                int paper, IterWeights wt = IterWeights()) {
     using T = typename Tr<MODE>::T;
     using A = typename Tr<MODE>::A;
-    constexpr int V = Tr<MODE>::V;
+    constexpr int V = VW;
     using VT = Vec<T, V>;
     using VS = Vec<uint8_t, V>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(128) k_check(const int32_t* __restrict__ row_p
 // Variable-node pass. Block = 4 warps = 4 columns; lane = one frame vector.
 // test_prev: the previous decision's syndrome (in unsat) decides whether a frame stops.
 // ------------------------------------------------------------------------------------
-template <int MODE>
+template <int MODE, int VW = Tr<MODE>::V>
 __global__ void __launch_bounds__(128) k_var(const int32_t* __restrict__ col_ptr,
                                              const int32_t* __restrict__ col_edge, int N,
                                              const typename Tr<MODE>::R* __restrict__ r,
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(128) k_var(const int32_t* __restrict__ col_ptr
     using T = typename Tr<MODE>::T;
     using R = typename Tr<MODE>::R;
     using A = typename Tr<MODE>::A;
-    constexpr int V = Tr<MODE>::V;
+    constexpr int V = VW;
     using VT = Vec<T, V>;
     using VR = Vec<R, V>;
     using VS = Vec<uint8_t, V>;
@@ -329,11 +329,10 @@ __global__ void k_finish(const int32_t* done_iter, const uint8_t* unsat_final, i
     if (out_ok) out_ok[f] = d >= 0 ? 1 : (unsat_final[f] == 0);
 }
 
-template <int MODE>
+template <int MODE, int V>
 int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_t st) {
     using T = typename Tr<MODE>::T;
     using R = typename Tr<MODE>::R;
-    constexpr int V = Tr<MODE>::V;
     const int Fp = w.Fp;
     T* s = (T*)w.s;
     T* eta = (T*)w.eta;
@@ -356,27 +355,27 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
             const IterWeights wt{g.col_class, a.w_alpha + (size_t)row * a.n_classes,
                                  a.w_beta + (size_t)row * a.n_classes};
             if (k == 1)
-                k_check<MODE, true, false, true><<<gc, 128, 0, st>>>(
+                k_check<MODE, true, false, true, V><<<gc, 128, 0, st>>>(
                     g.row_ptr, g.col_idx, a.M, s, eta, Fp, state, un, test_prev, w.n_done, a.frames,
                     a.paper_slicer, wt);
             else
-                k_check<MODE, false, false, true><<<gc, 128, 0, st>>>(
+                k_check<MODE, false, false, true, V><<<gc, 128, 0, st>>>(
                     g.row_ptr, g.col_idx, a.M, s, eta, Fp, state, un, test_prev, w.n_done, a.frames,
                     a.paper_slicer, wt);
         } else if (k == 1)
-            k_check<MODE, true, false><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp,
+            k_check<MODE, true, false, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp,
                                                            state, un, test_prev, w.n_done,
                                                            a.frames, a.paper_slicer);
         else
-            k_check<MODE, false, false><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp,
+            k_check<MODE, false, false, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp,
                                                             state, un, test_prev, w.n_done,
                                                             a.frames, a.paper_slicer);
-        k_var<MODE><<<gv, 128, 0, st>>>(g.col_ptr, g.col_edge, a.N, r, s, eta, Fp, state,
+        k_var<MODE, V><<<gv, 128, 0, st>>>(g.col_ptr, g.col_edge, a.N, r, s, eta, Fp, state,
                                         w.done_iter, un, test_prev, k, w.n_done, a.frames);
         launches += 2;
     }
     uint8_t* unf = w.unsat + (size_t)(a.L + 1) * Fp;
-    k_check<MODE, false, true><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp, state,
+    k_check<MODE, false, true, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp, state,
                                                    unf, 1, w.n_done, a.frames, a.paper_slicer);
     // (the final pass returns at once when every frame has stopped: their status is known)
     k_store<MODE><<<dim3((a.N + 31) / 32, (a.frames + 31) / 32), dim3(32, 8), 0, st>>>(
@@ -396,8 +395,25 @@ size_t stream_bytes(int mode, int32_t N, int64_t E, int32_t Fp, int32_t L) {
 }
 
 int stream_decode(int mode, const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
-                  cudaStream_t st) {
-    return mode == kModeFP32 ? run<kModeFP32>(g, a, w, st) : run<kModeFixed>(g, a, w, st);
+                  cudaStream_t st, int vw) {
+    // vw: frames per lane (0 = the 16-byte vector of the mode); w.Fp is a multiple of 32 vw.
+    if (mode == kModeFP32) {
+        switch (vw) {
+            case 1: return run<kModeFP32, 1>(g, a, w, st);
+            case 2: return run<kModeFP32, 2>(g, a, w, st);
+            case 0:
+            case 4: return run<kModeFP32, 4>(g, a, w, st);
+            default: return LDPC_ERR_INVALID_ARG;
+        }
+    }
+    switch (vw) {
+        case 1: return run<kModeFixed, 1>(g, a, w, st);
+        case 2: return run<kModeFixed, 2>(g, a, w, st);
+        case 4: return run<kModeFixed, 4>(g, a, w, st);
+        case 0:
+        case 8: return run<kModeFixed, 8>(g, a, w, st);
+        default: return LDPC_ERR_INVALID_ARG;
+    }
 }
 
 }  // namespace ldpc_impl

@@ -62,6 +62,7 @@ SIGNATURES = {
     "ldpc_set_stream": (ctypes.c_int, [P, P]),
     "ldpc_set_mode": (ctypes.c_int, [P, I32]),
     "ldpc_set_variant": (ctypes.c_int, [P, I32]),
+    "ldpc_set_stream_group": (ctypes.c_int, [P, I32]),
     "ldpc_set_tuning": (ctypes.c_int, [P, I32, I32, I32]),
     "ldpc_get_tuning": (ctypes.c_int, [P, PI32, PI32, PI32]),
     "ldpc_autotune": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(ctypes.c_float)]),
@@ -157,6 +158,10 @@ def ldpc_set_stream(h, stream_ptr):
 
 def ldpc_set_mode(h, mode):
     return load().ldpc_set_mode(h, mode)
+
+
+def ldpc_set_stream_group(h, frames_per_group):
+    return load().ldpc_set_stream_group(h, frames_per_group)
 
 
 def ldpc_set_variant(h, variant):
@@ -311,6 +316,10 @@ class Decoder:
         v = {"auto": LDPC_VARIANT_AUTO, "stream": LDPC_VARIANT_STREAM,
              "resident": LDPC_VARIANT_RESIDENT, "dense": LDPC_VARIANT_DENSE}[variant]
         _check(load().ldpc_set_variant(self.h, v), "ldpc_set_variant")
+
+    def set_stream_group(self, frames_per_group: int):
+        """Streaming variant: 0 automatic L2-sized frame groups, -1 none, > 0 group size."""
+        _check(load().ldpc_set_stream_group(self.h, frames_per_group), "ldpc_set_stream_group")
 
     def set_tuning(self, frames_per_tile=0, threads=0, index_placement=0):
         _check(load().ldpc_set_tuning(self.h, frames_per_tile, threads, index_placement),

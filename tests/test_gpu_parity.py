@@ -127,6 +127,27 @@ def test_irregular_64800_streaming(torch_cuda, mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("group", [32, 64])
+def test_streaming_in_l2_sized_frame_groups(torch_cuda, mode, group):
+    """The streaming variant decoding a batch in frame groups (one frame per lane), with a
+    ragged last group, against the oracle; early stop on and off."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder
+    code = inputs.irregular_code(2000, 1000, [2, 3, 8], [0.5, 0.375, 0.125], 9)
+    llr = inputs.all_zero_awgn_llr(150, code.N, 1.8, code.design_rate, 19)
+    for es in (True, False):
+        dec = Decoder.from_code(code, mode=mode)
+        dec.set_variant("stream")
+        dec.set_stream_group(group)
+        b, it, ok, sf = dec.decode(torch.from_numpy(llr).cuda(), 30, early_stop=es, want_ok=True,
+                                   want_soft=True)
+        torch.cuda.synchronize()
+        got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
+        assert_parity(got, oracle_decode(code, llr, 30, mode, early_stop=es), mode, f"group={group}")
+        dec.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_check_every_and_paper_slicer(torch_cuda, mode, variant):
     code = inputs.qc_code(4, 8, 32, 0.7, 3)
@@ -293,19 +314,20 @@ def test_dense_map_reduce_variant(torch_cuda, early_stop):
 
 
 def test_workspace_too_large_is_an_error_not_a_crash(torch_cuda):
-    """A streaming decode whose workspace cannot be allocated returns LDPC_ERR_OOM before
-    anything is launched (the LLR buffer is never read), and the handle stays usable."""
+    """Reserving a streaming workspace larger than the device returns LDPC_ERR_OOM (nothing
+    is launched and no frame buffer is involved), and the handle stays usable. Every
+    buffer passed to a decode here holds the frames it is told about."""
     torch = torch_cuda
     import ctypes
     from paper_2507_10424_gb300 import ldpc
     code = inputs.cfg_irregular_64800()
     dec = ldpc.Decoder.from_code(code)
+    dec.set_variant("stream")
     x = torch.zeros((8, code.N), device="cuda")
     bits = torch.zeros((8, code.N), dtype=torch.uint8, device="cuda")
     it = torch.zeros(8, dtype=torch.int32, device="cuda")
     P = lambda t: ctypes.c_void_p(t.data_ptr())
     huge = 2_000_000  # frames: about 1.6 TB of edge messages, more than the device holds
-    assert ldpc.ldpc_decode(dec.h, P(x), huge, 5, P(bits), P(it)) == ldpc.LDPC_ERR_OOM
     assert ldpc.ldpc_reserve(dec.h, huge) == ldpc.LDPC_ERR_OOM
     assert ldpc.ldpc_decode(dec.h, P(x), 8, 5, P(bits), P(it)) == ldpc.LDPC_OK
     torch.cuda.synchronize()
