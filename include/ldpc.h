@@ -74,6 +74,12 @@ typedef struct ldpc ldpc_t; /* opaque handle */
 #define LDPC_VARIANT_DENSE 3    /* the paper's dense m x n map-reduce form (Algorithm 2): a
                                    baseline; FP32 only, at most 65535 frames per call, and
                                    4 M N bytes of workspace per frame */
+#define LDPC_VARIANT_CLUSTER 4  /* one persistent kernel; a thread-block cluster of 2-16 CTAs
+                                   keeps a tile of frames in its distributed shared memory,
+                                   rows and columns split between the CTAs. For codes too
+                                   large for one SM; slower than streaming there on GB300
+                                   (scattered reads of other CTAs' shared memory), so it is
+                                   never chosen by AUTO */
 
 /*
  * ldpc_create: build a decoder for the M x N parity matrix H (host pointer, dense uint8,
@@ -261,7 +267,8 @@ int ldpc_set_stream(ldpc_t *h, void *cuda_stream);
 int ldpc_set_mode(ldpc_t *h, int32_t mode);
 
 /* ldpc_set_variant: choose the kernel variant (LDPC_VARIANT_*). RESIDENT fails with
- * LDPC_ERR_UNSUPPORTED when one frame of this code does not fit in shared memory. */
+ * LDPC_ERR_UNSUPPORTED when one frame of this code does not fit in shared memory, CLUSTER
+ * when one frame does not fit the shared memory of the requested (or any) cluster. */
 int ldpc_set_variant(ldpc_t *h, int32_t variant);
 
 /*
@@ -300,6 +307,26 @@ int ldpc_get_tuning(const ldpc_t *h, int32_t *frames_per_tile, int32_t *threads,
  * not depend on the grouping; small groups leave the GPU partly idle, which is why it is
  * off by default. Returns LDPC_ERR_INVALID_ARG for other values. */
 int ldpc_set_stream_group(ldpc_t *h, int32_t frames_per_group);
+
+/*
+ * ldpc_set_cluster_shape: launch shape of the cluster variant (0 = automatic for each field).
+ * cluster_size in {0, 1, 2, 4, 8, 16}: CTAs per cluster (automatic: the smallest of 2, 4,
+ * 8, 16 that holds a frame; 16 needs the device's non-portable cluster size);
+ * frames_per_tile in {0, 1, 2, 4}: frames interleaved per tile (automatic: the most that
+ * fit); threads in {0} or multiples of 32 in [64, 1024] (automatic: 1024). The CTAs of a
+ * cluster split the rows and the columns of H by edge count; each needs 16-bit slot ids
+ * (at most 65536 row slots and 65535 columns). Results do not depend on the shape.
+ * LDPC_ERR_INVALID_ARG for values outside these sets; a shape that does not fit the code
+ * shows up as LDPC_ERR_UNSUPPORTED from the cluster variant.
+ */
+int ldpc_set_cluster_shape(ldpc_t *h, int32_t cluster_size, int32_t frames_per_tile,
+                           int32_t threads);
+
+/* ldpc_get_cluster_shape: the cluster variant's shape in the current mode, and how many
+ * clusters the device holds at once (any pointer may be NULL). LDPC_ERR_UNSUPPORTED when
+ * no cluster shape fits. */
+int ldpc_get_cluster_shape(const ldpc_t *h, int32_t *cluster_size, int32_t *frames_per_tile,
+                           int32_t *threads, int32_t *clusters);
 
 /* ldpc_get_variant: the variant the next decode will run (AUTO resolved). */
 int ldpc_get_variant(const ldpc_t *h, int32_t *variant);

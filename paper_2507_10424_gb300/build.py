@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libldpc.so")
 SOURCES = ["graph.cpp", "api.cu", "stream_kernels.cu", "resident.cu", "resident_fp32.cu",
            "resident_fixed.cu", "noalloc.cu", "learn_kernels.cu", "batch.cu",
-           "dense_kernels.cu"]
+           "dense_kernels.cu", "cluster.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

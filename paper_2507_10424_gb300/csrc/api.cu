@@ -74,7 +74,15 @@ struct ldpc {
     size_t dense_cap = 0;
     int32_t stream_group = -1;   // streaming: -1 no frame groups, 0 L2-sized groups, > 0 group size
     int l2_bytes = 0;
-    int32_t* counters = nullptr;  // [0] resident tile counter, [1] streaming done count
+    int32_t* counters = nullptr;  // [0] resident / cluster tile counter, [1] streaming done count
+    // cluster variant: layouts built on demand from the host graph, one per cluster size
+    // 2^i; plans per mode, recomputed after any change of tuning or weights
+    HostGraph hg;
+    mutable DevCluster dcl[5];
+    mutable int dcl_state[5] = {};  // 0 not built, 1 built, -1 cannot be built
+    int32_t cl_C = 0, cl_FT = 0, cl_threads = 0;  // requested shape, 0 = automatic
+    mutable ClusterPlan cl_plan[2];
+    mutable int cl_valid[2] = {};
     int32_t last_launches = 0;
     // host pipeline staging (2 slots)
     cudaStream_t h2d = nullptr, d2h = nullptr;
@@ -90,6 +98,13 @@ static void free_graph(DevGraph& g) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     g = DevGraph();
+}
+
+static void free_cluster(DevCluster& c) {
+    void* ptrs[] = {c.meta, c.r_base, c.c_base, c.r_deg, c.c_deg, c.r_ref, c.c_ref, c.r_cls, c.pos_of_col};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    c = DevCluster();
 }
 
 static void free_stream_work(ldpc_t* h) {
@@ -159,16 +174,69 @@ static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L, int32_t gran
 
 // Resident plans for both modes under the current tuning and weights.
 static void replan(ldpc_t* h) {
+    h->cl_valid[0] = h->cl_valid[1] = 0;
     if (!h->dg.sliced) return;
     const int we = h->w_rows * h->dg.n_classes;
     h->plan[kModeFP32] = resident_plan(kModeFP32, h->dg, h->N, h->device, h->tuning, we);
     h->plan[kModeFixed] = resident_plan(kModeFixed, h->dg, h->N, h->device, h->tuning, 0);
 }
 
+// The cluster layout for cluster size 2^li, built and uploaded on first use.
+static bool cluster_layout(const ldpc_t* h, int li) {
+    if (h->dcl_state[li]) return h->dcl_state[li] > 0;
+    h->dcl_state[li] = -1;
+    ClusterGraph cgr;
+    if (!build_cluster(h->hg, 1 << li, cgr)) return false;
+    DevCluster d;
+    d.C = cgr.C;
+    d.E_cap = cgr.E_cap;
+    d.P_cap = cgr.P_cap;
+    if (upload(&d.meta, cgr.meta.data(), cgr.meta.size()) ||
+        upload(&d.r_base, cgr.r_base.data(), cgr.r_base.size()) ||
+        upload(&d.c_base, cgr.c_base.data(), cgr.c_base.size()) ||
+        upload(&d.r_deg, cgr.r_deg.data(), cgr.r_deg.size()) ||
+        upload(&d.c_deg, cgr.c_deg.data(), cgr.c_deg.size()) ||
+        upload(&d.r_ref, cgr.r_ref.data(), cgr.r_ref.size()) ||
+        upload(&d.c_ref, cgr.c_ref.data(), cgr.c_ref.size()) ||
+        upload(&d.r_cls, cgr.r_cls.data(), cgr.r_cls.size()) ||
+        upload(&d.pos_of_col, cgr.pos_of_col.data(), cgr.pos_of_col.size())) {
+        free_cluster(d);
+        cudaGetLastError();
+        return false;
+    }
+    h->dcl[li] = d;
+    h->dcl_state[li] = 1;
+    return true;
+}
+
+// Cluster plan of a mode: the requested cluster size, else the smallest real cluster
+// (2, 4, 8, 16 CTAs) that holds a tile.
+static const ClusterPlan& cluster_plan_of(const ldpc_t* h, int mode) {
+    if (h->cl_valid[mode]) return h->cl_plan[mode];
+    ClusterPlan best;
+    const int we = (mode == kModeFP32 && h->w_rows > 0) ? h->w_rows * h->dg.n_classes : 0;
+    for (int li = 0; li <= 4 && !best.ok; li++) {
+        const int C = 1 << li;
+        if (h->cl_C ? C != h->cl_C : C == 1) continue;
+        if (!cluster_layout(h, li)) continue;
+        best = cluster_plan(mode, h->dcl[li], h->cl_FT, h->cl_threads, we);
+    }
+    h->cl_plan[mode] = best;
+    h->cl_valid[mode] = 1;
+    return h->cl_plan[mode];
+}
+
+static int log2_of(int C) {
+    int li = 0;
+    while ((1 << li) < C) li++;
+    return li;
+}
+
+// AUTO: resident when a frame fits one SM, else streaming. The cluster variant is never
+// chosen automatically: on codes too large for one SM it measured slower than streaming,
+// its scattered 2- and 4-byte reads of other CTAs' shared memory being the bottleneck.
 static int resolved_variant(const ldpc_t* h) {
-    if (h->variant == LDPC_VARIANT_DENSE) return LDPC_VARIANT_DENSE;
-    if (h->variant == LDPC_VARIANT_STREAM) return LDPC_VARIANT_STREAM;
-    if (h->variant == LDPC_VARIANT_RESIDENT) return LDPC_VARIANT_RESIDENT;
+    if (h->variant != LDPC_VARIANT_AUTO) return h->variant;
     return h->plan[h->mode].ok ? LDPC_VARIANT_RESIDENT : LDPC_VARIANT_STREAM;
 }
 
@@ -253,6 +321,7 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
     }
     e = cudaMalloc((void**)&h->counters, 4 * sizeof(int32_t));
     if (e != cudaSuccess) return bail(alloc_fail(e));
+    h->hg = std::move(hg);
     g_last_error = LDPC_OK;
     return h;
 }
@@ -356,6 +425,10 @@ int ldpc_decode_ex(ldpc_t* h, const void* llr, int32_t llr_dtype, int32_t frames
     } else if (resolved_variant(h) == LDPC_VARIANT_RESIDENT) {
         if (!h->plan[h->mode].ok) return fail(LDPC_ERR_UNSUPPORTED);
         n = resident_decode(h->mode, h->dg, h->plan[h->mode], a, h->counters, h->num_sms, h->stream);
+    } else if (resolved_variant(h) == LDPC_VARIANT_CLUSTER) {
+        const ClusterPlan& p = cluster_plan_of(h, h->mode);
+        if (!p.ok) return fail(LDPC_ERR_UNSUPPORTED);
+        n = cluster_decode(h->mode, h->dcl[log2_of(p.C)], p, a, h->counters, h->stream);
     } else {
         // A batch whose streaming working set (messages, posteriors, channel values) would
         // overflow L2 is decoded in frame groups that fit, one frame per lane, each group
@@ -654,10 +727,37 @@ int ldpc_set_stream_group(ldpc_t* h, int32_t frames_per_group) {
     return LDPC_OK;
 }
 
+int ldpc_set_cluster_shape(ldpc_t* h, int32_t cluster_size, int32_t frames_per_tile, int32_t threads) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    const bool c_ok = cluster_size == 0 || cluster_size == 1 || cluster_size == 2 || cluster_size == 4 ||
+                      cluster_size == 8 || cluster_size == 16;
+    const bool f_ok = frames_per_tile == 0 || frames_per_tile == 1 || frames_per_tile == 2 || frames_per_tile == 4;
+    const bool t_ok = threads == 0 || (threads % 32 == 0 && threads >= 64 && threads <= 1024);
+    if (!c_ok || !f_ok || !t_ok) return fail(LDPC_ERR_INVALID_ARG);
+    h->cl_C = cluster_size;
+    h->cl_FT = frames_per_tile;
+    h->cl_threads = threads;
+    h->cl_valid[0] = h->cl_valid[1] = 0;
+    return LDPC_OK;
+}
+
+int ldpc_get_cluster_shape(const ldpc_t* h, int32_t* cluster_size, int32_t* frames_per_tile,
+                           int32_t* threads, int32_t* clusters) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    const ClusterPlan& p = cluster_plan_of(h, h->mode);
+    if (!p.ok) return fail(LDPC_ERR_UNSUPPORTED);
+    if (cluster_size) *cluster_size = p.C;
+    if (frames_per_tile) *frames_per_tile = p.FT;
+    if (threads) *threads = p.threads;
+    if (clusters) *clusters = p.clusters;
+    return LDPC_OK;
+}
+
 int ldpc_set_variant(ldpc_t* h, int32_t variant) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
-    if (variant < LDPC_VARIANT_AUTO || variant > LDPC_VARIANT_DENSE) return fail(LDPC_ERR_INVALID_ARG);
+    if (variant < LDPC_VARIANT_AUTO || variant > LDPC_VARIANT_CLUSTER) return fail(LDPC_ERR_INVALID_ARG);
     if (variant == LDPC_VARIANT_RESIDENT && !h->plan[h->mode].ok) return fail(LDPC_ERR_UNSUPPORTED);
+    if (variant == LDPC_VARIANT_CLUSTER && !cluster_plan_of(h, h->mode).ok) return fail(LDPC_ERR_UNSUPPORTED);
     h->variant = variant;
     return LDPC_OK;
 }
@@ -725,6 +825,7 @@ void ldpc_destroy(ldpc_t* h) {
     }
     free_stream_work(h);
     free_graph(h->dg);
+    for (auto& c : h->dcl) free_cluster(c);
     if (h->counters) cudaFree(h->counters);
     if (h->w_alpha) cudaFree(h->w_alpha);
     if (h->dense_work) cudaFree(h->dense_work);

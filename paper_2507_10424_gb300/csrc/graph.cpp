@@ -183,4 +183,101 @@ bool build_sliced(const HostGraph& g, SlicedGraph& sg) {
     return true;
 }
 
+// Cut items 0 .. n-1 into C contiguous ranges of about equal total degree.
+static std::vector<int32_t> cut_by_degree(const std::vector<int32_t>& ptr, int C) {
+    const int32_t n = (int32_t)ptr.size() - 1;
+    const int64_t E = ptr[n];
+    std::vector<int32_t> b(C + 1, n);
+    b[0] = 0;
+    int32_t x = 0;
+    for (int q = 1; q < C; q++) {
+        const int64_t target = E * q / C;
+        while (x < n && ptr[x] < target) x++;
+        b[q] = x;
+    }
+    return b;
+}
+
+// Items lo .. hi-1 sorted by degree (descending, stable).
+static std::vector<int32_t> range_by_degree(const std::vector<int32_t>& ptr, int32_t lo, int32_t hi) {
+    std::vector<int32_t> order(hi - lo);
+    std::iota(order.begin(), order.end(), lo);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return (ptr[a + 1] - ptr[a]) > (ptr[b + 1] - ptr[b]);
+    });
+    return order;
+}
+
+bool build_cluster(const HostGraph& g, int C, ClusterGraph& cg) {
+    if (C < 1 || C > 16 || g.max_dc > 255 || g.max_dv > 255) return false;
+    cg = ClusterGraph();
+    cg.C = C;
+    cg.meta.assign((size_t)C * kClMeta, 0);
+    cg.pos_of_col.assign(g.N, 0);
+    const std::vector<int32_t> J = cut_by_degree(g.col_ptr, C), I = cut_by_degree(g.row_ptr, C);
+    std::vector<uint8_t> owner(g.N, 0);
+    std::vector<std::vector<int32_t>> corder(C), rorder(C);
+    for (int q = 0; q < C; q++) {
+        corder[q] = range_by_degree(g.col_ptr, J[q], J[q + 1]);
+        rorder[q] = range_by_degree(g.row_ptr, I[q], I[q + 1]);
+        if (corder[q].size() > 65535) return false;
+        for (size_t p = 0; p < corder[q].size(); p++) {
+            cg.pos_of_col[corder[q][p]] = (uint16_t)p;
+            owner[corder[q][p]] = (uint8_t)q;
+        }
+    }
+    // row side: every edge's slot in its row owner's layout, and the column it reads
+    std::vector<uint32_t> slot_ref(g.E);
+    for (int q = 0; q < C; q++) {
+        int32_t* m = &cg.meta[(size_t)q * kClMeta];
+        std::vector<int32_t> base;
+        std::vector<uint8_t> deg;
+        const int32_t Ep = make_slices(g.row_ptr, rorder[q], base, deg);
+        if (Ep > 65536) return false;
+        m[kClRTasks] = (int32_t)deg.size();
+        m[kClRBase] = (int32_t)cg.r_base.size();
+        m[kClRDeg] = (int32_t)cg.r_deg.size();
+        m[kClRRef] = (int32_t)cg.r_ref.size();
+        const size_t off = cg.r_ref.size();
+        cg.r_base.insert(cg.r_base.end(), base.begin(), base.end());
+        cg.r_deg.insert(cg.r_deg.end(), deg.begin(), deg.end());
+        cg.r_ref.resize(off + Ep, 0);
+        cg.r_cls.resize(off + Ep, 0);
+        for (size_t t = 0; t < rorder[q].size(); t++) {
+            const int32_t i = rorder[q][t], sl = (int32_t)(t / 32), l = (int32_t)(t % 32);
+            for (int32_t k = 0; k < g.row_ptr[i + 1] - g.row_ptr[i]; k++) {
+                const int32_t slot = base[sl] + 32 * k + l, e = g.row_ptr[i] + k, c = g.col_idx[e];
+                cg.r_ref[off + slot] = ((uint32_t)owner[c] << 16) | cg.pos_of_col[c];
+                cg.r_cls[off + slot] = g.col_class.empty() ? 0 : g.col_class[c];
+                slot_ref[e] = ((uint32_t)q << 16) | (uint32_t)slot;
+            }
+        }
+        cg.E_cap = std::max(cg.E_cap, Ep);
+    }
+    // column side: the slots of a column's edges in ascending row order
+    for (int q = 0; q < C; q++) {
+        int32_t* m = &cg.meta[(size_t)q * kClMeta];
+        std::vector<int32_t> base;
+        std::vector<uint8_t> deg;
+        const int32_t Ecp = make_slices(g.col_ptr, corder[q], base, deg);
+        m[kClJ0] = J[q];
+        m[kClJ1] = J[q + 1];
+        m[kClCTasks] = (int32_t)deg.size();
+        m[kClCBase] = (int32_t)cg.c_base.size();
+        m[kClCDeg] = (int32_t)cg.c_deg.size();
+        m[kClCRef] = (int32_t)cg.c_ref.size();
+        const size_t off = cg.c_ref.size();
+        cg.c_base.insert(cg.c_base.end(), base.begin(), base.end());
+        cg.c_deg.insert(cg.c_deg.end(), deg.begin(), deg.end());
+        cg.c_ref.resize(off + Ecp, 0);
+        for (size_t t = 0; t < corder[q].size(); t++) {
+            const int32_t j = corder[q][t], sl = (int32_t)(t / 32), l = (int32_t)(t % 32);
+            for (int32_t k = 0; k < g.col_ptr[j + 1] - g.col_ptr[j]; k++)
+                cg.c_ref[off + base[sl] + 32 * k + l] = slot_ref[g.col_edge[g.col_ptr[j] + k]];
+        }
+        cg.P_cap = std::max(cg.P_cap, (int32_t)deg.size());
+    }
+    return true;
+}
+
 }  // namespace ldpc_impl

@@ -63,6 +63,45 @@ struct SlicedGraph {
 // Returns false when the code cannot use 16-bit slot ids or 8-bit degrees.
 bool build_sliced(const HostGraph& g, SlicedGraph& sg);
 
+// ---------------------------------------------------------------------------------------
+// Cluster layout: the C CTAs of a thread-block cluster share a tile of frames. CTA (rank)
+// q owns a contiguous range of rows and one of columns, each cut at about E q / C edges,
+// and lays them out like the sliced layout above: the messages of its rows and the
+// posteriors / channel values of its columns sit in its own shared memory. A reference
+// (rank << 16) | index names an entry in the shared memory of CTA `rank`:
+//   r_ref[row slot]    -> (owner of the edge's column, that column's position)
+//   c_ref[column slot] -> (owner of the edge's row, the edge's row slot), ascending rows
+// meta[q][...] gives CTA q's column range and the offsets of its parts of the arrays.
+// ---------------------------------------------------------------------------------------
+enum ClMeta { kClJ0, kClJ1, kClRTasks, kClCTasks, kClRBase, kClRDeg, kClRRef, kClCBase, kClCDeg,
+              kClCRef, kClMeta };
+struct ClusterGraph {
+    int32_t C = 0;
+    int32_t E_cap = 0, P_cap = 0;      // largest per-CTA row-slot / column-position counts
+    std::vector<int32_t> meta;         // [C][kClMeta]
+    std::vector<int32_t> r_base, c_base;
+    std::vector<uint8_t> r_deg, c_deg;
+    std::vector<uint32_t> r_ref, c_ref;
+    std::vector<uint8_t> r_cls;        // class of the edge's bit, by row slot (as r_ref)
+    std::vector<uint16_t> pos_of_col;  // N: position of column j in its owner's layout
+};
+// Returns false when a CTA's part needs more than 16-bit slot ids or 8-bit degrees.
+bool build_cluster(const HostGraph& g, int C, ClusterGraph& cg);
+
+// Device copy of a cluster layout.
+struct DevCluster {
+    int32_t C = 0, E_cap = 0, P_cap = 0;
+    int32_t* meta = nullptr;
+    int32_t* r_base = nullptr;
+    int32_t* c_base = nullptr;
+    uint8_t* r_deg = nullptr;
+    uint8_t* c_deg = nullptr;
+    uint32_t* r_ref = nullptr;
+    uint32_t* c_ref = nullptr;
+    uint8_t* r_cls = nullptr;
+    uint16_t* pos_of_col = nullptr;
+};
+
 // Device copies of the graph.
 struct DevGraph {
     // CSR/CSC (streaming kernels)
@@ -151,6 +190,19 @@ ResidentPlan resident_plan(int mode, const DevGraph& dg, int32_t N, int device,
                            const ResidentTuning& tune = ResidentTuning(), int w_entries = 0);
 int resident_decode(int mode, const DevGraph& dg, const ResidentPlan& p, const DecodeArgs& a,
                     int32_t* tile_counter, int num_sms, cudaStream_t st);
+
+// Cluster variant: C CTAs (a thread-block cluster) per tile of FT frames.
+struct ClusterPlan {
+    int ok = 0;
+    int C = 0, FT = 0, threads = 0;
+    int clusters = 0;     // clusters resident at once on the device
+    size_t smem = 0;      // dynamic shared memory per CTA
+};
+// The plan for cluster size C (a layout built for C) and frames per tile FT (0: the most
+// that fit); threads 0 = 1024.
+ClusterPlan cluster_plan(int mode, const DevCluster& dc, int FT, int threads, int w_entries);
+int cluster_decode(int mode, const DevCluster& dc, const ClusterPlan& p, const DecodeArgs& a,
+                   int32_t* tile_counter, cudaStream_t st);
 
 // Read access to a handle's graph and settings for entry points outside api.cu.
 struct HandleView {

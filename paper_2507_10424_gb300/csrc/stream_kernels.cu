@@ -402,7 +402,7 @@ int stream_decode(int mode, const DevGraph& g, const DecodeArgs& a, const Stream
             case 1: return run<kModeFP32, 1>(g, a, w, st);
             case 2: return run<kModeFP32, 2>(g, a, w, st);
             case 0:
-            case 4: return run<kModeFP32, 4>(g, a, w, st);
+            case Tr<kModeFP32>::V: return run<kModeFP32, Tr<kModeFP32>::V>(g, a, w, st);
             default: return LDPC_ERR_INVALID_ARG;
         }
     }
@@ -411,7 +411,7 @@ int stream_decode(int mode, const DevGraph& g, const DecodeArgs& a, const Stream
         case 2: return run<kModeFixed, 2>(g, a, w, st);
         case 4: return run<kModeFixed, 4>(g, a, w, st);
         case 0:
-        case 8: return run<kModeFixed, 8>(g, a, w, st);
+        case Tr<kModeFixed>::V: return run<kModeFixed, Tr<kModeFixed>::V>(g, a, w, st);
         default: return LDPC_ERR_INVALID_ARG;
     }
 }

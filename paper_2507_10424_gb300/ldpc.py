@@ -34,6 +34,7 @@ LDPC_VARIANT_AUTO = 0
 LDPC_VARIANT_STREAM = 1
 LDPC_VARIANT_RESIDENT = 2
 LDPC_VARIANT_DENSE = 3
+LDPC_VARIANT_CLUSTER = 4
 LDPC_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 # name -> (restype, argtypes), exactly the declarations of include/ldpc.h
@@ -63,6 +64,8 @@ SIGNATURES = {
     "ldpc_set_mode": (ctypes.c_int, [P, I32]),
     "ldpc_set_variant": (ctypes.c_int, [P, I32]),
     "ldpc_set_stream_group": (ctypes.c_int, [P, I32]),
+    "ldpc_set_cluster_shape": (ctypes.c_int, [P, I32, I32, I32]),
+    "ldpc_get_cluster_shape": (ctypes.c_int, [P, PI32, PI32, PI32, PI32]),
     "ldpc_set_tuning": (ctypes.c_int, [P, I32, I32, I32]),
     "ldpc_get_tuning": (ctypes.c_int, [P, PI32, PI32, PI32]),
     "ldpc_autotune": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(ctypes.c_float)]),
@@ -162,6 +165,17 @@ def ldpc_set_mode(h, mode):
 
 def ldpc_set_stream_group(h, frames_per_group):
     return load().ldpc_set_stream_group(h, frames_per_group)
+
+
+def ldpc_set_cluster_shape(h, cluster_size, frames_per_tile, threads):
+    return load().ldpc_set_cluster_shape(h, cluster_size, frames_per_tile, threads)
+
+
+def ldpc_get_cluster_shape(h):
+    """(cluster_size, frames_per_tile, threads, clusters) of the cluster variant."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(load().ldpc_get_cluster_shape(h, *[ctypes.byref(x) for x in v]), "ldpc_get_cluster_shape")
+    return tuple(x.value for x in v)
 
 
 def ldpc_set_variant(h, variant):
@@ -314,8 +328,18 @@ class Decoder:
 
     def set_variant(self, variant: str):
         v = {"auto": LDPC_VARIANT_AUTO, "stream": LDPC_VARIANT_STREAM,
-             "resident": LDPC_VARIANT_RESIDENT, "dense": LDPC_VARIANT_DENSE}[variant]
+             "resident": LDPC_VARIANT_RESIDENT, "dense": LDPC_VARIANT_DENSE,
+             "cluster": LDPC_VARIANT_CLUSTER}[variant]
         _check(load().ldpc_set_variant(self.h, v), "ldpc_set_variant")
+
+    def set_cluster_shape(self, cluster_size=0, frames_per_tile=0, threads=0):
+        """Cluster variant: CTAs per cluster, frames per tile, CTA size (0 = automatic)."""
+        _check(load().ldpc_set_cluster_shape(self.h, cluster_size, frames_per_tile, threads),
+               "ldpc_set_cluster_shape")
+
+    def cluster_shape(self):
+        """(cluster_size, frames_per_tile, threads, clusters resident at once)."""
+        return ldpc_get_cluster_shape(self.h)
 
     def set_stream_group(self, frames_per_group: int):
         """Streaming variant: 0 automatic L2-sized frame groups, -1 none, > 0 group size."""
@@ -352,7 +376,7 @@ class Decoder:
 
     def variant(self) -> str:
         return {LDPC_VARIANT_STREAM: "stream", LDPC_VARIANT_RESIDENT: "resident",
-                LDPC_VARIANT_DENSE: "dense"}[ldpc_get_variant(self.h)]
+                LDPC_VARIANT_DENSE: "dense", LDPC_VARIANT_CLUSTER: "cluster"}[ldpc_get_variant(self.h)]
 
     def set_mode(self, mode: str):
         _check(load().ldpc_set_mode(self.h, {"fp32": LDPC_MODE_FP32, "fixed": LDPC_MODE_FIXED}[mode]),

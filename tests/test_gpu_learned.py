@@ -35,7 +35,7 @@ def random_weights(T, C, seed):
             rng.uniform(0.0, 0.4, (T, C)).astype(np.float32))
 
 
-@pytest.mark.parametrize("variant", ["stream", "resident"])
+@pytest.mark.parametrize("variant", ["stream", "resident", "cluster"])
 @pytest.mark.parametrize("early_stop", [True, False])
 def test_weighted_decode_matches_oracle(torch_cuda, variant, early_stop):
     torch = torch_cuda
@@ -59,7 +59,7 @@ def test_weighted_decode_matches_oracle(torch_cuda, variant, early_stop):
         dec.close()
 
 
-@pytest.mark.parametrize("variant", ["stream", "resident"])
+@pytest.mark.parametrize("variant", ["stream", "resident", "cluster"])
 def test_unit_weights_equal_plain_on_gpu(torch_cuda, variant):
     torch = torch_cuda
     from paper_2507_10424_gb300.ldpc import Decoder

@@ -72,7 +72,7 @@ def tanner_code():
 
 
 MODES = ["fp32", "fixed"]
-VARIANTS = ["stream", "resident"]
+VARIANTS = ["stream", "resident", "cluster"]
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -121,9 +121,58 @@ def test_irregular_64800_streaming(torch_cuda, mode):
     """Irregular N=64800 (weights 2/3/8), all-zero codeword at 1.0 dB, 50 iterations, early stop."""
     code = inputs.cfg_irregular_64800()
     llr = inputs.all_zero_awgn_llr(24, code.N, 1.0, code.design_rate, 41)
-    got = gpu_decode(torch_cuda, code, llr, 50, mode, "auto")
-    assert got[4] == "stream"  # one frame does not fit in shared memory
+    got = gpu_decode(torch_cuda, code, llr, 50, mode, "stream")
+    assert got[4] == "stream"
     assert_parity(got, oracle_decode(code, llr, 50, mode), mode, "irregular64800")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_irregular_64800_cluster(torch_cuda, mode):
+    """The same code with a tile held across a thread-block cluster (one FP32 frame is
+    about 1.3 MB: more than one SM's shared memory, less than eight SMs')."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder
+    code = inputs.cfg_irregular_64800()
+    llr = inputs.all_zero_awgn_llr(24, code.N, 1.3, code.design_rate, 43)
+    got = gpu_decode(torch, code, llr, 50, mode, "cluster")
+    assert got[4] == "cluster"
+    assert_parity(got, oracle_decode(code, llr, 50, mode), mode, "irregular64800 cluster")
+    dec = Decoder.from_code(code, mode=mode)
+    C, FT, threads, clusters = dec.cluster_shape()
+    assert C in (4, 8, 16) and clusters * C <= 152 and clusters >= 1
+    dec.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_every_cluster_shape(torch_cuda, mode):
+    """Results must not depend on the cluster size, frames per tile or CTA size."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
+    code = inputs.irregular_code(2000, 1000, [2, 3, 8], [0.5, 0.375, 0.125], 9)
+    llr = inputs.all_zero_awgn_llr(45, code.N, 1.6, code.design_rate, 12)
+    x = torch.from_numpy(llr).cuda()
+    tried = set()
+    for es in (True, False):
+        want = oracle_decode(code, llr, 18, mode, early_stop=es)
+        for C in (1, 2, 4, 8, 16):
+            for ft in (0, 1, 2, 4):
+                for th in (0, 256, 608):
+                    dec = Decoder.from_code(code, mode=mode)
+                    dec.set_cluster_shape(C, ft, th)
+                    try:
+                        dec.set_variant("cluster")
+                    except LdpcError:
+                        dec.close()
+                        continue
+                    shape = dec.cluster_shape()
+                    assert shape[0] == C and (ft == 0 or shape[1] == ft)
+                    b, it, ok, sf = dec.decode(x, 18, early_stop=es, want_ok=True, want_soft=True)
+                    torch.cuda.synchronize()
+                    got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
+                    assert_parity(got, want, mode, f"C={C} FT={ft} threads={th} early_stop={es}")
+                    tried.add((C, shape[1]))
+                    dec.close()
+    assert {(1, 1), (2, 1), (4, 1), (8, 1)} <= tried
 
 
 @pytest.mark.parametrize("mode", MODES)
