@@ -265,13 +265,187 @@ __device__ __forceinline__ void phase_a(const Idx& ix, VecR<typename RT<MODE>::T
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Fixed point with an even number of interleaved frames: the int16 values of two frames
+// share a 32-bit word (frame 2p in the low half, 2p + 1 in the high half) and phase A
+// works on the pair at once with the packed 16-bit min / max / add instructions. Every
+// step is exact, so the results are those of the per-frame code above:
+//   lambda = sat(s - eta): two 32-bit differences, saturated and packed by one
+//            conversion (to [-32768, 32767]), then max with -32767 (symmetric limit);
+//   |lambda| = max(lambda, -lambda), -x = ~x + 1 lane by lane;
+//   min0, min1, the XOR of the words (the sign bits of both lanes), as before;
+//   sweep 2: magnitude min1 where |lambda| = min0 (|lambda| - min0 >= 0, so
+//            min(|lambda| - min0, 1) is 0 there and 1 elsewhere), conditional negation
+//            by (m ^ mask) + (mask & 1) with the lane mask of the new sign.
+// ---------------------------------------------------------------------------------------
+template <int P>
+struct alignas(4 * P) Words {
+    uint32_t w[P];
+};
+__device__ __forceinline__ uint32_t p_min(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t p_max(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t p_add(uint32_t a, uint32_t b) {  // lane-wise, wrapping
+    uint32_t d;
+    asm("add.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t p_neg(uint32_t a) { return p_add(~a, 0x00010001u); }
+__device__ __forceinline__ int32_t p_lo(uint32_t w) { return (int32_t)(int16_t)(w & 0xffffu); }
+__device__ __forceinline__ int32_t p_hi(uint32_t w) { return (int32_t)w >> 16; }
+// Both lanes saturated to [-32767, 32767] and packed (lo in the low half).
+__device__ __forceinline__ uint32_t p_pack_sat(int32_t lo, int32_t hi) {
+    uint32_t d;
+    asm("cvt.pack.sat.s16.s32 %0, %1, %2;" : "=r"(d) : "r"(hi), "r"(lo));
+    return p_max(d, 0x80018001u);
+}
+// Lanes of all ones where bit 0 / bit 16 of b01 is set (b01 has no other bits).
+__device__ __forceinline__ uint32_t p_spread(uint32_t b01) { return b01 * 0xffffu; }
+
+template <int FT, bool FIRST, bool SYN, bool UPD, bool PAPER>
+__device__ __forceinline__ void phase_a_packed(const Idx& ix, VecR<int16_t, FT>* eta_v,
+                                               const VecR<int16_t, FT>* s_v, int n_rtasks,
+                                               uint32_t* unsat_w) {
+    constexpr int P = FT / 2;
+    using WT = Words<P>;
+    constexpr int UNR = FT >= 4 ? 2 : 4;
+    WT* eta = reinterpret_cast<WT*>(eta_v);
+    const WT* s = reinterpret_cast<const WT*>(s_v);
+    const int nth = blockDim.x;
+    for (int k = 0;; k++) {
+        const int task = snake(k, nth);
+        if (task >= n_rtasks) break;
+        const int d = ix.r_deg[task];
+        if (d == 0) continue;
+        const int base = ix.r_base[task >> 5] + (task & 31);
+        uint32_t min0[P], min1[P], sx[P], zx[P];
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            min0[p] = 0x7fff7fffu;
+            min1[p] = 0x7fff7fffu;
+            sx[p] = 0;
+            zx[p] = 0;
+        }
+#pragma unroll UNR
+        for (int t = 0; t < d; t++) {
+            const int slot = base + 32 * t;
+            const WT sv = s[ix.r_slot_pos[slot]];
+            if (SYN) {
+#pragma unroll
+                for (int p = 0; p < P; p++) zx[p] ^= PAPER ? p_neg(sv.w[p]) : sv.w[p];
+            }
+            if (UPD) {
+                WT ev;
+                if (!FIRST) ev = eta[slot];
+                WT lv;
+#pragma unroll
+                for (int p = 0; p < P; p++) {
+                    const uint32_t lam =
+                        FIRST ? sv.w[p]
+                              : p_pack_sat(p_lo(sv.w[p]) - p_lo(ev.w[p]), p_hi(sv.w[p]) - p_hi(ev.w[p]));
+                    const uint32_t m = p_max(lam, p_neg(lam));
+                    min1[p] = p_min(min1[p], p_max(min0[p], m));
+                    min0[p] = p_min(min0[p], m);
+                    sx[p] ^= lam;
+                    lv.w[p] = lam;
+                }
+                eta[slot] = lv;  // stash lambda for sweep 2
+            }
+        }
+        if (SYN) {
+            uint32_t z = 0;
+#pragma unroll
+            for (int p = 0; p < P; p++) z |= (((zx[p] >> 15) & 1u) | ((zx[p] >> 30) & 2u)) << (2 * p);
+            if (z) atomicOr(unsat_w, z);
+        }
+        if (UPD) {
+            uint32_t nmin0[P];
+#pragma unroll
+            for (int p = 0; p < P; p++) nmin0[p] = p_neg(min0[p]);
+#pragma unroll UNR
+            for (int t = 0; t < d; t++) {
+                const int slot = base + 32 * t;
+                const WT lv = eta[slot];
+                WT out;
+#pragma unroll
+                for (int p = 0; p < P; p++) {
+                    const uint32_t lam = lv.w[p];
+                    const uint32_t a = p_max(lam, p_neg(lam));
+                    const uint32_t ne = p_spread(p_min(p_add(a, nmin0[p]), 0x00010001u));
+                    const uint32_t m = (min0[p] & ne) | (min1[p] & ~ne);
+                    const uint32_t sb = ((lam ^ sx[p]) >> 15) & 0x00010001u;
+                    out.w[p] = p_add(m ^ p_spread(sb), sb);
+                }
+                eta[slot] = out;
+            }
+        }
+    }
+}
+
+// Phase B of the packed fixed-point form: 32-bit sums, saturated and packed at the end.
+template <int FT>
+__device__ __forceinline__ void phase_b_packed(const Idx& ix, const VecR<int16_t, FT>* eta_v,
+                                               VecR<int16_t, FT>* s_v, const VecR<int16_t, FT>* r_v,
+                                               int N) {
+    constexpr int P = FT / 2;
+    using WT = Words<P>;
+    const WT* eta = reinterpret_cast<const WT*>(eta_v);
+    WT* s = reinterpret_cast<WT*>(s_v);
+    const WT* r = reinterpret_cast<const WT*>(r_v);
+    const int nth = blockDim.x;
+    for (int k = 0;; k++) {
+        const int p0 = snake(k, nth);
+        if (p0 >= N) break;
+        const int d = ix.c_deg[p0];
+        const int base = ix.c_base[p0 >> 5] + (p0 & 31);
+        const WT rv = r[p0];
+        int32_t lo[P], hi[P];
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            lo[p] = p_lo(rv.w[p]);
+            hi[p] = p_hi(rv.w[p]);
+        }
+#pragma unroll 4
+        for (int t = 0; t < d; t++) {
+            const WT ev = eta[ix.c_slot[base + 32 * t]];
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                lo[p] += p_lo(ev.w[p]);
+                hi[p] += p_hi(ev.w[p]);
+            }
+        }
+        WT out;
+#pragma unroll
+        for (int p = 0; p < P; p++) out.w[p] = p_pack_sat(lo[p], hi[p]);
+        s[p0] = out;
+    }
+}
+
+// Phase A in the packed form where it applies (fixed point, even FT), else per frame.
+template <int MODE, int FT, bool FIRST, bool SYN, bool UPD, bool PAPER, bool W>
+__device__ __forceinline__ void phase_a_sel(const Idx& ix, VecR<typename RT<MODE>::T, FT>* eta,
+                                            const VecR<typename RT<MODE>::T, FT>* s, int n_rtasks,
+                                            uint32_t* uw) {
+    if constexpr (MODE == kModeFixed && FT % 2 == 0)
+        phase_a_packed<FT, FIRST, SYN, UPD, PAPER>(ix, eta, s, n_rtasks, uw);
+    else
+        phase_a<MODE, FT, FIRST, SYN, UPD, PAPER, W>(ix, eta, s, n_rtasks, uw);
+}
+
 // One phase A of the iteration, specialised on (first, syndrome, update).
 template <int MODE, int FT, bool PAPER, bool W>
 __device__ __forceinline__ void phase_a_any(bool first, bool syn, bool upd, const Idx& ix,
                                             VecR<typename RT<MODE>::T, FT>* eta,
                                             const VecR<typename RT<MODE>::T, FT>* s, int n_rtasks,
                                             uint32_t* uw) {
-#define LDPC_PHASE_A(F, S, U) phase_a<MODE, FT, F, S, U, PAPER, W>(ix, eta, s, n_rtasks, uw)
+#define LDPC_PHASE_A(F, S, U) phase_a_sel<MODE, FT, F, S, U, PAPER, W>(ix, eta, s, n_rtasks, uw)
     if (first) {
         if (!upd) LDPC_PHASE_A(true, true, false);
         else if (syn) LDPC_PHASE_A(true, true, true);
@@ -393,7 +567,10 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
                 __syncthreads();  // the emitted posteriors are read before phase B rewrites them
             }
         }
-        phase_b<MODE, FT>(ix, eta, s, r, N);
+        if constexpr (MODE == kModeFixed && FT % 2 == 0)
+            phase_b_packed<FT>(ix, eta, s, r, N);
+        else
+            phase_b<MODE, FT>(ix, eta, s, r, N);
         if (threadIdx.x == 0) unsat_w[par ^ 1] = 0;
         __syncthreads();
     }
