@@ -214,8 +214,11 @@ int ldpc_train_backward(ldpc_t *h, int32_t frames, int32_t iters, const float *a
  * device, all with or all without LDPC_FLAG_PAPER_SLICER, each small enough for the
  * resident variant's sliced layout). Its kernel takes (code, frame) tiles from one work
  * counter, largest codes first; a code whose frame fits in shared memory keeps its
- * messages there, a larger one uses a per-CTA slot of the batch's global scratch.
- * Results equal ldpc_decode_ex with check_every = 1 on each code.
+ * messages there. A larger code is by default decoded by the streaming kernels on a
+ * second stream forked from (and joined back to) the batch's stream, alongside the
+ * persistent kernel; ldpc_batch_set_large_codes(b, 0) puts it in the persistent launch
+ * instead, with a per-CTA slot of the batch's global scratch. Either way the launch is
+ * one recordable unit. Results equal ldpc_decode_ex with check_every = 1 on each code.
  *
  * ldpc_batch_create: NULL on failure (bad handle, mixed slicers, device mismatch, OOM).
  */
@@ -235,8 +238,15 @@ int ldpc_batch_set_io(ldpc_batch_t *b, int32_t code, const float *llr, int32_t f
  * early_stop (synchronous; waits for the batch's stream). */
 int ldpc_batch_prepare(ldpc_batch_t *b, int32_t max_iter, int32_t early_stop);
 
-/* ldpc_batch_launch: enqueue the prepared decode (a counter reset and one kernel). */
+/* ldpc_batch_launch: enqueue the prepared decode (a counter reset and the persistent
+ * kernel, plus the streaming kernels of the large codes between a fork and a join). */
 int ldpc_batch_launch(ldpc_batch_t *b);
+
+/* ldpc_batch_set_large_codes: codes too large for shared memory are decoded by the
+ * streaming kernels (streaming = 1, the default) or inside the persistent launch from
+ * global scratch (0). Takes effect at the next ldpc_batch_prepare. LDPC_ERR_INVALID_ARG
+ * for other values. */
+int ldpc_batch_set_large_codes(ldpc_batch_t *b, int32_t streaming);
 
 /* ldpc_batch_decode: ldpc_batch_prepare then ldpc_batch_launch. */
 int ldpc_batch_decode(ldpc_batch_t *b, int32_t max_iter, int32_t early_stop);

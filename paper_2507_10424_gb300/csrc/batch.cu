@@ -3,13 +3,17 @@
 // One kernel decodes the frames of every code in the batch: its CTAs take tiles (code,
 // frame) from a single atomic work counter, largest codes first, and run every flooding
 // iteration of the tile with the resident variant's tile body (decode_tile). A code whose
-// frame fits the launch's shared memory keeps eta, s and r there; a larger one keeps them
-// in the CTA's own slot of a global scratch buffer (which stays in L2 at these sizes).
-// The index arrays of every code are read from global memory. FP32 mode.
+// frame fits the launch's shared memory keeps eta, s and r there. A code too large for
+// that is, by default, decoded by the streaming kernels on a second stream forked from
+// the batch's stream (so they can fill the SMs that the persistent kernel's last tiles
+// leave idle); optionally it joins the persistent launch instead, with eta, s and r in
+// the CTA's own slot of a global scratch buffer. The index arrays of every code are read
+// from global memory. FP32 mode.
 //
-// The launch (a memset of the work counter and the kernel) touches only buffers fixed when
-// the batch's inputs and outputs are set, so it can be recorded once in a CUDA graph and
-// replayed (ldpc_batch_capture / ldpc_batch_replay).
+// The launch (a memset of the work counter, the kernel, and the streaming kernels of the
+// large codes between a fork and a join event) touches only buffers fixed when the batch
+// is prepared, so it can be recorded once in a CUDA graph and replayed
+// (ldpc_batch_capture / ldpc_batch_replay).
 #include <algorithm>
 #include <new>
 #include <vector>
@@ -104,11 +108,28 @@ struct ldpc_batch {
     int threads = 512, grid = 0;
     cudaStream_t stream = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int32_t last_launches = 0;
+    int32_t last_launches = 0, captured_launches = 0;
+    // codes too large for shared memory: streaming kernels (1) or the persistent launch (0)
+    int large_stream = 1;
+    struct Streamed {
+        int32_t code;
+        DecodeArgs a;
+        StreamWork w;
+        void* mem = nullptr;
+        size_t bytes = 0;
+    };
+    std::vector<Streamed> streamed;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 static void batch_free(ldpc_batch_t* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto& x : b->streamed)
+        if (x.mem) cudaFree(x.mem);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_counter) cudaFree(b->d_counter);
@@ -128,18 +149,38 @@ static int batch_occupancy(ldpc_batch_t* b, int threads, int* grid) {
     return LDPC_OK;
 }
 
-// Enqueue the launch (capturable): reset the work counter, run the kernel.
+// Enqueue the launch (capturable): the streaming decodes of the large codes on the side
+// stream between a fork and a join event, the work counter reset and the persistent kernel
+// on the batch's stream. Returns the number of kernels enqueued, or a negative status.
 static int batch_enqueue(ldpc_batch_t* b) {
+    int launches = 0;
+    const bool side = !b->streamed.empty();
+    if (side) {
+        if (cudaEventRecord(b->fork, b->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(b->side, b->fork, 0) != cudaSuccess)
+            return LDPC_ERR_CUDA;
+        for (auto& x : b->streamed) {
+            if (x.a.frames == 0) continue;
+            const int n = stream_decode(kModeFP32, *b->views[x.code].dg, x.a, x.w, b->side);
+            if (n < 0) return n;
+            launches += n;
+        }
+    }
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), b->stream) != cudaSuccess) return LDPC_ERR_CUDA;
-    if (b->n_tiles == 0) return LDPC_OK;
-    const int grid = std::min(b->grid, b->n_tiles);
-    if (b->paper)
-        k_multi<true><<<grid, b->threads, b->smem, b->stream>>>(b->d_desc, b->d_tiles, b->n_tiles,
-                                                                b->d_counter, b->d_scratch, b->slot_bytes);
-    else
-        k_multi<false><<<grid, b->threads, b->smem, b->stream>>>(b->d_desc, b->d_tiles, b->n_tiles,
-                                                                 b->d_counter, b->d_scratch, b->slot_bytes);
-    return cudaGetLastError() == cudaSuccess ? LDPC_OK : LDPC_ERR_CUDA;
+    if (b->n_tiles > 0) {
+        const int grid = std::min(b->grid, b->n_tiles);
+        if (b->paper)
+            k_multi<true><<<grid, b->threads, b->smem, b->stream>>>(b->d_desc, b->d_tiles, b->n_tiles,
+                                                                    b->d_counter, b->d_scratch, b->slot_bytes);
+        else
+            k_multi<false><<<grid, b->threads, b->smem, b->stream>>>(b->d_desc, b->d_tiles, b->n_tiles,
+                                                                     b->d_counter, b->d_scratch, b->slot_bytes);
+        launches++;
+    }
+    if (side && (cudaEventRecord(b->join, b->side) != cudaSuccess ||
+                 cudaStreamWaitEvent(b->stream, b->join, 0) != cudaSuccess))
+        return LDPC_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? launches : LDPC_ERR_CUDA;
 }
 
 extern "C" {
@@ -187,7 +228,10 @@ ldpc_batch_t* ldpc_batch_create(int32_t n_codes, ldpc_t* const* codes) {
         b->frames.push_back(0);
     }
     b->slot_bytes = (slot + 255) & ~(size_t)255;
-    cudaError_t e = cudaMalloc((void**)&b->d_desc, sizeof(CodeDesc) * n_codes);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_desc, sizeof(CodeDesc) * n_codes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int32_t));
     if (e == cudaSuccess && batch_occupancy(b, b->threads, &b->grid) != LDPC_OK) e = cudaErrorInvalidConfiguration;
     if (e == cudaSuccess && b->slot_bytes) e = cudaMalloc((void**)&b->d_scratch, b->slot_bytes * b->grid);
@@ -255,8 +299,67 @@ int ldpc_batch_prepare(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
         return b->views[x].E > b->views[y].E;
     });
     std::vector<Tile> tiles;
-    for (int32_t c : order)
+    std::vector<ldpc_batch::Streamed> keep;
+    for (int32_t c : order) {
+        if (b->large_stream && !b->desc[c].in_smem) {
+            // the streaming decode of this code: workspace sized for its frames and max_iter
+            ldpc_batch::Streamed x;
+            for (auto& old : b->streamed)
+                if (old.code == c) {
+                    x = old;
+                    old.mem = nullptr;
+                }
+            const ResArgs& ra = b->desc[c].a;
+            const HandleView& v = b->views[c];
+            const int32_t Fp = (b->frames[c] + 255) & ~255;
+            const size_t need = stream_bytes(kModeFP32, v.N, v.E, Fp, max_iter);
+            if (need > x.bytes) {
+                if (x.mem) {
+                    cudaStreamSynchronize(b->side);
+                    cudaFree(x.mem);
+                }
+                x.mem = nullptr;
+                x.bytes = 0;
+                if (cudaMalloc(&x.mem, need) != cudaSuccess) {
+                    cudaGetLastError();
+                    for (auto& y : keep) cudaFree(y.mem);
+                    return LDPC_ERR_OOM;
+                }
+                x.bytes = need;
+            }
+            x.code = c;
+            x.w = stream_carve(kModeFP32, x.mem, v.N, v.E, Fp, max_iter);
+            DecodeArgs& a = x.a;
+            a = DecodeArgs();
+            a.M = v.M;
+            a.N = v.N;
+            a.E = (int32_t)v.E;
+            a.frames = b->frames[c];
+            a.L = max_iter;
+            a.early_stop = early_stop ? 1 : 0;
+            a.check_every = 1;
+            a.paper_slicer = b->paper;
+            a.llr_is_i8 = 0;
+            a.llr = ra.llr;
+            a.out_bits = ra.out_bits;
+            a.out_iters = ra.out_iters;
+            a.out_ok = ra.out_ok;
+            a.out_soft = ra.out_soft;
+            keep.push_back(x);
+            continue;
+        }
         for (int32_t f = 0; f < b->frames[c]; f += b->desc[c].ft) tiles.push_back(Tile{c, f});
+    }
+    for (auto& old : b->streamed)
+        if (old.mem) {
+            cudaStreamSynchronize(b->side);
+            cudaFree(old.mem);
+        }
+    b->streamed = keep;
+    if (b->exec) {  // a recorded launch refers to the old work list: record again
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
     if ((int32_t)tiles.size() > b->tiles_cap) {
         if (b->d_tiles) cudaFree(b->d_tiles);
         b->d_tiles = nullptr;
@@ -277,9 +380,16 @@ int ldpc_batch_prepare(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
 
 int ldpc_batch_launch(ldpc_batch_t* b) {
     if (!b) return LDPC_ERR_BAD_POINTER;
-    const int rc = batch_enqueue(b);
-    b->last_launches = b->n_tiles ? 1 : 0;
-    return rc;
+    const int n = batch_enqueue(b);
+    b->last_launches = n < 0 ? 0 : n;
+    return n < 0 ? n : LDPC_OK;
+}
+
+int ldpc_batch_set_large_codes(ldpc_batch_t* b, int32_t streaming) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    if (streaming != 0 && streaming != 1) return LDPC_ERR_INVALID_ARG;
+    b->large_stream = streaming;
+    return LDPC_OK;  // takes effect at the next ldpc_batch_prepare
 }
 
 int ldpc_batch_decode(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
@@ -296,9 +406,10 @@ int ldpc_batch_capture(ldpc_batch_t* b) {
     }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LDPC_ERR_CUDA;
-    const int rc = batch_enqueue(b);
+    const int n = batch_enqueue(b);
     const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-    if (rc != LDPC_OK || e != cudaSuccess) {
+    if (n >= 0) b->captured_launches = n;
+    if (n < 0 || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
         return LDPC_ERR_CUDA;
@@ -316,7 +427,7 @@ int ldpc_batch_capture(ldpc_batch_t* b) {
 int ldpc_batch_replay(ldpc_batch_t* b) {
     if (!b) return LDPC_ERR_BAD_POINTER;
     if (!b->exec) return LDPC_ERR_INVALID_ARG;
-    b->last_launches = b->n_tiles ? 1 : 0;
+    b->last_launches = b->captured_launches;
     return cudaGraphLaunch(b->exec, b->stream) == cudaSuccess ? LDPC_OK : LDPC_ERR_CUDA;
 }
 
@@ -357,8 +468,8 @@ int ldpc_batch_autotune(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop, i
     for (int th = 256; th <= kMaxThreads; th += 128) {
         if (ldpc_batch_set_threads(b, th) != LDPC_OK) continue;
         float ms = 0.0f;
-        bool bad = batch_enqueue(b) != LDPC_OK || cudaEventRecord(e0, b->stream) != cudaSuccess;
-        for (int r = 0; r < 2 && !bad; r++) bad = batch_enqueue(b) != LDPC_OK;
+        bool bad = batch_enqueue(b) < 0 || cudaEventRecord(e0, b->stream) != cudaSuccess;
+        for (int r = 0; r < 2 && !bad; r++) bad = batch_enqueue(b) < 0;
         bad = bad || cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess;
         if (bad) {

@@ -168,6 +168,8 @@ struct StreamWork {
 int stream_decode(int mode, const DevGraph& dg, const DecodeArgs& a, const StreamWork& w,
                   cudaStream_t st, int vw = 0);
 size_t stream_bytes(int mode, int32_t N, int64_t E, int32_t Fp, int32_t L);
+// The workspace of stream_bytes(mode, N, E, Fp, L) bytes at mem (Fp a multiple of 256).
+StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t E, int32_t Fp, int32_t L);
 
 // Dense variant (the paper's m x n map-reduce form, a baseline): workspace bytes and launcher.
 size_t dense_bytes(int32_t M, int32_t N, int32_t frames);

@@ -170,13 +170,12 @@ __global__ void __launch_bounds__(128) k_check(const int32_t* __restrict__ row_p
                 const A lam = FIRST ? sa : lam_of(sa, (A)ev.x[v]);
                 const A a = absval(lam);
                 const uint32_t sg = lam < A(0);
-                if (a < min0[v]) {
-                    min1[v] = min0[v];
-                    min0[v] = a;
-                    loc[v] = t;
-                } else if (a < min1[v]) {
-                    min1[v] = a;
-                }
+                // Observation 1 without branches: a new minimum demotes min0 to min1 and
+                // records its location (the first one: ties do not move it)
+                const bool lt0 = a < min0[v];
+                min1[v] = lt0 ? min0[v] : min(min1[v], a);
+                min0[v] = lt0 ? a : min0[v];
+                loc[v] = lt0 ? t : loc[v];
                 neg ^= sg << v;
                 msk[v] |= (sg << (t & 31));
                 lv.x[v] = (T)lam;
@@ -392,6 +391,28 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
 size_t stream_bytes(int mode, int32_t N, int64_t E, int32_t Fp, int32_t L) {
     size_t tb = mode == kModeFP32 ? 4 : 2, rb = mode == kModeFP32 ? 4 : 1;
     return (size_t)E * Fp * tb + (size_t)N * Fp * (tb + rb) + (size_t)Fp * 5 + (size_t)(L + 2) * Fp + 256;
+}
+
+StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t E, int32_t Fp, int32_t L) {
+    // Fp is a multiple of 256, so every region below starts 256-byte aligned
+    const size_t tb = mode == kModeFP32 ? 4 : 2, rb = mode == kModeFP32 ? 4 : 1;
+    char* p = (char*)mem;
+    StreamWork w;
+    w.Fp = Fp;
+    w.eta = p;
+    p += (size_t)E * Fp * tb;
+    w.s = p;
+    p += (size_t)N * Fp * tb;
+    w.r = p;
+    p += (size_t)N * Fp * rb;
+    w.done_iter = (int32_t*)p;
+    p += (size_t)Fp * 4;
+    w.state = (uint8_t*)p;
+    p += (size_t)Fp;
+    w.unsat = (uint8_t*)p;
+    p += (size_t)(L + 2) * Fp;
+    w.n_done = (int32_t*)p;
+    return w;
 }
 
 int stream_decode(int mode, const DevGraph& g, const DecodeArgs& a, const StreamWork& w,

@@ -59,6 +59,7 @@ SIGNATURES = {
     "ldpc_batch_set_threads": (ctypes.c_int, [P, I32]),
     "ldpc_batch_autotune": (ctypes.c_int, [P, I32, I32, PI32, ctypes.POINTER(ctypes.c_float)]),
     "ldpc_batch_info": (ctypes.c_int, [P, PI32, PI32, PI32, PI32]),
+    "ldpc_batch_set_large_codes": (ctypes.c_int, [P, I32]),
     "ldpc_batch_destroy": (None, [P]),
     "ldpc_set_stream": (ctypes.c_int, [P, P]),
     "ldpc_set_mode": (ctypes.c_int, [P, I32]),
@@ -492,6 +493,11 @@ class Batch:
 
     def decode(self, max_iter, early_stop=True):
         _check(load().ldpc_batch_decode(self.b, max_iter, int(early_stop)), "ldpc_batch_decode")
+
+    def set_large_codes(self, streaming: bool):
+        """Codes too large for shared memory: streaming kernels (True) or the persistent
+        launch from global scratch (False); takes effect at the next prepare."""
+        _check(load().ldpc_batch_set_large_codes(self.b, int(streaming)), "ldpc_batch_set_large_codes")
 
     def capture(self):
         _check(load().ldpc_batch_capture(self.b), "ldpc_batch_capture")

@@ -36,12 +36,16 @@ def check_code(code, llr, out, L, label):
     np.testing.assert_allclose(soft, ws, rtol=1e-5, atol=0, err_msg=label)
 
 
-def test_batch_matches_oracle_and_graph_replay(torch_cuda):
+@pytest.mark.parametrize("large_streaming", [True, False])
+def test_batch_matches_oracle_and_graph_replay(torch_cuda, large_streaming):
+    """The code too large for shared memory goes through the streaming kernels on the
+    side stream (True) or the persistent launch's global scratch (False)."""
     torch = torch_cuda
     from paper_2507_10424_gb300.ldpc import Batch, Decoder
     codes, frames = mixed_small()
     decs = [Decoder.from_code(c) for c in codes]
     batch = Batch(decs)
+    batch.set_large_codes(large_streaming)
     L = 25
     ins, outs = [], []
     for k, (c, F) in enumerate(zip(codes, frames)):
@@ -52,7 +56,8 @@ def test_batch_matches_oracle_and_graph_replay(torch_cuda):
     batch.decode(L)
     batch.stream.synchronize()
     info = batch.info()
-    assert info["n_tiles"] >= sum(frames) // 4 and info["codes_in_shared_memory"] == 3
+    assert info["codes_in_shared_memory"] == 3
+    assert info["n_tiles"] >= (sum(frames[:3]) // 4 if large_streaming else sum(frames) // 4)
     for k, c in enumerate(codes):
         if frames[k]:
             check_code(c, ins[k][0], outs[k], L, f"code {k}")
