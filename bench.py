@@ -242,10 +242,72 @@ def other_workloads(timed):
                 "fer": float((o[0] != 0).any(dim=1).float().mean().item()),
                 "edge_message_GBs_at_mean_iter": F * float(it.mean().item()) * B / (ms * 1e-3) / 1e9}
             dec.close()
+    # the same large code with a frame tile held across a thread-block cluster's shared
+    # memory (never chosen automatically: measured slower than streaming)
+    code = inputs.cfg_irregular_64800()
+    F, L = 4096, 50
+    llr = torch.from_numpy(inputs.all_zero_awgn_llr(F, code.N, 1.0, code.design_rate, 17)).cuda()
+    for mode in ("fp32", "fixed"):
+        dec = Decoder.from_code(code, mode=mode)
+        dec.set_variant("cluster")
+        o = (torch.empty((F, code.N), dtype=torch.uint8, device="cuda"),
+             torch.empty(F, dtype=torch.int32, device="cuda"), None, None)
+        ms = timed(lambda: dec.decode(llr, L, early_stop=True, out=o), 3, 1)
+        C, FT, th, ncl = dec.cluster_shape()
+        out[f"irregular64800/{mode}/cluster"] = {
+            "variant": "cluster", "cluster_ctas": C, "frames_per_tile": FT, "threads": th,
+            "clusters": ncl, "frames": F, "ebn0_db": 1.0, "max_iter": L, "ms_per_call": ms,
+            "Gbit/s": F * code.N / (ms * 1e-3) / 1e9, "mean_iter": float(o[1].float().mean().item())}
+        dec.close()
     return out
 
 
 # ------------------------------------------------------------------ learned decoder
+
+def learned_vs_plain_large(timed):
+    """Learned normalised/offset Min-Sum on the irregular N=64800 code, one weight pair per
+    column degree (2, 3, 8) and iteration: trained here (20 unrolled iterations, 100 steps of
+    512 all-zero frames at Eb/N0 uniform in [0.8, 1.4] dB; the later iterations reuse the
+    last row), then FER and mean iterations of both decoders (streaming variant, 4096
+    frames, early stop) at 1.2 and 1.4 dB for iteration limits 30..50, and decoded Gbit/s of
+    both at equal FER at 1.4 dB (plain at 50 iterations, learned at its matching limit)."""
+    import torch
+    from paper_2507_10424_gb300 import inputs, learn
+    from paper_2507_10424_gb300.ldpc import Decoder
+    code = inputs.cfg_irregular_64800()
+    dec = Decoder.from_code(code)
+    t = time.perf_counter()
+    alpha, beta, losses = learn.train_weights(dec, code, iters=20, steps=100, batch=512,
+                                              ebn0=(0.8, 1.4), lr=0.02, seed=1, every=True,
+                                              encode=False)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t
+    limits = (30, 35, 40, 45, 50)
+    rows = learn.compare(dec, code, (alpha, beta), ebn0_points=(1.2, 1.4), frames=4096,
+                         iters=limits, encode=False)
+    match = {f"{e:.1f}dB": learn.iterations_to_match(rows, e, 50) for e in (1.2, 1.4)}
+    L_l = match["1.4dB"] or 50
+    src = learn.FrameSource(code, seed=11, encode=False)
+    llr, bits = src.batch(4096, 1.4)
+    out = (torch.empty_like(bits), torch.empty(4096, dtype=torch.int32, device="cuda"), None, None)
+    res = {}
+    for name, w, L in (("plain", None, 50), ("learned", (alpha, beta), L_l)):
+        dec.set_weights(*(w if w else (None,)))
+        ms = timed(lambda: dec.decode(llr, L, early_stop=True, out=out), 3, 1)
+        fer = float((out[0] != bits).any(dim=1).float().mean().item())
+        res[name] = {"max_iter": L, "ms_per_call": ms, "Gbit/s": 4096 * code.N / (ms * 1e-3) / 1e9,
+                     "fer": fer, "mean_iter": float(out[1].float().mean().item())}
+    dec.set_weights(None)
+    cls = dec.classes()
+    dec.close()
+    return {"code": "irregular N=64800 M=32400, column weights 2/3/8", "classes": cls,
+            "train_steps": 100, "train_s": train_s,
+            "loss_first_last": [float(np.mean(losses[:5])), float(np.mean(losses[-5:]))],
+            "alpha_first_last_iteration": [alpha[0].round(4).tolist(), alpha[-1].round(4).tolist()],
+            "beta_first_last_iteration": [beta[0].round(4).tolist(), beta[-1].round(4).tolist()],
+            "iterations_to_match_plain_fer_at_50": match, "equal_fer_throughput_1.4dB": res,
+            "fer_table": rows}
+
 
 def learned_vs_plain(timed):
     """Learned normalised/offset Min-Sum on the (3,6)-regular N=576 code: trained here
@@ -547,6 +609,7 @@ def main():
         if rank == 0:
             result["other_workloads"] = other_workloads(timed)
             result["learned"] = learned_vs_plain(timed)
+            result["learned_large"] = learned_vs_plain_large(timed)
             result["mixed_codes"] = mixed_codes(timed)
         if world == 1 and rank == 0:
             val, n, dt = oracle_rate(code, llr, L, mode)

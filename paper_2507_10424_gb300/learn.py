@@ -73,16 +73,24 @@ class WeightedMinSum:
 
 
 class FrameSource:
-    """Random codewords of a code, BPSK over AWGN, on the GPU (seeded)."""
+    """Random codewords of a code, BPSK over AWGN, on the GPU (seeded).
 
-    def __init__(self, code, device="cuda", seed=0):
+    encode=False sends the all-zero codeword instead (for codes too large for the GF(2)
+    encoder): Min-Sum, normalised or offset, is symmetric under BPSK over AWGN, so its
+    error rates and the expected loss do not depend on the codeword sent.
+    """
+
+    def __init__(self, code, device="cuda", seed=0, encode=True):
         import torch
         from . import inputs
-        enc = inputs.Encoder(code)
-        self.N, self.K, self.rate = code.N, enc.K, code.design_rate
-        self.P = torch.from_numpy(enc.P).to(device)                 # [rank][K]
-        self.free = torch.from_numpy(enc.free).to(device)
-        self.pivots = torch.from_numpy(enc.pivots).to(device)
+        self.N, self.rate = code.N, code.design_rate
+        self.encode = encode
+        if encode:
+            enc = inputs.Encoder(code)
+            self.K = enc.K
+            self.P = torch.from_numpy(enc.P).to(device)                 # [rank][K]
+            self.free = torch.from_numpy(enc.free).to(device)
+            self.pivots = torch.from_numpy(enc.pivots).to(device)
         self.device = device
         self.gen = torch.Generator(device=device)
         self.gen.manual_seed(seed)
@@ -90,11 +98,12 @@ class FrameSource:
     def batch(self, F, ebn0_db):
         """ebn0_db: a float, or (lo, hi) for a per-frame uniform draw. Returns (llr, bits)."""
         import torch
-        info = torch.randint(0, 2, (F, self.K), generator=self.gen, device=self.device,
-                             dtype=torch.float32)
         c = torch.zeros((F, self.N), device=self.device)
-        c[:, self.free] = info
-        c[:, self.pivots] = torch.remainder(info @ self.P.T, 2.0)
+        if self.encode:
+            info = torch.randint(0, 2, (F, self.K), generator=self.gen, device=self.device,
+                                 dtype=torch.float32)
+            c[:, self.free] = info
+            c[:, self.pivots] = torch.remainder(info @ self.P.T, 2.0)
         if isinstance(ebn0_db, tuple):
             e = torch.rand((F, 1), generator=self.gen, device=self.device) * (ebn0_db[1] - ebn0_db[0]) + ebn0_db[0]
         else:
@@ -106,7 +115,7 @@ class FrameSource:
 
 
 def train_weights(dec, code, iters=10, steps=300, batch=4096, ebn0=(1.0, 4.0), lr=0.02,
-                  seed=1, log_every=0, every=True):
+                  seed=1, log_every=0, every=True, encode=True):
     """Train alpha, beta [iters][n_classes] from plain Min-Sum (alpha = 1, beta = 0).
 
     every=True: the loss is the mean over iterations of the cross-entropy of that
@@ -118,7 +127,7 @@ def train_weights(dec, code, iters=10, steps=300, batch=4096, ebn0=(1.0, 4.0), l
     alpha = torch.ones((iters, C), device="cuda", requires_grad=True)
     beta = torch.zeros((iters, C), device="cuda", requires_grad=True)
     opt = torch.optim.Adam([alpha, beta], lr=lr)
-    src = FrameSource(code, seed=seed)
+    src = FrameSource(code, seed=seed, encode=encode)
     losses = []
     for step in range(steps):
         llr, bits = src.batch(batch, ebn0)
@@ -149,9 +158,9 @@ def frame_error_rate(dec, llr, bits, max_iter, weights=None):
 
 
 def compare(dec, code, weights, ebn0_points=(2.0, 2.5, 3.0), frames=20000,
-            iters=(5, 6, 7, 8, 9, 10, 12, 14, 16, 20), seed=7):
+            iters=(5, 6, 7, 8, 9, 10, 12, 14, 16, 20), seed=7, encode=True):
     """FER and mean iterations of plain and learned Min-Sum at several iteration limits."""
-    src = FrameSource(code, seed=seed)
+    src = FrameSource(code, seed=seed, encode=encode)
     rows = []
     for e in ebn0_points:
         llr, bits = src.batch(frames, float(e))
