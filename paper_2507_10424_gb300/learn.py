@@ -158,7 +158,7 @@ def frame_error_rate(dec, llr, bits, max_iter, weights=None):
 
 
 def compare(dec, code, weights, ebn0_points=(2.0, 2.5, 3.0), frames=20000,
-            iters=(5, 6, 7, 8, 9, 10, 12, 14, 16, 20), seed=7, encode=True):
+            iters=(5, 6, 7, 8, 9, 10, 11, 12, 14, 16, 20), seed=7, encode=True):
     """FER and mean iterations of plain and learned Min-Sum at several iteration limits."""
     src = FrameSource(code, seed=seed, encode=encode)
     rows = []
