@@ -49,6 +49,7 @@ typedef struct ldpc ldpc_t; /* opaque handle */
 #define LDPC_ERR_BAD_POINTER (-3)  /* NULL where required, or host memory where device memory is required */
 #define LDPC_ERR_OOM (-4)          /* device or host allocation failed */
 #define LDPC_ERR_CUDA (-5)         /* a CUDA runtime call failed; see ldpc_last_cuda_error */
+#define LDPC_ERR_TIMEOUT (-6)      /* a bounded wait inside a kernel ran out (ldpc_check_device) */
 #define LDPC_ERR_UNSUPPORTED (-8)  /* the request needs a feature this build or device lacks */
 
 /* Arithmetic modes. */
@@ -317,6 +318,43 @@ int ldpc_get_tuning(const ldpc_t *h, int32_t *frames_per_tile, int32_t *threads,
  * not depend on the grouping; small groups leave the GPU partly idle, which is why it is
  * off by default. Returns LDPC_ERR_INVALID_ARG for other values. */
 int ldpc_set_stream_group(ldpc_t *h, int32_t frames_per_group);
+
+/*
+ * ldpc_set_stream_staging: shape of the streaming variant's check pass for codes whose
+ * rows have at most 16 edges. Row i then owns 8 or 16 message slots (a padded row
+ * layout). Each warp of a persistent kernel keeps `stages` shared-memory stages in
+ * flight. Into each stage, the TMA engine's bulk asynchronous copies (cp.async.bulk)
+ * bring one row's gathered posteriors s_j and old messages for 32 x 4 (FP32) or 32 x 8
+ * (fixed point) frames, completing on an mbarrier, while the warp computes an earlier
+ * row (Section III's row reductions).
+ *   warps_per_cta in {0 (automatic: 8), 1..12};
+ *   stages in {-1 (off: one thread per row and frame vector loads its row itself),
+ *              0 (automatic: 3), 2..8}.
+ * Results do not depend on the shape. A shape whose shared memory does not fit the device
+ * falls back to the unstaged kernel. LDPC_ERR_INVALID_ARG for other values.
+ */
+int ldpc_set_stream_staging(ldpc_t *h, int32_t warps_per_cta, int32_t stages);
+
+/* ldpc_get_stream_staging: the staging in force (stages 0 when off). */
+int ldpc_get_stream_staging(const ldpc_t *h, int32_t *warps_per_cta, int32_t *stages);
+
+/*
+ * ldpc_check_device: waits for the handle's stream, then reads and clears the handle's
+ * device error word. That word covers this handle's decodes, including a batch's large
+ * codes, which run the streaming kernels on their code's handle. Returns LDPC_OK, or
+ * LDPC_ERR_TIMEOUT when a bounded wait inside a kernel ran out since the last check. The
+ * kernel then gave up its waits, let its own copies in flight land, and returned, so the
+ * outputs of that decode are not valid. LDPC_ERR_CUDA when the stream reports an error.
+ */
+int ldpc_check_device(ldpc_t *h);
+
+/*
+ * ldpc_set_wait_limit: tries of each bounded wait in the staged kernels. One try waits at
+ * most about 20 microseconds. The default 65536 bounds a wait near 1.3 s, far above any
+ * real copy. A limit of 0 makes every wait give up at once, which is how the tests check
+ * the timeout path without a fault. tries must be >= 0, else LDPC_ERR_INVALID_ARG.
+ */
+int ldpc_set_wait_limit(ldpc_t *h, int32_t tries);
 
 /*
  * ldpc_set_cluster_shape: launch shape of the cluster variant (0 = automatic for each field).

@@ -74,7 +74,12 @@ struct ldpc {
     size_t dense_cap = 0;
     int32_t stream_group = -1;   // streaming: -1 no frame groups, 0 L2-sized groups, > 0 group size
     int l2_bytes = 0;
-    int32_t* counters = nullptr;  // [0] resident / cluster tile counter, [1] streaming done count
+    int32_t* counters = nullptr;  // [0] resident / cluster tile counter, [1] streaming done
+                                  // count, [2] device error word (bounded waits that ran out)
+    // staged streaming check pass: requested warps per CTA and stages (0 = automatic,
+    // stages -1 = off) and the tries of each bounded wait
+    int32_t st_warps = 0, st_stages = 0;
+    uint32_t wait_limit = 1u << 16;
     // cluster variant: layouts built on demand from the host graph, one per cluster size
     // 2^i; plans per mode, recomputed after any change of tuning or weights
     HostGraph hg;
@@ -94,7 +99,7 @@ struct ldpc {
 static void free_graph(DevGraph& g) {
     void* ptrs[] = {g.row_ptr, g.col_idx, g.col_ptr, g.col_edge, g.packed, g.r_base,
                     g.r_deg, g.r_slot_pos, g.c_base, g.c_deg, g.c_slot, g.col_pos,
-                    g.col_class, g.r_slot_cls};
+                    g.col_class, g.r_slot_cls, g.ell_col, g.ell_deg, g.ell_cslot};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     g = DevGraph();
@@ -120,6 +125,15 @@ static void free_stream_work(ldpc_t* h) {
 // Largest batch of one streaming decode (its grids put frame blocks on the y dimension).
 constexpr int32_t kMaxStreamFrames = 65535 * 32;
 
+// The staged check pass settings of a handle, applied to a streaming workspace.
+static void apply_staging(const ldpc_t* h, StreamWork& w) {
+    w.err = h->counters + 2;
+    w.num_sms = h->num_sms;
+    w.stage_warps = h->st_warps > 0 ? h->st_warps : kStageWarpsDefault;
+    w.stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
+    w.wait_limit = h->wait_limit;
+}
+
 static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L, int32_t granule = 256) {
     if (frames > kMaxStreamFrames) return fail(LDPC_ERR_INVALID_ARG);
     const int32_t Fp = (frames + granule - 1) / granule * granule;
@@ -130,7 +144,7 @@ static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L, int32_t gran
             h->sw_big = nullptr;
         }
         const size_t tb = 4, rb = 4;  // sized for fp32; the fixed mode uses less
-        const size_t eta = (size_t)h->E * Fp * tb, sb = (size_t)h->N * Fp * tb,
+        const size_t eta = (size_t)h->dg.eta_slots * Fp * tb, sb = (size_t)h->N * Fp * tb,
                      rr = (size_t)h->N * Fp * rb;
         const size_t total = eta + sb + rr + (size_t)Fp * 4 + (size_t)Fp + 1024;
         cudaError_t e = cudaMalloc(&h->sw_big, total);
@@ -169,6 +183,7 @@ static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L, int32_t gran
     h->sw.Fp = Fp;
     h->sw.unsat = h->sw_unsat;
     h->sw.n_done = h->counters + 1;
+    apply_staging(h, h->sw);
     return LDPC_OK;
 }
 
@@ -284,6 +299,19 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
         (rc = upload(&h->dg.col_edge, hg.col_edge.data(), hg.col_edge.size())))
         return bail(rc);
     h->dg.max_dc = hg.max_dc;
+    h->dg.eta_slots = hg.E;
+    // padded row layout of the streaming kernels (rows of at most 16 edges)
+    {
+        EllGraph eg;
+        if (build_ell(hg, eg)) {
+            if ((rc = upload(&h->dg.ell_col, eg.ell_col.data(), eg.ell_col.size())) ||
+                (rc = upload(&h->dg.ell_deg, eg.ell_deg.data(), eg.ell_deg.size())) ||
+                (rc = upload(&h->dg.ell_cslot, eg.ell_cslot.data(), eg.ell_cslot.size())))
+                return bail(rc);
+            h->dg.ell_D = eg.D;
+            h->dg.eta_slots = (int64_t)hg.M * eg.D;
+        }
+    }
     // edge classes (learned weights)
     h->class_degree = hg.class_degree;
     h->dg.n_classes = (int32_t)hg.class_degree.size();
@@ -321,6 +349,8 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
     }
     e = cudaMalloc((void**)&h->counters, 4 * sizeof(int32_t));
     if (e != cudaSuccess) return bail(alloc_fail(e));
+    e = cudaMemset(h->counters, 0, 4 * sizeof(int32_t));
+    if (e != cudaSuccess) return bail(cuda_fail(e));
     h->hg = std::move(hg);
     g_last_error = LDPC_OK;
     return h;
@@ -330,8 +360,14 @@ int ldpc_impl::handle_view(ldpc_t* h, HandleView* v) {
     if (!h || !v) return LDPC_ERR_BAD_POINTER;
     *v = HandleView{h->device, h->mode, h->flags, h->M, h->N, h->E, &h->dg, h->stream,
                     &h->last_launches, h->w_rows, h->w_alpha};
+    v->num_sms = h->num_sms;
+    v->err = h->counters + 2;
+    v->stage_warps = h->st_warps > 0 ? h->st_warps : kStageWarpsDefault;
+    v->stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
+    v->wait_limit = h->wait_limit;
     return LDPC_OK;
 }
+
 
 extern "C" {
 
@@ -727,6 +763,44 @@ int ldpc_set_stream_group(ldpc_t* h, int32_t frames_per_group) {
     return LDPC_OK;
 }
 
+int ldpc_set_stream_staging(ldpc_t* h, int32_t warps_per_cta, int32_t stages) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (warps_per_cta < 0 || warps_per_cta > 12 || stages < -1 || stages == 1 || stages > 8)
+        return fail(LDPC_ERR_INVALID_ARG);
+    h->st_warps = warps_per_cta;
+    h->st_stages = stages;
+    apply_staging(h, h->sw);
+    return LDPC_OK;
+}
+
+int ldpc_get_stream_staging(const ldpc_t* h, int32_t* warps_per_cta, int32_t* stages) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (warps_per_cta) *warps_per_cta = h->st_warps > 0 ? h->st_warps : kStageWarpsDefault;
+    if (stages) *stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
+    return LDPC_OK;
+}
+
+int ldpc_check_device(ldpc_t* h) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int32_t word = 0;
+    e = cudaMemcpy(&word, h->counters + 2, sizeof(word), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (word == 0) return LDPC_OK;
+    e = cudaMemset(h->counters + 2, 0, sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e);
+    return fail(LDPC_ERR_TIMEOUT);
+}
+
+int ldpc_set_wait_limit(ldpc_t* h, int32_t tries) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (tries < 0) return fail(LDPC_ERR_INVALID_ARG);
+    h->wait_limit = (uint32_t)tries;
+    apply_staging(h, h->sw);
+    return LDPC_OK;
+}
+
 int ldpc_set_cluster_shape(ldpc_t* h, int32_t cluster_size, int32_t frames_per_tile, int32_t threads) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
     const bool c_ok = cluster_size == 0 || cluster_size == 1 || cluster_size == 2 || cluster_size == 4 ||
@@ -803,6 +877,7 @@ const char* ldpc_strerror(int status) {
         case LDPC_ERR_BAD_POINTER: return "bad pointer (NULL, or host memory where device memory is required)";
         case LDPC_ERR_OOM: return "out of memory";
         case LDPC_ERR_CUDA: return "CUDA runtime error";
+        case LDPC_ERR_TIMEOUT: return "a bounded wait inside a kernel ran out";
         case LDPC_ERR_UNSUPPORTED: return "unsupported for this code or device";
     }
     return "unknown status";

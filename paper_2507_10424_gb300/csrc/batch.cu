@@ -312,7 +312,7 @@ int ldpc_batch_prepare(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
             const ResArgs& ra = b->desc[c].a;
             const HandleView& v = b->views[c];
             const int32_t Fp = (b->frames[c] + 255) & ~255;
-            const size_t need = stream_bytes(kModeFP32, v.N, v.E, Fp, max_iter);
+            const size_t need = stream_bytes(kModeFP32, v.N, v.dg->eta_slots, Fp, max_iter);
             if (need > x.bytes) {
                 if (x.mem) {
                     cudaStreamSynchronize(b->side);
@@ -328,7 +328,12 @@ int ldpc_batch_prepare(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
                 x.bytes = need;
             }
             x.code = c;
-            x.w = stream_carve(kModeFP32, x.mem, v.N, v.E, Fp, max_iter);
+            x.w = stream_carve(kModeFP32, x.mem, v.N, v.dg->eta_slots, Fp, max_iter);
+            x.w.err = v.err;  // the code handle's device error word (ldpc_check_device)
+            x.w.num_sms = v.num_sms;
+            x.w.stage_warps = v.stage_warps;
+            x.w.stages = v.stages;
+            x.w.wait_limit = v.wait_limit;
             DecodeArgs& a = x.a;
             a = DecodeArgs();
             a.M = v.M;

@@ -280,4 +280,24 @@ bool build_cluster(const HostGraph& g, int C, ClusterGraph& cg) {
     return true;
 }
 
+bool build_ell(const HostGraph& g, EllGraph& eg) {
+    if (g.max_dc > 16) return false;
+    const int32_t D = g.max_dc <= 8 ? 8 : 16;
+    eg.D = D;
+    eg.ell_col.assign((size_t)g.M * D, 0);
+    eg.ell_deg.assign(g.M, 0);
+    std::vector<int64_t> slot_of_edge(g.E);
+    for (int32_t i = 0; i < g.M; i++) {
+        const int32_t e0 = g.row_ptr[i], d = g.row_ptr[i + 1] - e0;
+        eg.ell_deg[i] = (uint8_t)d;
+        for (int32_t t = 0; t < D; t++)  // padding: the row's first column (column 0 if empty)
+            eg.ell_col[(size_t)i * D + t] = d == 0 ? 0 : g.col_idx[e0 + (t < d ? t : 0)];
+        for (int32_t t = 0; t < d; t++) slot_of_edge[e0 + t] = (int64_t)i * D + t;
+    }
+    if ((int64_t)g.M * D >= (int64_t)INT32_MAX) return false;
+    eg.ell_cslot.resize(g.E);
+    for (int64_t q = 0; q < g.E; q++) eg.ell_cslot[q] = (int32_t)slot_of_edge[g.col_edge[q]];
+    return true;
+}
+
 }  // namespace ldpc_impl

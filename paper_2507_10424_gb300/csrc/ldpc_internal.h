@@ -64,6 +64,23 @@ struct SlicedGraph {
 bool build_sliced(const HostGraph& g, SlicedGraph& sg);
 
 // ---------------------------------------------------------------------------------------
+// Padded row layout of the streaming kernels (codes whose rows have at most 16 edges):
+// every row owns D = 8 or 16 message slots, the t-th edge of row i at slot i D + t, so a
+// row's columns and messages sit at known offsets and load without a row-pointer lookup.
+//   ell_col[i D + t]  column of the t-th edge (t < deg(i)); padding repeats a valid column
+//   ell_deg[i]        deg(i)
+//   ell_cslot[q]      slot of the q-th edge of the CSC order (ascending rows per column)
+// ---------------------------------------------------------------------------------------
+struct EllGraph {
+    int32_t D = 0;
+    std::vector<int32_t> ell_col;
+    std::vector<uint8_t> ell_deg;
+    std::vector<int32_t> ell_cslot;
+};
+// Returns false when a row has more than 16 edges (the layout is then not used).
+bool build_ell(const HostGraph& g, EllGraph& eg);
+
+// ---------------------------------------------------------------------------------------
 // Cluster layout: the C CTAs of a thread-block cluster share a tile of frames. CTA (rank)
 // q owns a contiguous range of rows and one of columns, each cut at about E q / C edges,
 // and lays them out like the sliced layout above: the messages of its rows and the
@@ -125,6 +142,13 @@ struct DevGraph {
     int32_t n_rslices = 0, n_cslices = 0, E_pad = 0, Ec_pad = 0;
     int32_t sliced = 0;  // the sliced layout exists
     int32_t max_dc = 0;  // longest row (set for every code)
+    // padded row layout (streaming kernels); ell_D = 0 when absent
+    int32_t* ell_col = nullptr;
+    uint8_t* ell_deg = nullptr;
+    int32_t* ell_cslot = nullptr;
+    int32_t ell_D = 0;
+    // message slots of the streaming workspace: M ell_D with the padded layout, else E
+    int64_t eta_slots = 0;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -155,21 +179,31 @@ struct StreamWork {
     int32_t Fp = 0;
     void* r = nullptr;         // [N][Fp] float / int8
     void* s = nullptr;         // [N][Fp] float / int16
-    void* eta = nullptr;       // [E][Fp] float / int16
+    void* eta = nullptr;       // [eta_slots][Fp] float / int16
     int32_t* done_iter = nullptr;  // [Fp]: iteration at which the frame stopped, -1 while running
     uint8_t* state = nullptr;      // [Fp]: 1 while the frame is being decoded
     uint8_t* unsat = nullptr;      // [(L+2)][Fp]
     int32_t* n_done = nullptr;     // [1]
+    // staged check pass (padded row layout only): warps per CTA and shared-memory stages
+    // per warp, 0 stages = the register kernel; err: device error word (kernels set it,
+    // the host reads and clears it); wait_limit: tries of each bounded wait
+    int32_t* err = nullptr;
+    int32_t stage_warps = 0, stages = 0;
+    uint32_t wait_limit = 1u << 16;
+    int32_t num_sms = 0;
 };
+// Default staging of the streaming check pass (the shape chosen on GB300).
+constexpr int32_t kStageWarpsDefault = 8, kStagesDefault = 3;
 
 // Launchers; return the number of kernels enqueued, or a negative status.
 // vw: frames per lane (0: a 16-byte vector, 4 fp32 / 8 int16; else 1, 2, 4 or 8 with the
 // frame stride w.Fp a multiple of 32 vw)
 int stream_decode(int mode, const DevGraph& dg, const DecodeArgs& a, const StreamWork& w,
                   cudaStream_t st, int vw = 0);
-size_t stream_bytes(int mode, int32_t N, int64_t E, int32_t Fp, int32_t L);
-// The workspace of stream_bytes(mode, N, E, Fp, L) bytes at mem (Fp a multiple of 256).
-StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t E, int32_t Fp, int32_t L);
+// slots: the graph's eta_slots (message slots per frame).
+size_t stream_bytes(int mode, int32_t N, int64_t slots, int32_t Fp, int32_t L);
+// The workspace of stream_bytes(mode, N, slots, Fp, L) bytes at mem (Fp a multiple of 256).
+StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t slots, int32_t Fp, int32_t L);
 
 // Dense variant (the paper's m x n map-reduce form, a baseline): workspace bytes and launcher.
 size_t dense_bytes(int32_t M, int32_t N, int32_t frames);
@@ -216,6 +250,10 @@ struct HandleView {
     int32_t* last_launches;
     int32_t w_rows;          // learned weights in force (FP32 mode), 0 if none
     const float* w_alpha;    // device [w_rows][n_classes], beta follows
+    int32_t num_sms = 0;
+    int32_t* err = nullptr;  // device error word of the handle
+    int32_t stage_warps = 0, stages = 0;  // staged streaming check pass (stages 0 = off)
+    uint32_t wait_limit = 0;
 };
 int handle_view(::ldpc_t* h, HandleView* v);
 

@@ -76,7 +76,7 @@ extern "C" int ldpc_decode_noalloc(ldpc_t* h, const void* llr, int32_t llr_dtype
     const int32_t Fp = (frames + 255) & ~255;
     const size_t tb = v.mode == kModeFP32 ? 4 : 2, rb = v.mode == kModeFP32 ? 4 : 1;
     const size_t o_eta = 0;
-    const size_t o_s = o_eta + al256((size_t)v.E * Fp * tb);
+    const size_t o_s = o_eta + al256((size_t)v.dg->eta_slots * Fp * tb);
     const size_t o_r = o_s + al256((size_t)v.N * Fp * tb);
     const size_t o_done = o_r + al256((size_t)v.N * Fp * rb);
     const size_t o_state = o_done + al256((size_t)Fp * 4);
@@ -96,6 +96,11 @@ extern "C" int ldpc_decode_noalloc(ldpc_t* h, const void* llr, int32_t llr_dtype
     w.state = (uint8_t*)(base + o_state);
     w.unsat = (uint8_t*)(base + o_unsat);
     w.n_done = (int32_t*)(base + o_count);
+    w.err = v.err;  // the handle's device error word (ldpc_check_device)
+    w.num_sms = v.num_sms;
+    w.stage_warps = v.stage_warps;
+    w.stages = v.stages;
+    w.wait_limit = v.wait_limit;
     DecodeArgs a;
     a.M = v.M;
     a.N = v.N;

@@ -1,0 +1,41 @@
+// Packed 16-bit integer helpers of the fixed-point mode: the int16 values of two frames
+// share a 32-bit word (the even frame in the low half, the odd frame in the high half) and
+// one instruction treats both. Every helper is exact on values in [-32767, 32767].
+#pragma once
+
+#include <stdint.h>
+
+namespace ldpc_impl {
+
+template <int P>
+struct alignas(4 * P) Words {
+    uint32_t w[P];
+};
+__device__ __forceinline__ uint32_t p_min(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t p_max(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t p_add(uint32_t a, uint32_t b) {  // lane-wise, wrapping
+    uint32_t d;
+    asm("add.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t p_neg(uint32_t a) { return p_add(~a, 0x00010001u); }
+__device__ __forceinline__ int32_t p_lo(uint32_t w) { return (int32_t)(int16_t)(w & 0xffffu); }
+__device__ __forceinline__ int32_t p_hi(uint32_t w) { return (int32_t)w >> 16; }
+// Both lanes saturated to [-32767, 32767] and packed (lo in the low half).
+__device__ __forceinline__ uint32_t p_pack_sat(int32_t lo, int32_t hi) {
+    uint32_t d;
+    asm("cvt.pack.sat.s16.s32 %0, %1, %2;" : "=r"(d) : "r"(hi), "r"(lo));
+    return p_max(d, 0x80018001u);
+}
+// Lanes of all ones where bit 0 / bit 16 of b01 is set (b01 has no other bits).
+__device__ __forceinline__ uint32_t p_spread(uint32_t b01) { return b01 * 0xffffu; }
+
+}  // namespace ldpc_impl

@@ -28,6 +28,7 @@
 
 #include "../../include/ldpc.h"
 #include "ldpc_internal.h"
+#include "packed16.cuh"
 
 namespace ldpc_impl {
 namespace resident {
@@ -278,36 +279,7 @@ __device__ __forceinline__ void phase_a(const Idx& ix, VecR<typename RT<MODE>::T
 //            min(|lambda| - min0, 1) is 0 there and 1 elsewhere), conditional negation
 //            by (m ^ mask) + (mask & 1) with the lane mask of the new sign.
 // ---------------------------------------------------------------------------------------
-template <int P>
-struct alignas(4 * P) Words {
-    uint32_t w[P];
-};
-__device__ __forceinline__ uint32_t p_min(uint32_t a, uint32_t b) {
-    uint32_t d;
-    asm("min.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-__device__ __forceinline__ uint32_t p_max(uint32_t a, uint32_t b) {
-    uint32_t d;
-    asm("max.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-__device__ __forceinline__ uint32_t p_add(uint32_t a, uint32_t b) {  // lane-wise, wrapping
-    uint32_t d;
-    asm("add.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-__device__ __forceinline__ uint32_t p_neg(uint32_t a) { return p_add(~a, 0x00010001u); }
-__device__ __forceinline__ int32_t p_lo(uint32_t w) { return (int32_t)(int16_t)(w & 0xffffu); }
-__device__ __forceinline__ int32_t p_hi(uint32_t w) { return (int32_t)w >> 16; }
-// Both lanes saturated to [-32767, 32767] and packed (lo in the low half).
-__device__ __forceinline__ uint32_t p_pack_sat(int32_t lo, int32_t hi) {
-    uint32_t d;
-    asm("cvt.pack.sat.s16.s32 %0, %1, %2;" : "=r"(d) : "r"(hi), "r"(lo));
-    return p_max(d, 0x80018001u);
-}
-// Lanes of all ones where bit 0 / bit 16 of b01 is set (b01 has no other bits).
-__device__ __forceinline__ uint32_t p_spread(uint32_t b01) { return b01 * 0xffffu; }
+
 
 template <int FT, bool FIRST, bool SYN, bool UPD, bool PAPER>
 __device__ __forceinline__ void phase_a_packed(const Idx& ix, VecR<int16_t, FT>* eta_v,

@@ -1,7 +1,9 @@
 // Streaming variant: edge messages eta live in HBM in a frame-interleaved
-// structure-of-arrays layout, element (edge e, frame f) at e * Fp + f. A thread owns V
-// consecutive frames (one 16-byte vector: 4 x fp32 or 8 x int16) of one row or column,
-// so each warp moves 512 contiguous bytes per edge whatever the structure of H.
+// structure-of-arrays layout, element (message slot e, frame f) at e * Fp + f. The slots
+// are the padded row layout's (row i owns slots i D .. i D + D - 1) when every row has at
+// most 16 edges, else the CSR edge ids. A thread owns V consecutive frames (one 16-byte
+// vector: 4 x fp32 or 8 x int16) of one row or column, so each warp moves 512 contiguous
+// bytes per edge whatever the structure of H.
 //
 // Per flooding iteration k (Algorithm 1):
 //   k_check: for every check i and frame: lambda_e = s_j - eta_e (eq. eta_update with
@@ -14,6 +16,10 @@
 // A final syndrome-only pass gives the status of frames that never stopped early.
 #include "../../include/ldpc.h"
 #include "ldpc_internal.h"
+#include "packed16.cuh"
+
+#include <algorithm>
+#include <type_traits>
 
 namespace ldpc_impl {
 namespace {
@@ -94,9 +100,9 @@ __global__ void k_load(const void* llr, int llr_i8, int frames, int N, typename 
         if (j < N && f < Fp) {
             float v = tile[threadIdx.x][y];
             size_t idx = (size_t)j * Fp + f;
-            if (MODE == kModeFP32) {
-                r[idx] = (R)v;
-                s[idx] = (T)v;
+            if (MODE == kModeFP32) {  // "+ 0.0f" turns -0.0 into +0.0, no other value
+                r[idx] = (R)(v + 0.0f);
+                s[idx] = (T)(v + 0.0f);
             } else {
                 int8_t q = llr_i8 ? (int8_t)v : quantize(v);
                 r[idx] = (R)q;
@@ -219,6 +225,486 @@ __global__ void __launch_bounds__(128) k_check(const int32_t* __restrict__ row_p
 }
 
 // ------------------------------------------------------------------------------------
+// Check-node pass on the padded row layout (rows of at most D edges; same block and lane
+// mapping as k_check). Row i's columns and messages sit at slots i D .. i D + D - 1, so
+// every load but the gather of s is issued at entry: the frame state, the degree and the
+// columns together, then the old messages and the gathered s of the whole row, and only
+// then the arithmetic. lambda stays in registers between the two sweeps; the new magnitude
+// is min1 where |lambda| = min0 (Observation 1: on a tie min1 = min0, so the first
+// location needs no tracking) and the sign is the XOR of the row's sign bits with the
+// edge's own (Observation 2).
+// Sign bits are read directly: FP32 s never holds -0.0 (k_load adds +0.0, and round-to-
+// nearest sums and differences of values other than -0.0 are never -0.0), so the sign bit
+// of lambda and of s is [v < 0]; the same holds for int32. Fixed point with an even
+// number of frames per lane works on packed int16 pairs, exactly as per frame.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t sbits(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ uint32_t sbits(int32_t x) { return (uint32_t)x; }
+__device__ __forceinline__ float signed_mag(float m, uint32_t sgn) {  // m >= 0
+    return __uint_as_float(__float_as_uint(m) | (sgn & 0x80000000u));
+}
+__device__ __forceinline__ int32_t signed_mag(int32_t m, uint32_t sgn) { return (int32_t)sgn < 0 ? -m : m; }
+
+// Read-only (non-coherent) load of a 2-, 4-, 8- or 16-byte vector.
+template <typename VT>
+__device__ __forceinline__ VT ld_nc(const VT* p) {
+    VT v;
+    if constexpr (sizeof(VT) == 16) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4*>(p));
+        memcpy(&v, &x, 16);
+    } else if constexpr (sizeof(VT) == 8) {
+        const uint2 x = __ldg(reinterpret_cast<const uint2*>(p));
+        memcpy(&v, &x, 8);
+    } else if constexpr (sizeof(VT) == 4) {
+        const unsigned int x = __ldg(reinterpret_cast<const unsigned int*>(p));
+        memcpy(&v, &x, 4);
+    } else {
+        static_assert(sizeof(VT) == 2, "2-, 4-, 8- or 16-byte vectors");
+        const unsigned short x = __ldg(reinterpret_cast<const unsigned short*>(p));
+        memcpy(&v, &x, 2);
+    }
+    return v;
+}
+
+template <int MODE, int VW>
+struct RowVec {  // per-frame values
+    using VT = Vec<typename Tr<MODE>::T, VW>;
+    static constexpr bool kPacked = false;
+};
+template <int VW>
+struct RowVec<kModeFixed, VW> {
+    static constexpr bool kPacked = VW % 2 == 0;  // int16 pairs in 32-bit words
+    using VT = typename std::conditional<kPacked, Words<(VW + 1) / 2>, Vec<int16_t, VW>>::type;
+};
+
+// Operands of a row update held in registers: sv[t], ev[t] = the gathered s and the old
+// message of edge t; lambda replaces s in sv.
+template <typename VT, int D>
+struct RegRow {
+    VT sv[D], ev[D];
+    const int* cols;
+    __device__ __forceinline__ VT s(int t) const { return sv[t]; }
+    __device__ __forceinline__ VT e(int t) const { return ev[t]; }
+    __device__ __forceinline__ void keep(int t, const VT& l) { sv[t] = l; }
+    __device__ __forceinline__ VT lam(int t) const { return sv[t]; }
+    __device__ __forceinline__ int col(int t) const { return cols[t]; }
+};
+// Operands in a shared-memory stage: chunk t holds s of edge t (lambda replaces it),
+// chunk D + t the old message; this lane's vector sits at byte lane sizeof(VT).
+template <typename VT, int D>
+struct SmemRow {
+    unsigned char* st;
+    int chunk, lane;
+    const int* cols;
+    __device__ __forceinline__ VT* at(int c) const {
+        return reinterpret_cast<VT*>(st + (size_t)c * chunk + (size_t)lane * sizeof(VT));
+    }
+    __device__ __forceinline__ VT s(int t) const { return *at(t); }
+    __device__ __forceinline__ VT e(int t) const { return *at(D + t); }
+    __device__ __forceinline__ void keep(int t, const VT& l) { *at(t) = l; }
+    __device__ __forceinline__ VT lam(int t) const { return *at(t); }
+    __device__ __forceinline__ int col(int t) const { return cols[t]; }
+};
+
+// The row update of one lane's VW frames over the d <= D edges of a row (Observation 1:
+// min0, min1; Observation 2: XOR of sign bits): writes the new messages to erow + t Fp
+// and returns the syndrome bits of the gathered s (bit v for frame v) when SYN.
+template <int MODE, bool FIRST, bool SYN, bool PAPER, bool W, int VW, int D, class Row>
+__device__ __forceinline__ uint32_t row_update(Row& row, int d, typename Tr<MODE>::T* erow, int Fp,
+                                               const IterWeights& wt) {
+    using T = typename Tr<MODE>::T;
+    using A = typename Tr<MODE>::A;
+    using RV = RowVec<MODE, VW>;
+    using VT = typename RV::VT;
+    uint32_t z = 0;
+    if constexpr (!RV::kPacked) {
+        A min0[VW], min1[VW];
+        uint32_t sx[VW], zx[VW];
+#pragma unroll
+        for (int v = 0; v < VW; v++) {
+            min0[v] = big(A());
+            min1[v] = big(A());
+            sx[v] = 0;
+            zx[v] = 0;
+        }
+#pragma unroll
+        for (int t = 0; t < D; t++)
+            if (t < d) {
+                const VT sv = row.s(t);
+                VT ev;
+                if (!FIRST) ev = row.e(t);
+                VT lv;
+#pragma unroll
+                for (int v = 0; v < VW; v++) {
+                    const A sa = (A)sv.x[v];
+                    if (SYN) zx[v] ^= PAPER ? sbits(A(0) - sa) : sbits(sa);
+                    const A l = FIRST ? sa : lam_of(sa, (A)ev.x[v]);
+                    const A m = absval(l);
+                    min1[v] = min(min1[v], max(min0[v], m));
+                    min0[v] = min(min0[v], m);
+                    sx[v] ^= sbits(l);
+                    lv.x[v] = (T)l;  // exact: lambda is saturated to the storage range
+                }
+                row.keep(t, lv);
+            }
+        if (SYN) {
+#pragma unroll
+            for (int v = 0; v < VW; v++) z |= (zx[v] >> 31) << v;
+        }
+#pragma unroll
+        for (int t = 0; t < D; t++)
+            if (t < d) {
+                float wa = 1.0f, wb = 0.0f;
+                if constexpr (W) {
+                    const int cls = __ldg(wt.col_class + row.col(t));
+                    wa = __ldg(wt.alpha + cls);
+                    wb = __ldg(wt.beta + cls);
+                }
+                const VT lv = row.lam(t);
+                VT out;
+#pragma unroll
+                for (int v = 0; v < VW; v++) {
+                    const A l = (A)lv.x[v];
+                    A m = absval(l) == min0[v] ? min1[v] : min0[v];
+                    if constexpr (W) {  // max(fma(alpha, m, -beta), 0)
+                        const float x = __fmaf_rn(wa, (float)m, -wb);
+                        m = (A)(x > 0.0f ? x : 0.0f);
+                    }
+                    out.x[v] = (T)signed_mag(m, sbits(l) ^ sx[v]);
+                }
+                *reinterpret_cast<VT*>(erow + (size_t)t * Fp) = out;
+            }
+    } else {
+        constexpr int P = VW / 2;
+        uint32_t min0[P], min1[P], sx[P], zx[P];
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            min0[p] = 0x7fff7fffu;
+            min1[p] = 0x7fff7fffu;
+            sx[p] = 0;
+            zx[p] = 0;
+        }
+#pragma unroll
+        for (int t = 0; t < D; t++)
+            if (t < d) {
+                const VT sv = row.s(t);
+                VT ev;
+                if (!FIRST) ev = row.e(t);
+                VT lv;
+#pragma unroll
+                for (int p = 0; p < P; p++) {
+                    const uint32_t sw = sv.w[p];
+                    if (SYN) zx[p] ^= PAPER ? p_neg(sw) : sw;
+                    const uint32_t l =
+                        FIRST ? sw : p_pack_sat(p_lo(sw) - p_lo(ev.w[p]), p_hi(sw) - p_hi(ev.w[p]));
+                    const uint32_t m = p_max(l, p_neg(l));
+                    min1[p] = p_min(min1[p], p_max(min0[p], m));
+                    min0[p] = p_min(min0[p], m);
+                    sx[p] ^= l;
+                    lv.w[p] = l;
+                }
+                row.keep(t, lv);
+            }
+        if (SYN) {
+#pragma unroll
+            for (int p = 0; p < P; p++) z |= (((zx[p] >> 15) & 1u) | ((zx[p] >> 30) & 2u)) << (2 * p);
+        }
+        uint32_t nmin0[P];
+#pragma unroll
+        for (int p = 0; p < P; p++) nmin0[p] = p_neg(min0[p]);
+#pragma unroll
+        for (int t = 0; t < D; t++)
+            if (t < d) {
+                const VT lv = row.lam(t);
+                VT out;
+#pragma unroll
+                for (int p = 0; p < P; p++) {
+                    const uint32_t l = lv.w[p];
+                    const uint32_t a = p_max(l, p_neg(l));
+                    // lanes where |lambda| != min0 take min0, the others min1
+                    const uint32_t ne = p_spread(p_min(p_add(a, nmin0[p]), 0x00010001u));
+                    const uint32_t m = (min0[p] & ne) | (min1[p] & ~ne);
+                    const uint32_t sb = ((l ^ sx[p]) >> 15) & 0x00010001u;
+                    out.w[p] = p_add(m ^ p_spread(sb), sb);
+                }
+                *reinterpret_cast<VT*>(erow + (size_t)t * Fp) = out;
+            }
+    }
+    return z;
+}
+
+template <int MODE, bool FIRST, bool W, int VW, int D>
+__global__ void __launch_bounds__(128, D <= 8 ? 4 : 2)
+    k_check_ell(const int32_t* __restrict__ ell_col, const uint8_t* __restrict__ ell_deg, int M,
+                const typename Tr<MODE>::T* __restrict__ s, typename Tr<MODE>::T* __restrict__ eta,
+                int Fp, const uint8_t* __restrict__ state, uint8_t* __restrict__ unsat, int do_syn,
+                int paper, IterWeights wt = IterWeights()) {
+    using T = typename Tr<MODE>::T;
+    using VT = typename RowVec<MODE, VW>::VT;
+    using VS = Vec<uint8_t, VW>;
+    static_assert(sizeof(VT) == sizeof(T) * VW, "one vector = VW frames");
+    static_assert(D % 4 == 0, "columns load as 16-byte vectors");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 4 + warp;
+    const int f0 = (blockIdx.y * 32 + lane) * VW;
+    if (i >= M) return;
+    const VS st = *reinterpret_cast<const VS*>(state + f0);
+    const int d = __ldg(ell_deg + i);
+    int c[D];
+#pragma unroll
+    for (int q = 0; q < D / 4; q++) {
+        const int4 v = __ldg(reinterpret_cast<const int4*>(ell_col + (size_t)i * D) + q);
+        c[4 * q] = v.x;
+        c[4 * q + 1] = v.y;
+        c[4 * q + 2] = v.z;
+        c[4 * q + 3] = v.w;
+    }
+    uint32_t act = 0;
+#pragma unroll
+    for (int v = 0; v < VW; v++) act |= (uint32_t)(st.x[v] != 0) << v;
+    if (!act) return;
+
+    T* const erow = eta + (size_t)i * D * Fp + f0;
+    RegRow<VT, D> row;
+    row.cols = c;
+#pragma unroll
+    for (int t = 0; t < D; t++)
+        if (t < d) {
+            row.sv[t] = ld_nc(reinterpret_cast<const VT*>(s + (size_t)c[t] * Fp + f0));
+            if (!FIRST) row.ev[t] = *reinterpret_cast<const VT*>(erow + (size_t)t * Fp);
+        }
+    uint32_t z = 0;
+    if (!do_syn) z = row_update<MODE, FIRST, false, false, W, VW, D>(row, d, erow, Fp, wt);
+    else if (!paper) z = row_update<MODE, FIRST, true, false, W, VW, D>(row, d, erow, Fp, wt);
+    else z = row_update<MODE, FIRST, true, true, W, VW, D>(row, d, erow, Fp, wt);
+    if (do_syn) {
+        z &= act;
+        if (z) {
+#pragma unroll
+            for (int v = 0; v < VW; v++)
+                if ((z >> v) & 1) unsat[f0 + v] = 1;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Staged check pass (padded row layout): a persistent kernel in which every warp runs its
+// own pipeline of S shared-memory stages. A task is one row of one frame block (32 lanes x
+// VW frames); the warp's tasks are warp_id, warp_id + W_total, ... (rows fastest, so all
+// warps work on the same frame block at a time and its s stays in L2). For the task of
+// step k + S - 1 the warp's lanes issue bulk asynchronous copies (cp.async.bulk, the TMA
+// engine's untiled form) of the row's gathered s chunks and old message chunks into stage
+// (k + S - 1) mod S, completing on that stage's mbarrier, while it computes the task of
+// step k from stage k mod S; the row data (degree, columns, frame state) of the task after
+// that is loaded one step ahead. Shared memory, not registers, holds the bytes in flight.
+// Every wait is bounded: on timeout the kernel records kErrTimeout in *err, waits (again
+// bounded) for its own copies still in flight, and returns.
+// ------------------------------------------------------------------------------------
+constexpr int kErrTimeout = 1;
+constexpr uint32_t kDrainTries = 1u << 16;  // about 1.3 s at most
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// One try of at most about 20 us (the suspend-time hint) for the phase of the parity.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t n = 0; n < limit; n++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// L2 eviction policies: the gathered posteriors are read by about d_v rows of the frame
+// block being swept (keep them), the messages are read once per pass (let them go first).
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// Global -> shared bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) under an L2 cache policy, completing `bytes` transactions on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                         uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+struct StagedArgs {
+    const int32_t* ell_col;
+    const uint8_t* ell_deg;
+    int M, Fp, n_fblocks, stages, paper;
+    uint32_t wait_limit;
+    const uint8_t* state;
+    uint8_t* unsat;
+    int32_t* err;
+};
+
+// Shared memory of one warp: S stages of [D s chunks][D message chunks], each chunk
+// 32 VW sizeof(T) bytes; then per stage one 32-bit word per lane (degree << 8 | frame
+// mask) and D column ids; then S mbarriers.
+template <int MODE, int VW, int D>
+struct StagedLayout {
+    static constexpr int kChunk = 32 * VW * (int)sizeof(typename Tr<MODE>::T);
+    static constexpr int kStage = 2 * D * kChunk;
+    static constexpr int kMeta = 32 * 4 + D * 4;
+    __host__ __device__ static constexpr size_t warp_bytes(int S) {
+        return (size_t)S * (kStage + kMeta + 8);
+    }
+};
+
+constexpr int kStagedMaxThreads = 384;
+
+// SYN: test the syndrome of the gathered s (the decision of the previous iteration).
+template <int MODE, bool FIRST, bool SYN, bool W, int VW, int D>
+__global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const StagedArgs a,
+                                                      const typename Tr<MODE>::T* __restrict__ s,
+                                                      typename Tr<MODE>::T* __restrict__ eta,
+                                                      IterWeights wt) {
+    using T = typename Tr<MODE>::T;
+    using VT = typename RowVec<MODE, VW>::VT;
+    using VS = Vec<uint8_t, VW>;
+    using LY = StagedLayout<MODE, VW, D>;
+    static_assert(LY::kChunk % 16 == 0, "bulk copies move multiples of 16 bytes");
+    extern __shared__ __align__(128) unsigned char smem_st[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int S = a.stages, M = a.M, NB = a.n_fblocks;
+    unsigned char* const buf = smem_st + (size_t)warp * S * LY::kStage;
+    unsigned char* const meta = smem_st + (size_t)nw * S * LY::kStage + (size_t)warp * S * LY::kMeta;
+    uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_st + (size_t)nw * S * (LY::kStage + LY::kMeta)) +
+                          (size_t)warp * S;
+    if (lane == 0)
+        for (int q = 0; q < S; q++) mbar_init(&bar[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
+
+    // tasks first, first + stride, ... with task = y M + i (row i of frame block y); the
+    // host guarantees M NB + stride < 2^31. (i, y) advance without a division per task.
+    const int first = blockIdx.x * nw + warp, stride = gridDim.x * nw;
+    const int di = stride % M, dy = stride / M;
+    const int FB = 32 * VW;  // frames per block
+    const uint32_t tx = (FIRST ? 1u : 2u) * (uint32_t)LY::kChunk;
+    int ci = first % M, cy = first / M;  // the task being computed
+    int ni = ci, ny = cy;                // the next task to issue
+    int nx_d = 0, nx_c = 0;              // its row data, loaded one step ahead
+    uint32_t nx_act = 0;
+    uint32_t pend = 0, phase = 0;        // per stage: copies in flight / parity awaited
+    const uint64_t keep_s = policy_evict_last(), drop_eta = policy_evict_first();
+
+    auto load_row = [&]() {
+        if (ny >= NB) return;
+        nx_d = __ldg(a.ell_deg + ni);
+        nx_c = lane < D ? __ldg(a.ell_col + (size_t)ni * D + lane) : 0;
+        const VS st = *reinterpret_cast<const VS*>(a.state + (size_t)ny * FB + lane * VW);
+        uint32_t m = 0;
+#pragma unroll
+        for (int v = 0; v < VW; v++) m |= (uint32_t)(st.x[v] != 0) << v;
+        nx_act = m;
+    };
+    // issue the copies of the next task into stage q and move on to the task after it; a
+    // frame block with no active frame gets no copies (its phase completes at once)
+    auto issue = [&](int q) {
+        if (ny >= NB) return;
+        const int d = nx_d;
+        const bool any = __ballot_sync(0xffffffffu, nx_act != 0) != 0;
+        reinterpret_cast<uint32_t*>(meta + (size_t)q * LY::kMeta)[lane] =
+            ((uint32_t)d << 8) | (any ? nx_act : 0u);
+        if (lane < D) reinterpret_cast<int*>(meta + (size_t)q * LY::kMeta + 128)[lane] = nx_c;
+        // the generic-proxy reads of this stage (its previous task) precede the copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive_expect_tx(&bar[q], any ? tx * (uint32_t)d : 0u);
+        __syncwarp();
+        if (any && lane < d) {
+            unsigned char* st = buf + (size_t)q * LY::kStage;
+            const size_t fo = (size_t)ny * FB;
+            bulk_g2s(st + (size_t)lane * LY::kChunk, s + (size_t)nx_c * a.Fp + fo, LY::kChunk, &bar[q],
+                     keep_s);
+            if (!FIRST)
+                bulk_g2s(st + (size_t)(D + lane) * LY::kChunk, eta + ((size_t)ni * D + lane) * a.Fp + fo,
+                         LY::kChunk, &bar[q], drop_eta);
+        }
+        pend |= 1u << q;
+        ni += di;
+        ny += dy;
+        if (ni >= M) {
+            ni -= M;
+            ny++;
+        }
+        load_row();
+    };
+
+    load_row();
+    for (int q = 0; q < S; q++) issue(q);
+    for (int q = 0; cy < NB; q = (q + 1 == S) ? 0 : q + 1) {
+        const uint32_t par = (phase >> q) & 1u;
+        // the warp agrees on the outcome, so that it leaves or stays together
+        if (!__all_sync(0xffffffffu, mbar_wait(&bar[q], par, a.wait_limit))) {
+            if (lane == 0) atomicExch(a.err, kErrTimeout);
+            for (int j = 0; j < S; j++)  // let the copies in flight land (bounded)
+                if ((pend >> j) & 1u) mbar_wait(&bar[j], (phase >> j) & 1u, kDrainTries);
+            return;
+        }
+        phase ^= 1u << q;
+        pend &= ~(1u << q);
+        const uint32_t mw = reinterpret_cast<const uint32_t*>(meta + (size_t)q * LY::kMeta)[lane];
+        const uint32_t act = mw & 0xffu;
+        const int d = (int)(mw >> 8);
+        const unsigned char* st = buf + (size_t)q * LY::kStage;
+        if (act) {
+            const int f0 = cy * FB + lane * VW;
+            SmemRow<VT, D> row{const_cast<unsigned char*>(st), LY::kChunk, lane,
+                               reinterpret_cast<const int*>(meta + (size_t)q * LY::kMeta + 128)};
+            T* const erow = eta + (size_t)ci * D * a.Fp + f0;
+            if constexpr (SYN) {
+                uint32_t z = a.paper ? row_update<MODE, FIRST, true, true, W, VW, D>(row, d, erow, a.Fp, wt)
+                                     : row_update<MODE, FIRST, true, false, W, VW, D>(row, d, erow, a.Fp, wt);
+                z &= act;
+                if (z) {
+#pragma unroll
+                    for (int v = 0; v < VW; v++)
+                        if ((z >> v) & 1) a.unsat[f0 + v] = 1;
+                }
+            } else {
+                row_update<MODE, FIRST, false, false, W, VW, D>(row, d, erow, a.Fp, wt);
+            }
+        }
+        __syncwarp();
+        issue(q);  // the task S steps ahead into the stage just read
+        ci += di;
+        cy += dy;
+        if (ci >= M) {
+            ci -= M;
+            cy++;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // Variable-node pass. Block = 4 warps = 4 columns; lane = one frame vector.
 // test_prev: the previous decision's syndrome (in unsat) decides whether a frame stops.
 // ------------------------------------------------------------------------------------
@@ -328,6 +814,87 @@ __global__ void k_finish(const int32_t* done_iter, const uint8_t* unsat_final, i
     if (out_ok) out_ok[f] = d >= 0 ? 1 : (unsat_final[f] == 0);
 }
 
+// Launch of the staged check pass; false when the shape does not fit the device or the
+// task count does not fit 32 bits (the caller then runs the unstaged kernel).
+template <int MODE, int V, bool FIRST, bool W, int D>
+bool launch_staged(const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
+                   const typename Tr<MODE>::T* s, typename Tr<MODE>::T* eta, uint8_t* un,
+                   int test_prev, const IterWeights& wt, cudaStream_t st) {
+    if (w.stages <= 0 || w.stage_warps <= 0 || w.num_sms <= 0 || !w.err) return false;
+    using LY = StagedLayout<MODE, V, D>;
+    const int threads = 32 * w.stage_warps;
+    if (threads > kStagedMaxThreads) return false;
+    const size_t smem = LY::warp_bytes(w.stages) * w.stage_warps;
+    auto kern = test_prev ? k_check_staged<MODE, FIRST, true, W, V, D> : k_check_staged<MODE, FIRST, false, W, V, D>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    const int nb = w.Fp / (32 * V);
+    const long long tasks = (long long)a.M * nb;
+    const long long ctas = std::max<long long>(1, std::min<long long>((long long)w.num_sms * per_sm,
+                                               (tasks + w.stage_warps - 1) / w.stage_warps));
+    if (tasks + ctas * w.stage_warps >= (1ll << 31)) return false;
+    StagedArgs sa;
+    sa.ell_col = g.ell_col;
+    sa.ell_deg = g.ell_deg;
+    sa.M = a.M;
+    sa.Fp = w.Fp;
+    sa.n_fblocks = nb;
+    sa.stages = w.stages;
+    sa.paper = a.paper_slicer;
+    sa.wait_limit = w.wait_limit;
+    sa.state = w.state;
+    sa.unsat = un;
+    sa.err = w.err;
+    kern<<<(int)ctas, threads, smem, st>>>(sa, s, eta, wt);
+    return true;
+}
+
+// One check pass of iteration k: with the padded row layout, the staged kernel (when
+// staging is on) or the register kernel; else the general kernel on the CSR order.
+template <int MODE, int V, bool FIRST, bool W>
+void check_pass_t(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, dim3 gc,
+                  const typename Tr<MODE>::T* s, typename Tr<MODE>::T* eta, uint8_t* un,
+                  int test_prev, const IterWeights& wt, cudaStream_t st) {
+    const int Fp = w.Fp;
+    if (g.ell_D == 8) {
+        if (launch_staged<MODE, V, FIRST, W, 8>(g, a, w, s, eta, un, test_prev, wt, st)) return;
+        k_check_ell<MODE, FIRST, W, V, 8><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, eta, Fp,
+                                                              w.state, un, test_prev, a.paper_slicer, wt);
+        return;
+    }
+    if (g.ell_D == 16) {
+        if (launch_staged<MODE, V, FIRST, W, 16>(g, a, w, s, eta, un, test_prev, wt, st)) return;
+        k_check_ell<MODE, FIRST, W, V, 16><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, eta, Fp,
+                                                               w.state, un, test_prev, a.paper_slicer, wt);
+        return;
+    }
+    k_check<MODE, FIRST, false, W, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp,
+                                                          w.state, un, test_prev, w.n_done, a.frames,
+                                                          a.paper_slicer, wt);
+}
+
+template <int MODE, int V>
+void check_pass(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, dim3 gc,
+                const typename Tr<MODE>::T* s, typename Tr<MODE>::T* eta, uint8_t* un,
+                int test_prev, bool first, const IterWeights& wt, cudaStream_t st) {
+    const bool wgt = MODE == kModeFP32 && wt.alpha != nullptr;
+    if (first) {
+        if (wgt) check_pass_t<MODE, V, true, true>(g, a, w, gc, s, eta, un, test_prev, wt, st);
+        else check_pass_t<MODE, V, true, false>(g, a, w, gc, s, eta, un, test_prev, wt, st);
+    } else {
+        if (wgt) check_pass_t<MODE, V, false, true>(g, a, w, gc, s, eta, un, test_prev, wt, st);
+        else check_pass_t<MODE, V, false, false>(g, a, w, gc, s, eta, un, test_prev, wt, st);
+    }
+}
+
 template <int MODE, int V>
 int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_t st) {
     using T = typename Tr<MODE>::T;
@@ -346,30 +913,19 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
                                                                         a.N, r, s, Fp);
     launches++;
     const dim3 gc((a.M + 3) / 4, Fp / (32 * V)), gv((a.N + 3) / 4, Fp / (32 * V));
+    // message slot of each edge in column order: padded-row slots or CSR edge ids
+    const int32_t* cslot = g.ell_D ? g.ell_cslot : g.col_edge;
     for (int k = 1; k <= a.L; k++) {
         const int test_prev = a.early_stop && ((k - 1) % a.check_every == 0);
         uint8_t* un = w.unsat + (size_t)k * Fp;
+        IterWeights wt{};
         if (MODE == kModeFP32 && a.w_rows > 0) {
             const int row = (k < a.w_rows ? k : a.w_rows) - 1;
-            const IterWeights wt{g.col_class, a.w_alpha + (size_t)row * a.n_classes,
-                                 a.w_beta + (size_t)row * a.n_classes};
-            if (k == 1)
-                k_check<MODE, true, false, true, V><<<gc, 128, 0, st>>>(
-                    g.row_ptr, g.col_idx, a.M, s, eta, Fp, state, un, test_prev, w.n_done, a.frames,
-                    a.paper_slicer, wt);
-            else
-                k_check<MODE, false, false, true, V><<<gc, 128, 0, st>>>(
-                    g.row_ptr, g.col_idx, a.M, s, eta, Fp, state, un, test_prev, w.n_done, a.frames,
-                    a.paper_slicer, wt);
-        } else if (k == 1)
-            k_check<MODE, true, false, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp,
-                                                           state, un, test_prev, w.n_done,
-                                                           a.frames, a.paper_slicer);
-        else
-            k_check<MODE, false, false, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp,
-                                                            state, un, test_prev, w.n_done,
-                                                            a.frames, a.paper_slicer);
-        k_var<MODE, V><<<gv, 128, 0, st>>>(g.col_ptr, g.col_edge, a.N, r, s, eta, Fp, state,
+            wt = IterWeights{g.col_class, a.w_alpha + (size_t)row * a.n_classes,
+                             a.w_beta + (size_t)row * a.n_classes};
+        }
+        check_pass<MODE, V>(g, a, w, gc, s, eta, un, test_prev, k == 1, wt, st);
+        k_var<MODE, V><<<gv, 128, 0, st>>>(g.col_ptr, cslot, a.N, r, s, eta, Fp, state,
                                         w.done_iter, un, test_prev, k, w.n_done, a.frames);
         launches += 2;
     }
@@ -388,19 +944,19 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
 
 }  // namespace
 
-size_t stream_bytes(int mode, int32_t N, int64_t E, int32_t Fp, int32_t L) {
+size_t stream_bytes(int mode, int32_t N, int64_t slots, int32_t Fp, int32_t L) {
     size_t tb = mode == kModeFP32 ? 4 : 2, rb = mode == kModeFP32 ? 4 : 1;
-    return (size_t)E * Fp * tb + (size_t)N * Fp * (tb + rb) + (size_t)Fp * 5 + (size_t)(L + 2) * Fp + 256;
+    return (size_t)slots * Fp * tb + (size_t)N * Fp * (tb + rb) + (size_t)Fp * 5 + (size_t)(L + 2) * Fp + 256;
 }
 
-StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t E, int32_t Fp, int32_t L) {
+StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t slots, int32_t Fp, int32_t L) {
     // Fp is a multiple of 256, so every region below starts 256-byte aligned
     const size_t tb = mode == kModeFP32 ? 4 : 2, rb = mode == kModeFP32 ? 4 : 1;
     char* p = (char*)mem;
     StreamWork w;
     w.Fp = Fp;
     w.eta = p;
-    p += (size_t)E * Fp * tb;
+    p += (size_t)slots * Fp * tb;
     w.s = p;
     p += (size_t)N * Fp * tb;
     w.r = p;
@@ -412,6 +968,7 @@ StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t E, int32_t Fp, i
     w.unsat = (uint8_t*)p;
     p += (size_t)(L + 2) * Fp;
     w.n_done = (int32_t*)p;
+    w.err = w.n_done + 1;
     return w;
 }
 

@@ -21,6 +21,7 @@ LDPC_ERR_INVALID_H = -2
 LDPC_ERR_BAD_POINTER = -3
 LDPC_ERR_OOM = -4
 LDPC_ERR_CUDA = -5
+LDPC_ERR_TIMEOUT = -6
 LDPC_ERR_UNSUPPORTED = -8
 LDPC_MODE_FP32 = 0
 LDPC_MODE_FIXED = 1
@@ -65,6 +66,10 @@ SIGNATURES = {
     "ldpc_set_mode": (ctypes.c_int, [P, I32]),
     "ldpc_set_variant": (ctypes.c_int, [P, I32]),
     "ldpc_set_stream_group": (ctypes.c_int, [P, I32]),
+    "ldpc_set_stream_staging": (ctypes.c_int, [P, I32, I32]),
+    "ldpc_get_stream_staging": (ctypes.c_int, [P, PI32, PI32]),
+    "ldpc_check_device": (ctypes.c_int, [P]),
+    "ldpc_set_wait_limit": (ctypes.c_int, [P, I32]),
     "ldpc_set_cluster_shape": (ctypes.c_int, [P, I32, I32, I32]),
     "ldpc_get_cluster_shape": (ctypes.c_int, [P, PI32, PI32, PI32, PI32]),
     "ldpc_set_tuning": (ctypes.c_int, [P, I32, I32, I32]),
@@ -166,6 +171,24 @@ def ldpc_set_mode(h, mode):
 
 def ldpc_set_stream_group(h, frames_per_group):
     return load().ldpc_set_stream_group(h, frames_per_group)
+
+
+def ldpc_set_stream_staging(h, warps_per_cta, stages):
+    return load().ldpc_set_stream_staging(h, warps_per_cta, stages)
+
+
+def ldpc_get_stream_staging(h):
+    w, s = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().ldpc_get_stream_staging(h, ctypes.byref(w), ctypes.byref(s)), "ldpc_get_stream_staging")
+    return w.value, s.value
+
+
+def ldpc_check_device(h):
+    return load().ldpc_check_device(h)
+
+
+def ldpc_set_wait_limit(h, tries):
+    return load().ldpc_set_wait_limit(h, tries)
 
 
 def ldpc_set_cluster_shape(h, cluster_size, frames_per_tile, threads):
@@ -345,6 +368,24 @@ class Decoder:
     def set_stream_group(self, frames_per_group: int):
         """Streaming variant: 0 automatic L2-sized frame groups, -1 none, > 0 group size."""
         _check(load().ldpc_set_stream_group(self.h, frames_per_group), "ldpc_set_stream_group")
+
+    def set_stream_staging(self, warps_per_cta=0, stages=0):
+        """Streaming check pass: warps per CTA and shared-memory stages per warp of the
+        staged (bulk-copy) kernel; 0 = automatic, stages -1 = unstaged kernel."""
+        _check(load().ldpc_set_stream_staging(self.h, warps_per_cta, stages), "ldpc_set_stream_staging")
+
+    def stream_staging(self):
+        """(warps per CTA, stages) in force; stages 0 when the staged kernel is off."""
+        return ldpc_get_stream_staging(self.h)
+
+    def check_device(self):
+        """Wait for the handle's stream and raise LdpcError(LDPC_ERR_TIMEOUT) if a bounded
+        wait inside a kernel ran out since the last check."""
+        _check(load().ldpc_check_device(self.h), "ldpc_check_device")
+
+    def set_wait_limit(self, tries: int):
+        """Tries of each bounded wait in the staged kernels (0: give up at once)."""
+        _check(load().ldpc_set_wait_limit(self.h, tries), "ldpc_set_wait_limit")
 
     def set_tuning(self, frames_per_tile=0, threads=0, index_placement=0):
         _check(load().ldpc_set_tuning(self.h, frames_per_tile, threads, index_placement),

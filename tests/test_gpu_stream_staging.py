@@ -1,0 +1,102 @@
+"""The streaming variant's check pass on the padded row layout: the staged kernel (bulk
+asynchronous copies into shared-memory stages, one pipeline per warp) in several shapes,
+and the unstaged kernel, each against the CPU oracle (fixed point bit-exact; FP32 bits,
+iterations and status identical, posteriors within 1e-5 relative). Also the bounded waits:
+a wait limit of 0 makes every staged wait give up at once, which must surface as
+LDPC_ERR_TIMEOUT from ldpc_check_device without a fault, and the next decode must be
+correct again.
+"""
+import numpy as np
+import pytest
+
+from paper_2507_10424_gb300 import inputs
+from test_gpu_parity import assert_parity, oracle_decode, torch_cuda  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+# (warps per CTA, stages): unstaged, then staged shapes including the smallest ones
+SHAPES = [(0, -1), (1, 2), (4, 3), (8, 3), (2, 8)]
+
+
+def staged_decode(torch, code, llr, L, mode, shape, early_stop=True, paper_slicer=False):
+    from paper_2507_10424_gb300.ldpc import Decoder
+    dec = Decoder.from_code(code, mode=mode, paper_slicer=paper_slicer)
+    dec.set_variant("stream")
+    dec.set_stream_staging(*shape)
+    x = torch.from_numpy(np.ascontiguousarray(llr)).cuda()
+    bits, iters, ok, soft = dec.decode(x, L, early_stop=early_stop, want_ok=True, want_soft=True)
+    dec.check_device()
+    got = (bits.cpu().numpy(), iters.cpu().numpy(), ok.cpu().numpy(), soft.cpu().numpy())
+    dec.close()
+    return got
+
+
+def codes():
+    # rows of 6-7 edges (8 slots), of 10-16 edges (16 slots), and an irregular code with
+    # mixed row weights 3..8
+    return {
+        "regular576": inputs.cfg_regular_576(),
+        "qc2304": inputs.cfg_qc_2304(),
+        "irregular1200": inputs.irregular_code(1200, 500, [2, 3, 8], [0.5, 0.375, 0.125], 9),
+    }
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fixed"])
+@pytest.mark.parametrize("name", ["regular576", "qc2304", "irregular1200"])
+def test_staged_shapes_match_oracle(torch_cuda, mode, name):
+    code = codes()[name]
+    F = 300  # not a multiple of a frame block: the last block is ragged
+    llr = inputs.all_zero_awgn_llr(F, code.N, 2.0, code.design_rate, 41)
+    for early_stop in (True, False):
+        want = oracle_decode(code, llr, 12, mode, early_stop=early_stop)
+        for shape in SHAPES:
+            got = staged_decode(torch_cuda, code, llr, 12, mode, shape, early_stop)
+            assert_parity(got, want, mode, f"{name} {mode} {shape} early_stop={early_stop}")
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fixed"])
+def test_staged_paper_slicer_and_random_codewords(torch_cuda, mode):
+    code = inputs.cfg_regular_576()
+    cw = inputs.Encoder(code).random_codewords(200, 5)
+    llr = inputs.bpsk_awgn_llr(cw, 2.5, code.design_rate, 6)
+    want = oracle_decode(code, llr, 15, mode, paper_slicer=True)
+    got = staged_decode(torch_cuda, code, llr, 15, mode, (4, 3), paper_slicer=True)
+    assert_parity(got, want, mode, "paper slicer")
+
+
+def test_staging_settings_round_trip(torch_cuda):
+    from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
+    dec = Decoder.from_code(inputs.cfg_regular_576())
+    assert dec.stream_staging() == (8, 3)
+    dec.set_stream_staging(2, 5)
+    assert dec.stream_staging() == (2, 5)
+    dec.set_stream_staging(0, -1)
+    assert dec.stream_staging()[1] == 0
+    for bad in ((13, 3), (-1, 3), (4, 1), (4, 9), (4, -2)):
+        with pytest.raises(LdpcError):
+            dec.set_stream_staging(*bad)
+    dec.close()
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fixed"])
+def test_wait_that_runs_out_is_reported_and_the_next_decode_is_correct(torch_cuda, mode):
+    from paper_2507_10424_gb300.ldpc import Decoder, LdpcError, LDPC_ERR_TIMEOUT
+    torch = torch_cuda
+    code = inputs.cfg_regular_576()
+    llr = inputs.all_zero_awgn_llr(256, code.N, 2.0, code.design_rate, 43)
+    x = torch.from_numpy(llr).cuda()
+    dec = Decoder.from_code(code, mode=mode)
+    dec.set_variant("stream")
+    dec.set_stream_staging(4, 3)
+    dec.set_wait_limit(0)  # every staged wait gives up at its first look
+    dec.decode(x, 10)
+    with pytest.raises(LdpcError) as e:
+        dec.check_device()
+    assert e.value.status == LDPC_ERR_TIMEOUT
+    dec.check_device()  # the word was cleared by the read
+    dec.set_wait_limit(1 << 16)
+    bits, iters, ok, soft = dec.decode(x, 10, want_ok=True, want_soft=True)
+    dec.check_device()
+    got = (bits.cpu().numpy(), iters.cpu().numpy(), ok.cpu().numpy(), soft.cpu().numpy())
+    assert_parity(got, oracle_decode(code, llr, 10, mode), mode, "after a timeout")
+    dec.close()
