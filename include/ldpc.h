@@ -324,19 +324,23 @@ int ldpc_set_stream_group(ldpc_t *h, int32_t frames_per_group);
  * rows have at most 16 edges. Row i then owns 8 or 16 message slots (a padded row
  * layout). Each warp of a persistent kernel keeps `stages` shared-memory stages in
  * flight. Into each stage, the TMA engine's bulk asynchronous copies (cp.async.bulk)
- * bring one row's gathered posteriors s_j and old messages for 32 x 4 (FP32) or 32 x 8
- * (fixed point) frames, completing on an mbarrier, while the warp computes an earlier
- * row (Section III's row reductions).
- *   warps_per_cta in {0 (automatic: 8), 1..12};
+ * bring one row's gathered posteriors s_j and old messages for 32 x frames_per_lane
+ * frames, completing on an mbarrier, while the warp computes an earlier row (Section
+ * III's row reductions).
+ *   warps_per_cta in {0 (automatic: 8), 1..24};
  *   stages in {-1 (off: one thread per row and frame vector loads its row itself),
- *              0 (automatic: 3), 2..8}.
+ *              0 (automatic: 3), 2..8};
+ *   frames_per_lane in {0 (automatic: the mode's 16-byte vector, 4 FP32 or 8 int16 frames),
+ *                       1, 2, 4, 8 (at most the automatic width)}.
  * Results do not depend on the shape. A shape whose shared memory does not fit the device
  * falls back to the unstaged kernel. LDPC_ERR_INVALID_ARG for other values.
  */
-int ldpc_set_stream_staging(ldpc_t *h, int32_t warps_per_cta, int32_t stages);
+int ldpc_set_stream_staging(ldpc_t *h, int32_t warps_per_cta, int32_t stages, int32_t frames_per_lane);
 
-/* ldpc_get_stream_staging: the staging in force (stages 0 when off). */
-int ldpc_get_stream_staging(const ldpc_t *h, int32_t *warps_per_cta, int32_t *stages);
+/* ldpc_get_stream_staging: the staging in force (stages 0 when off; frames_per_lane 0 when
+ * automatic). */
+int ldpc_get_stream_staging(const ldpc_t *h, int32_t *warps_per_cta, int32_t *stages,
+                            int32_t *frames_per_lane);
 
 /*
  * ldpc_check_device: waits for the handle's stream, then reads and clears the handle's

@@ -78,7 +78,7 @@ struct ldpc {
                                   // count, [2] device error word (bounded waits that ran out)
     // staged streaming check pass: requested warps per CTA and stages (0 = automatic,
     // stages -1 = off) and the tries of each bounded wait
-    int32_t st_warps = 0, st_stages = 0;
+    int32_t st_warps = 0, st_stages = 0, st_vw = 0;
     uint32_t wait_limit = 1u << 16;
     // cluster variant: layouts built on demand from the host graph, one per cluster size
     // 2^i; plans per mode, recomputed after any change of tuning or weights
@@ -99,7 +99,7 @@ struct ldpc {
 static void free_graph(DevGraph& g) {
     void* ptrs[] = {g.row_ptr, g.col_idx, g.col_ptr, g.col_edge, g.packed, g.r_base,
                     g.r_deg, g.r_slot_pos, g.c_base, g.c_deg, g.c_slot, g.col_pos,
-                    g.col_class, g.r_slot_cls, g.ell_col, g.ell_deg, g.ell_cslot};
+                    g.col_class, g.r_slot_cls, g.ell_col, g.ell_deg, g.ell_cslot, g.ell_cls};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     g = DevGraph();
@@ -131,6 +131,7 @@ static void apply_staging(const ldpc_t* h, StreamWork& w) {
     w.num_sms = h->num_sms;
     w.stage_warps = h->st_warps > 0 ? h->st_warps : kStageWarpsDefault;
     w.stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
+    w.stage_vw = h->st_vw;
     w.wait_limit = h->wait_limit;
 }
 
@@ -306,7 +307,8 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
         if (build_ell(hg, eg)) {
             if ((rc = upload(&h->dg.ell_col, eg.ell_col.data(), eg.ell_col.size())) ||
                 (rc = upload(&h->dg.ell_deg, eg.ell_deg.data(), eg.ell_deg.size())) ||
-                (rc = upload(&h->dg.ell_cslot, eg.ell_cslot.data(), eg.ell_cslot.size())))
+                (rc = upload(&h->dg.ell_cslot, eg.ell_cslot.data(), eg.ell_cslot.size())) ||
+                (rc = upload(&h->dg.ell_cls, eg.ell_cls.data(), eg.ell_cls.size())))
                 return bail(rc);
             h->dg.ell_D = eg.D;
             h->dg.eta_slots = (int64_t)hg.M * eg.D;
@@ -364,6 +366,7 @@ int ldpc_impl::handle_view(ldpc_t* h, HandleView* v) {
     v->err = h->counters + 2;
     v->stage_warps = h->st_warps > 0 ? h->st_warps : kStageWarpsDefault;
     v->stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
+    v->stage_vw = h->st_vw;
     v->wait_limit = h->wait_limit;
     return LDPC_OK;
 }
@@ -763,20 +766,25 @@ int ldpc_set_stream_group(ldpc_t* h, int32_t frames_per_group) {
     return LDPC_OK;
 }
 
-int ldpc_set_stream_staging(ldpc_t* h, int32_t warps_per_cta, int32_t stages) {
+int ldpc_set_stream_staging(ldpc_t* h, int32_t warps_per_cta, int32_t stages, int32_t frames_per_lane) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
-    if (warps_per_cta < 0 || warps_per_cta > 12 || stages < -1 || stages == 1 || stages > 8)
+    if (warps_per_cta < 0 || warps_per_cta > 24 || stages < -1 || stages == 1 || stages > 8 ||
+        (frames_per_lane != 0 && frames_per_lane != 1 && frames_per_lane != 2 && frames_per_lane != 4 &&
+         frames_per_lane != 8))
         return fail(LDPC_ERR_INVALID_ARG);
     h->st_warps = warps_per_cta;
     h->st_stages = stages;
+    h->st_vw = frames_per_lane;
     apply_staging(h, h->sw);
     return LDPC_OK;
 }
 
-int ldpc_get_stream_staging(const ldpc_t* h, int32_t* warps_per_cta, int32_t* stages) {
+int ldpc_get_stream_staging(const ldpc_t* h, int32_t* warps_per_cta, int32_t* stages,
+                            int32_t* frames_per_lane) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
     if (warps_per_cta) *warps_per_cta = h->st_warps > 0 ? h->st_warps : kStageWarpsDefault;
     if (stages) *stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
+    if (frames_per_lane) *frames_per_lane = h->st_vw;
     return LDPC_OK;
 }
 

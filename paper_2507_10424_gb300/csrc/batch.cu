@@ -333,6 +333,7 @@ int ldpc_batch_prepare(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
             x.w.num_sms = v.num_sms;
             x.w.stage_warps = v.stage_warps;
             x.w.stages = v.stages;
+            x.w.stage_vw = v.stage_vw;
             x.w.wait_limit = v.wait_limit;
             DecodeArgs& a = x.a;
             a = DecodeArgs();

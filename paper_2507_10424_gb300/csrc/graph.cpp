@@ -297,6 +297,10 @@ bool build_ell(const HostGraph& g, EllGraph& eg) {
     if ((int64_t)g.M * D >= (int64_t)INT32_MAX) return false;
     eg.ell_cslot.resize(g.E);
     for (int64_t q = 0; q < g.E; q++) eg.ell_cslot[q] = (int32_t)slot_of_edge[g.col_edge[q]];
+    eg.ell_cls.assign((size_t)g.M * D, 0);
+    for (int32_t i = 0; i < g.M; i++)
+        for (int32_t t = 0; t < g.row_ptr[i + 1] - g.row_ptr[i]; t++)
+            eg.ell_cls[(size_t)i * D + t] = g.col_class[g.col_idx[g.row_ptr[i] + t]];
     return true;
 }
 

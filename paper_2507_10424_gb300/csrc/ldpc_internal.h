@@ -70,12 +70,14 @@ bool build_sliced(const HostGraph& g, SlicedGraph& sg);
 //   ell_col[i D + t]  column of the t-th edge (t < deg(i)); padding repeats a valid column
 //   ell_deg[i]        deg(i)
 //   ell_cslot[q]      slot of the q-th edge of the CSC order (ascending rows per column)
+//   ell_cls[i D + t]  learned-weight class of the edge's bit (0 for padding)
 // ---------------------------------------------------------------------------------------
 struct EllGraph {
     int32_t D = 0;
     std::vector<int32_t> ell_col;
     std::vector<uint8_t> ell_deg;
     std::vector<int32_t> ell_cslot;
+    std::vector<uint8_t> ell_cls;
 };
 // Returns false when a row has more than 16 edges (the layout is then not used).
 bool build_ell(const HostGraph& g, EllGraph& eg);
@@ -146,6 +148,7 @@ struct DevGraph {
     int32_t* ell_col = nullptr;
     uint8_t* ell_deg = nullptr;
     int32_t* ell_cslot = nullptr;
+    uint8_t* ell_cls = nullptr;
     int32_t ell_D = 0;
     // message slots of the streaming workspace: M ell_D with the padded layout, else E
     int64_t eta_slots = 0;
@@ -189,6 +192,7 @@ struct StreamWork {
     // the host reads and clears it); wait_limit: tries of each bounded wait
     int32_t* err = nullptr;
     int32_t stage_warps = 0, stages = 0;
+    int32_t stage_vw = 0;  // frames per lane of the staged kernel (0: the run's vector width)
     uint32_t wait_limit = 1u << 16;
     int32_t num_sms = 0;
 };
@@ -253,6 +257,7 @@ struct HandleView {
     int32_t num_sms = 0;
     int32_t* err = nullptr;  // device error word of the handle
     int32_t stage_warps = 0, stages = 0;  // staged streaming check pass (stages 0 = off)
+    int32_t stage_vw = 0;
     uint32_t wait_limit = 0;
 };
 int handle_view(::ldpc_t* h, HandleView* v);

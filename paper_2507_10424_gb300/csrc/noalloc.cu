@@ -100,6 +100,7 @@ extern "C" int ldpc_decode_noalloc(ldpc_t* h, const void* llr, int32_t llr_dtype
     w.num_sms = v.num_sms;
     w.stage_warps = v.stage_warps;
     w.stages = v.stages;
+    w.stage_vw = v.stage_vw;
     w.wait_limit = v.wait_limit;
     DecodeArgs a;
     a.M = v.M;

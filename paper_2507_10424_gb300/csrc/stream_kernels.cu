@@ -287,7 +287,12 @@ struct RegRow {
     __device__ __forceinline__ VT e(int t) const { return ev[t]; }
     __device__ __forceinline__ void keep(int t, const VT& l) { sv[t] = l; }
     __device__ __forceinline__ VT lam(int t) const { return sv[t]; }
-    __device__ __forceinline__ int col(int t) const { return cols[t]; }
+    // learned weights of edge t: through the class of its column
+    __device__ __forceinline__ void weights(int t, const IterWeights& wt, float& wa, float& wb) const {
+        const int cls = __ldg(wt.col_class + cols[t]);
+        wa = __ldg(wt.alpha + cls);
+        wb = __ldg(wt.beta + cls);
+    }
 };
 // Operands in a shared-memory stage: chunk t holds s of edge t (lambda replaces it),
 // chunk D + t the old message; this lane's vector sits at byte lane sizeof(VT).
@@ -295,7 +300,9 @@ template <typename VT, int D>
 struct SmemRow {
     unsigned char* st;
     int chunk, lane;
-    const int* cols;
+    const int* cls;       // learned-weight class of each edge (shared memory)
+    const float* walpha;  // weight tables of the iteration (shared memory)
+    const float* wbeta;
     __device__ __forceinline__ VT* at(int c) const {
         return reinterpret_cast<VT*>(st + (size_t)c * chunk + (size_t)lane * sizeof(VT));
     }
@@ -303,7 +310,11 @@ struct SmemRow {
     __device__ __forceinline__ VT e(int t) const { return *at(D + t); }
     __device__ __forceinline__ void keep(int t, const VT& l) { *at(t) = l; }
     __device__ __forceinline__ VT lam(int t) const { return *at(t); }
-    __device__ __forceinline__ int col(int t) const { return cols[t]; }
+    __device__ __forceinline__ void weights(int t, const IterWeights&, float& wa, float& wb) const {
+        const int c = cls[t];
+        wa = walpha[c];
+        wb = wbeta[c];
+    }
 };
 
 // The row update of one lane's VW frames over the d <= D edges of a row (Observation 1:
@@ -355,11 +366,7 @@ __device__ __forceinline__ uint32_t row_update(Row& row, int d, typename Tr<MODE
         for (int t = 0; t < D; t++)
             if (t < d) {
                 float wa = 1.0f, wb = 0.0f;
-                if constexpr (W) {
-                    const int cls = __ldg(wt.col_class + row.col(t));
-                    wa = __ldg(wt.alpha + cls);
-                    wb = __ldg(wt.beta + cls);
-                }
+                if constexpr (W) row.weights(t, wt, wa, wb);
                 const VT lv = row.lam(t);
                 VT out;
 #pragma unroll
@@ -557,7 +564,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 struct StagedArgs {
     const int32_t* ell_col;
     const uint8_t* ell_deg;
-    int M, Fp, n_fblocks, stages, paper;
+    const uint8_t* ell_cls;  // learned-weight class of each slot
+    int M, Fp, n_fblocks, stages, paper, n_classes;
     uint32_t wait_limit;
     const uint8_t* state;
     uint8_t* unsat;
@@ -566,7 +574,8 @@ struct StagedArgs {
 
 // Shared memory of one warp: S stages of [D s chunks][D message chunks], each chunk
 // 32 VW sizeof(T) bytes; then per stage one 32-bit word per lane (degree << 8 | frame
-// mask) and D column ids; then S mbarriers.
+// mask) and D learned-weight classes; then S mbarriers. With learned weights the CTA's
+// copy of the iteration's alpha and beta tables (256 entries each) follows.
 template <int MODE, int VW, int D>
 struct StagedLayout {
     static constexpr int kChunk = 32 * VW * (int)sizeof(typename Tr<MODE>::T);
@@ -575,6 +584,7 @@ struct StagedLayout {
     __host__ __device__ static constexpr size_t warp_bytes(int S) {
         return (size_t)S * (kStage + kMeta + 8);
     }
+    static constexpr int kWeightBytes = 2 * 256 * 4;
 };
 
 constexpr int kStagedMaxThreads = 384;
@@ -597,6 +607,15 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
     unsigned char* const meta = smem_st + (size_t)nw * S * LY::kStage + (size_t)warp * S * LY::kMeta;
     uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_st + (size_t)nw * S * (LY::kStage + LY::kMeta)) +
                           (size_t)warp * S;
+    float* const walpha = reinterpret_cast<float*>(smem_st + (size_t)nw * LY::warp_bytes(S));
+    float* const wbeta = walpha + 256;
+    if constexpr (W) {  // the iteration's weight tables, shared by the CTA
+        for (int c = threadIdx.x; c < a.n_classes; c += blockDim.x) {
+            walpha[c] = __ldg(wt.alpha + c);
+            wbeta[c] = __ldg(wt.beta + c);
+        }
+        __syncthreads();
+    }
     if (lane == 0)
         for (int q = 0; q < S; q++) mbar_init(&bar[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -610,7 +629,7 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
     const uint32_t tx = (FIRST ? 1u : 2u) * (uint32_t)LY::kChunk;
     int ci = first % M, cy = first / M;  // the task being computed
     int ni = ci, ny = cy;                // the next task to issue
-    int nx_d = 0, nx_c = 0;              // its row data, loaded one step ahead
+    int nx_d = 0, nx_c = 0, nx_cls = 0;  // its row data, loaded one step ahead
     uint32_t nx_act = 0;
     uint32_t pend = 0, phase = 0;        // per stage: copies in flight / parity awaited
     const uint64_t keep_s = policy_evict_last(), drop_eta = policy_evict_first();
@@ -619,6 +638,7 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
         if (ny >= NB) return;
         nx_d = __ldg(a.ell_deg + ni);
         nx_c = lane < D ? __ldg(a.ell_col + (size_t)ni * D + lane) : 0;
+        if (W) nx_cls = lane < D ? __ldg(a.ell_cls + (size_t)ni * D + lane) : 0;
         const VS st = *reinterpret_cast<const VS*>(a.state + (size_t)ny * FB + lane * VW);
         uint32_t m = 0;
 #pragma unroll
@@ -633,7 +653,7 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
         const bool any = __ballot_sync(0xffffffffu, nx_act != 0) != 0;
         reinterpret_cast<uint32_t*>(meta + (size_t)q * LY::kMeta)[lane] =
             ((uint32_t)d << 8) | (any ? nx_act : 0u);
-        if (lane < D) reinterpret_cast<int*>(meta + (size_t)q * LY::kMeta + 128)[lane] = nx_c;
+        if (W && lane < D) reinterpret_cast<int*>(meta + (size_t)q * LY::kMeta + 128)[lane] = nx_cls;
         // the generic-proxy reads of this stage (its previous task) precede the copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -674,11 +694,12 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
         const uint32_t mw = reinterpret_cast<const uint32_t*>(meta + (size_t)q * LY::kMeta)[lane];
         const uint32_t act = mw & 0xffu;
         const int d = (int)(mw >> 8);
-        const unsigned char* st = buf + (size_t)q * LY::kStage;
+        unsigned char* const st = buf + (size_t)q * LY::kStage;
         if (act) {
             const int f0 = cy * FB + lane * VW;
-            SmemRow<VT, D> row{const_cast<unsigned char*>(st), LY::kChunk, lane,
-                               reinterpret_cast<const int*>(meta + (size_t)q * LY::kMeta + 128)};
+            SmemRow<VT, D> row{st, LY::kChunk, lane,
+                               reinterpret_cast<const int*>(meta + (size_t)q * LY::kMeta + 128), walpha,
+                               wbeta};
             T* const erow = eta + (size_t)ci * D * a.Fp + f0;
             if constexpr (SYN) {
                 uint32_t z = a.paper ? row_update<MODE, FIRST, true, true, W, VW, D>(row, d, erow, a.Fp, wt)
@@ -824,7 +845,8 @@ bool launch_staged(const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
     using LY = StagedLayout<MODE, V, D>;
     const int threads = 32 * w.stage_warps;
     if (threads > kStagedMaxThreads) return false;
-    const size_t smem = LY::warp_bytes(w.stages) * w.stage_warps;
+    const size_t smem = LY::warp_bytes(w.stages) * w.stage_warps + (W ? LY::kWeightBytes : 0);
+    if (W && a.n_classes > 256) return false;
     auto kern = test_prev ? k_check_staged<MODE, FIRST, true, W, V, D> : k_check_staged<MODE, FIRST, false, W, V, D>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
@@ -844,6 +866,8 @@ bool launch_staged(const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
     StagedArgs sa;
     sa.ell_col = g.ell_col;
     sa.ell_deg = g.ell_deg;
+    sa.ell_cls = g.ell_cls;
+    sa.n_classes = a.n_classes;
     sa.M = a.M;
     sa.Fp = w.Fp;
     sa.n_fblocks = nb;
@@ -857,6 +881,28 @@ bool launch_staged(const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
     return true;
 }
 
+// The staged launch with w.stage_vw frames per lane (0: the run's V); any width up to V
+// works on the same frame stride.
+template <int MODE, int V, bool FIRST, bool W, int D>
+bool staged(const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
+            const typename Tr<MODE>::T* s, typename Tr<MODE>::T* eta, uint8_t* un, int test_prev,
+            const IterWeights& wt, cudaStream_t st) {
+    switch (w.stage_vw) {
+        case 0: return launch_staged<MODE, V, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
+        case 1: return launch_staged<MODE, 1, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
+        case 2:
+            if constexpr (V >= 2) return launch_staged<MODE, 2, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
+            break;
+        case 4:
+            if constexpr (V >= 4) return launch_staged<MODE, 4, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
+            break;
+        case 8:
+            if constexpr (V >= 8) return launch_staged<MODE, 8, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
+            break;
+    }
+    return launch_staged<MODE, V, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
+}
+
 // One check pass of iteration k: with the padded row layout, the staged kernel (when
 // staging is on) or the register kernel; else the general kernel on the CSR order.
 template <int MODE, int V, bool FIRST, bool W>
@@ -865,13 +911,13 @@ void check_pass_t(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, d
                   int test_prev, const IterWeights& wt, cudaStream_t st) {
     const int Fp = w.Fp;
     if (g.ell_D == 8) {
-        if (launch_staged<MODE, V, FIRST, W, 8>(g, a, w, s, eta, un, test_prev, wt, st)) return;
+        if (staged<MODE, V, FIRST, W, 8>(g, a, w, s, eta, un, test_prev, wt, st)) return;
         k_check_ell<MODE, FIRST, W, V, 8><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, eta, Fp,
                                                               w.state, un, test_prev, a.paper_slicer, wt);
         return;
     }
     if (g.ell_D == 16) {
-        if (launch_staged<MODE, V, FIRST, W, 16>(g, a, w, s, eta, un, test_prev, wt, st)) return;
+        if (staged<MODE, V, FIRST, W, 16>(g, a, w, s, eta, un, test_prev, wt, st)) return;
         k_check_ell<MODE, FIRST, W, V, 16><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, eta, Fp,
                                                                w.state, un, test_prev, a.paper_slicer, wt);
         return;

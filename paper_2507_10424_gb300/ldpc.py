@@ -66,8 +66,8 @@ SIGNATURES = {
     "ldpc_set_mode": (ctypes.c_int, [P, I32]),
     "ldpc_set_variant": (ctypes.c_int, [P, I32]),
     "ldpc_set_stream_group": (ctypes.c_int, [P, I32]),
-    "ldpc_set_stream_staging": (ctypes.c_int, [P, I32, I32]),
-    "ldpc_get_stream_staging": (ctypes.c_int, [P, PI32, PI32]),
+    "ldpc_set_stream_staging": (ctypes.c_int, [P, I32, I32, I32]),
+    "ldpc_get_stream_staging": (ctypes.c_int, [P, PI32, PI32, PI32]),
     "ldpc_check_device": (ctypes.c_int, [P]),
     "ldpc_set_wait_limit": (ctypes.c_int, [P, I32]),
     "ldpc_set_cluster_shape": (ctypes.c_int, [P, I32, I32, I32]),
@@ -173,14 +173,15 @@ def ldpc_set_stream_group(h, frames_per_group):
     return load().ldpc_set_stream_group(h, frames_per_group)
 
 
-def ldpc_set_stream_staging(h, warps_per_cta, stages):
-    return load().ldpc_set_stream_staging(h, warps_per_cta, stages)
+def ldpc_set_stream_staging(h, warps_per_cta, stages, frames_per_lane=0):
+    return load().ldpc_set_stream_staging(h, warps_per_cta, stages, frames_per_lane)
 
 
 def ldpc_get_stream_staging(h):
-    w, s = ctypes.c_int32(), ctypes.c_int32()
-    _check(load().ldpc_get_stream_staging(h, ctypes.byref(w), ctypes.byref(s)), "ldpc_get_stream_staging")
-    return w.value, s.value
+    w, s, v = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().ldpc_get_stream_staging(h, ctypes.byref(w), ctypes.byref(s), ctypes.byref(v)),
+           "ldpc_get_stream_staging")
+    return w.value, s.value, v.value
 
 
 def ldpc_check_device(h):
@@ -369,13 +370,15 @@ class Decoder:
         """Streaming variant: 0 automatic L2-sized frame groups, -1 none, > 0 group size."""
         _check(load().ldpc_set_stream_group(self.h, frames_per_group), "ldpc_set_stream_group")
 
-    def set_stream_staging(self, warps_per_cta=0, stages=0):
-        """Streaming check pass: warps per CTA and shared-memory stages per warp of the
-        staged (bulk-copy) kernel; 0 = automatic, stages -1 = unstaged kernel."""
-        _check(load().ldpc_set_stream_staging(self.h, warps_per_cta, stages), "ldpc_set_stream_staging")
+    def set_stream_staging(self, warps_per_cta=0, stages=0, frames_per_lane=0):
+        """Streaming check pass: warps per CTA, shared-memory stages per warp and frames per
+        lane of the staged (bulk-copy) kernel; 0 = automatic, stages -1 = unstaged kernel."""
+        _check(load().ldpc_set_stream_staging(self.h, warps_per_cta, stages, frames_per_lane),
+               "ldpc_set_stream_staging")
 
     def stream_staging(self):
-        """(warps per CTA, stages) in force; stages 0 when the staged kernel is off."""
+        """(warps per CTA, stages, frames per lane) in force; stages 0 when the staged kernel
+        is off, frames per lane 0 when automatic."""
         return ldpc_get_stream_staging(self.h)
 
     def check_device(self):

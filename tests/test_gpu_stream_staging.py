@@ -14,8 +14,9 @@ from test_gpu_parity import assert_parity, oracle_decode, torch_cuda  # noqa: F4
 
 pytestmark = pytest.mark.gpu
 
-# (warps per CTA, stages): unstaged, then staged shapes including the smallest ones
-SHAPES = [(0, -1), (1, 2), (4, 3), (8, 3), (2, 8)]
+# (warps per CTA, stages, frames per lane): unstaged, then staged shapes including the
+# smallest ones and narrower lanes than the mode's vector
+SHAPES = [(0, -1, 0), (1, 2, 0), (4, 3, 0), (8, 3, 0), (2, 8, 0), (24, 2, 2), (12, 2, 1)]
 
 
 def staged_decode(torch, code, llr, L, mode, shape, early_stop=True, paper_slicer=False):
@@ -60,19 +61,19 @@ def test_staged_paper_slicer_and_random_codewords(torch_cuda, mode):
     cw = inputs.Encoder(code).random_codewords(200, 5)
     llr = inputs.bpsk_awgn_llr(cw, 2.5, code.design_rate, 6)
     want = oracle_decode(code, llr, 15, mode, paper_slicer=True)
-    got = staged_decode(torch_cuda, code, llr, 15, mode, (4, 3), paper_slicer=True)
+    got = staged_decode(torch_cuda, code, llr, 15, mode, (4, 3, 0), paper_slicer=True)
     assert_parity(got, want, mode, "paper slicer")
 
 
 def test_staging_settings_round_trip(torch_cuda):
     from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
     dec = Decoder.from_code(inputs.cfg_regular_576())
-    assert dec.stream_staging() == (8, 3)
-    dec.set_stream_staging(2, 5)
-    assert dec.stream_staging() == (2, 5)
+    assert dec.stream_staging() == (8, 3, 0)
+    dec.set_stream_staging(2, 5, 2)
+    assert dec.stream_staging() == (2, 5, 2)
     dec.set_stream_staging(0, -1)
     assert dec.stream_staging()[1] == 0
-    for bad in ((13, 3), (-1, 3), (4, 1), (4, 9), (4, -2)):
+    for bad in ((25, 3, 0), (-1, 3, 0), (4, 1, 0), (4, 9, 0), (4, -2, 0), (4, 3, 3), (4, 3, 16)):
         with pytest.raises(LdpcError):
             dec.set_stream_staging(*bad)
     dec.close()
@@ -87,7 +88,7 @@ def test_wait_that_runs_out_is_reported_and_the_next_decode_is_correct(torch_cud
     x = torch.from_numpy(llr).cuda()
     dec = Decoder.from_code(code, mode=mode)
     dec.set_variant("stream")
-    dec.set_stream_staging(4, 3)
+    dec.set_stream_staging(4, 3, 0)
     dec.set_wait_limit(0)  # every staged wait gives up at its first look
     dec.decode(x, 10)
     with pytest.raises(LdpcError) as e:
