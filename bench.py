@@ -50,18 +50,24 @@ def parse():
     ap.add_argument("--tuning", default="auto",
                     help="resident launch shape 'FT,threads[,index placement]' instead of the autotuner")
     ap.add_argument("--quick", action="store_true", help="skip the extra measurements")
+    ap.add_argument("--workload", choices=["qc2304", "irregular64800"], default="qc2304",
+                    help="qc2304: the headline batch; irregular64800: the large irregular code "
+                         "(all-zero codeword at Eb/N0 1.0 dB, decoded by the streaming kernels)")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ workload
 
-def make_code():
+def make_code(workload="qc2304"):
     from paper_2507_10424_gb300 import inputs
-    return inputs.cfg_qc_2304()
+    return inputs.cfg_irregular_64800() if workload == "irregular64800" else inputs.cfg_qc_2304()
 
 
-def make_llr(code, F, seed):
+def make_llr(code, F, seed, workload="qc2304"):
     from paper_2507_10424_gb300 import inputs
+    if workload == "irregular64800":  # all-zero codeword (the encoder of this code is impractical)
+        llr = inputs.all_zero_awgn_llr(F, code.N, 1.0, code.design_rate, seed)
+        return np.zeros((F, code.N), np.uint8), llr, np.array([0, F])
     enc = inputs.Encoder(code)
     cw = enc.random_codewords(F, seed)
     llr = np.empty((F, code.N), np.float32)
@@ -79,7 +85,10 @@ def edge_message_bytes(code, mode):
     return 2 * code.E * m + code.N * (br + 2 * bs)
 
 
-def workload_name(code, F, L):
+def workload_name(code, F, L, workload="qc2304"):
+    if workload == "irregular64800":
+        return (f"irregular, column weights 2/3/8: N={code.N} M={code.M} E={code.E}; {F} all-zero "
+                f"codewords, Eb/N0 1.0 dB; {L} flooding iterations, no early stop")
     return (f"QC 12x24 base, Z=96: N={code.N} M={code.M} E={code.E}; {F} random codewords, "
             f"Eb/N0 1.0-3.0 dB step 0.5; {L} flooding iterations, no early stop")
 
@@ -165,7 +174,7 @@ def measured_peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCES = {"k_resident": "resident.cuh", "k_check": "stream_kernels.cu"}
+KERNEL_SOURCES = {"k_resident": "resident.cuh", "k_check_staged": "stream_kernels.cu"}
 
 
 def kernel_source_hash(kernel):
@@ -408,10 +417,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    code = make_code()
+    code = make_code(args.workload)
     L = args.iters
     threads = cpu_threads()
-    _, llr, _ = make_llr(code, 4096, 7)
+    _, llr, _ = make_llr(code, 4096 if args.workload == "qc2304" else 256, 7, args.workload)
     g = oracle.Graph.from_code(code)
 
     def step(x):
@@ -423,7 +432,7 @@ def run_reference(args):
     t = time.perf_counter()
     step(llr[: max(threads, 32)])
     per_frame = (time.perf_counter() - t) / max(threads, 32)
-    S = int(min(4096, max(threads, 0.5 / max(per_frame, 1e-6))))  # ~0.5 s per step
+    S = int(min(len(llr), max(threads, 0.5 / max(per_frame, 1e-6))))  # ~0.5 s per step
     for w in range(args.warmup):
         step(llr[:S])
     t = time.perf_counter()
@@ -431,13 +440,15 @@ def run_reference(args):
         step(llr[:S])
     dt = time.perf_counter() - t
     val = S * code.N * args.steps / dt / 1e9
-    sample = f"{S} of the workload's frames per step on {threads} host threads"
+    sample = (f"{S} of the workload's {args.frames} frames per step (a bounded sample), "
+              f"on {threads} host threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "Gbit/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.mode == "fp32" else "i16",
-        "data": "synthetic", "config": {"workload": workload_name(code, S, L), "mode": args.mode},
+        "data": "synthetic",
+        "config": {"workload": workload_name(code, args.frames, L, args.workload), "mode": args.mode},
         "cpu_baseline": {"value": val, "unit": "Gbit/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -473,9 +484,10 @@ def main():
     def max_over_ranks(x):
         return shard.max_over_ranks(x, device="cuda")
 
-    code = make_code()
+    code = make_code(args.workload)
     F, L, mode = args.frames, args.iters, args.mode
-    cw, llr, bounds = make_llr(code, F, shard.rank_seed(1000, rank))
+    cw, llr, bounds = make_llr(code, F, shard.rank_seed(1000, rank), args.workload)
+    snrs = SNRS if args.workload == "qc2304" else [1.0]
     dec = Decoder.from_code(code, mode=mode)
     dec.set_variant(args.variant)
     variant = dec.variant()
@@ -528,7 +540,7 @@ def main():
     peak, peak_kind = measured_peak_hbm()
     B = edge_message_bytes(code, mode)
     alg_bytes = F * L * B
-    kname = "k_resident" if variant == "resident" else "k_check"
+    kname = "k_resident" if variant == "resident" else "k_check_staged"
     achieved = alg_bytes / (ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": ncu_traffic(kname, mode, F),
@@ -538,7 +550,7 @@ def main():
     # frame error rate per SNR point (outside the timed region)
     ber_fer = {}
     wrong = (bits != torch.from_numpy(cw).cuda()).any(dim=1).cpu().numpy()
-    for k, e in enumerate(SNRS):
+    for k, e in enumerate(snrs):
         a, b = bounds[k], bounds[k + 1]
         ber_fer[f"{e:.1f}dB"] = float(wrong[a:b].mean())
 
@@ -547,7 +559,7 @@ def main():
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if mode == "fp32" else "i16", "data": "synthetic",
-        "config": {"workload": workload_name(code, F, L), "frames_per_gpu": F, "iters": L,
+        "config": {"workload": workload_name(code, F, L, args.workload), "frames_per_gpu": F, "iters": L,
                    "early_stop": False, "mode": mode, "variant": variant,
                    "tuning": (dict(zip(("frames_per_tile", "threads", "index_placement"), dec.tuning()))
                               if variant == "resident" else None),
@@ -576,6 +588,7 @@ def main():
                          "h2d_bytes_per_step": int(xh.numel() * 4),
                          "d2h_bytes_per_step": int(bh.numel() + ih.numel() * 4),
                          "ms_per_step": te * 1e3}
+    if not args.quick and args.workload == "qc2304":
         # the other arithmetic mode and the other kernel variant, same workload
         others = {}
         for m2, v2 in (("fixed" if mode == "fp32" else "fp32", "auto"), (mode, "stream")):
@@ -611,12 +624,12 @@ def main():
             result["learned"] = learned_vs_plain(timed)
             result["learned_large"] = learned_vs_plain_large(timed)
             result["mixed_codes"] = mixed_codes(timed)
-        if world == 1 and rank == 0:
-            val, n, dt = oracle_rate(code, llr, L, mode)
-            result["cpu_baseline"] = {"value": val, "unit": "Gbit/s", "cores": cpu_threads(),
-                                      "kind": "oracle",
-                                      "sample": f"{n} frames of this workload, {L} iterations "
-                                                f"({dt:.1f} s on {cpu_threads()} threads)"}
+    if not args.quick and world == 1 and rank == 0:
+        val, n, dt = oracle_rate(code, llr, L, mode)
+        result["cpu_baseline"] = {"value": val, "unit": "Gbit/s", "cores": cpu_threads(),
+                                  "kind": "oracle",
+                                  "sample": f"{n} frames of this workload, {L} iterations "
+                                            f"({dt:.1f} s on {cpu_threads()} threads)"}
     if rank == 0:
         print(json.dumps(result))
     if world > 1:

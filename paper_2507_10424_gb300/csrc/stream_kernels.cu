@@ -495,6 +495,57 @@ __global__ void __launch_bounds__(128, D <= 8 ? 4 : 2)
 }
 
 // ------------------------------------------------------------------------------------
+// Final syndrome pass on the padded row layout (status of frames that never stopped): the
+// XOR of the decisions of a row's bits (eq. 1-2), every load of the row issued at once.
+// ------------------------------------------------------------------------------------
+template <int MODE, int VW, int D>
+__global__ void __launch_bounds__(128) k_syn_ell(const int32_t* __restrict__ ell_col,
+                                                 const uint8_t* __restrict__ ell_deg, int M,
+                                                 const typename Tr<MODE>::T* __restrict__ s, int Fp,
+                                                 const uint8_t* __restrict__ state,
+                                                 uint8_t* __restrict__ unsat, int paper) {
+    using A = typename Tr<MODE>::A;
+    using VT = Vec<typename Tr<MODE>::T, VW>;
+    using VS = Vec<uint8_t, VW>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 4 + warp;
+    const int f0 = (blockIdx.y * 32 + lane) * VW;
+    if (i >= M) return;
+    const VS st = *reinterpret_cast<const VS*>(state + f0);
+    const int d = __ldg(ell_deg + i);
+    int c[D];
+#pragma unroll
+    for (int q = 0; q < D / 4; q++) {
+        const int4 v = __ldg(reinterpret_cast<const int4*>(ell_col + (size_t)i * D) + q);
+        c[4 * q] = v.x;
+        c[4 * q + 1] = v.y;
+        c[4 * q + 2] = v.z;
+        c[4 * q + 3] = v.w;
+    }
+    uint32_t act = 0;
+#pragma unroll
+    for (int v = 0; v < VW; v++) act |= (uint32_t)(st.x[v] != 0) << v;
+    if (!act) return;
+    VT sv[D];
+#pragma unroll
+    for (int t = 0; t < D; t++)
+        if (t < d) sv[t] = ld_nc(reinterpret_cast<const VT*>(s + (size_t)c[t] * Fp + f0));
+    uint32_t z = 0;
+#pragma unroll
+    for (int t = 0; t < D; t++)
+        if (t < d) {
+#pragma unroll
+            for (int v = 0; v < VW; v++) z ^= slice((A)sv[t].x[v], paper) << v;
+        }
+    z &= act;
+    if (z) {
+#pragma unroll
+        for (int v = 0; v < VW; v++)
+            if ((z >> v) & 1) unsat[f0 + v] = 1;
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // Staged check pass (padded row layout): a persistent kernel in which every warp runs its
 // own pipeline of S shared-memory stages. A task is one row of one frame block (32 lanes x
 // VW frames); the warp's tasks are warp_id, warp_id + W_total, ... (rows fastest, so all
@@ -976,9 +1027,14 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
         launches += 2;
     }
     uint8_t* unf = w.unsat + (size_t)(a.L + 1) * Fp;
-    k_check<MODE, false, true, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp, state,
-                                                   unf, 1, w.n_done, a.frames, a.paper_slicer);
-    // (the final pass returns at once when every frame has stopped: their status is known)
+    if (g.ell_D == 8)
+        k_syn_ell<MODE, V, 8><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, Fp, state, unf, a.paper_slicer);
+    else if (g.ell_D == 16)
+        k_syn_ell<MODE, V, 16><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, Fp, state, unf, a.paper_slicer);
+    else
+        k_check<MODE, false, true, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp, state,
+                                                                 unf, 1, w.n_done, a.frames, a.paper_slicer);
+    // (frames that stopped early are skipped there: their status is known)
     k_store<MODE><<<dim3((a.N + 31) / 32, (a.frames + 31) / 32), dim3(32, 8), 0, st>>>(
         s, Fp, a.N, a.frames, a.out_bits, a.out_soft, a.paper_slicer);
     k_finish<<<(a.frames + 255) / 256, 256, 0, st>>>(w.done_iter, unf, a.frames, a.L, a.out_iters,
