@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=10)
     ap.add_argument("--variant", choices=["auto", "resident", "stream"], default="auto")
     ap.add_argument("--tuning", default="auto",
-                    help="resident launch shape 'FT,threads[,index placement]' instead of the autotuner")
+                    help="launch shape instead of the autotuner: resident 'FT,threads[,index "
+                         "placement]'; streaming 'warps per CTA,stages[,frames per lane]'")
     ap.add_argument("--quick", action="store_true", help="skip the extra measurements")
     ap.add_argument("--workload", choices=["qc2304", "irregular64800"], default="qc2304",
                     help="qc2304: the headline batch; irregular64800: the large irregular code "
@@ -174,7 +175,7 @@ def measured_peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCES = {"k_resident": "resident.cuh", "k_check_staged": "stream_kernels.cu"}
+KERNEL_SOURCES = {"k_resident": "resident.cuh"}
 
 
 def kernel_source_hash(kernel):
@@ -237,8 +238,7 @@ def other_workloads(timed):
         llr = torch.from_numpy(inputs.all_zero_awgn_llr(F, code.N, e, code.design_rate, 17)).cuda()
         for mode in ("fp32", "fixed"):
             dec = Decoder.from_code(code, mode=mode)
-            if dec.variant() == "resident":
-                dec.autotune(F, L)
+            dec.autotune(F, L)  # resident tile shape, or check-pass staging when streaming
             o = (torch.empty((F, code.N), dtype=torch.uint8, device="cuda"),
                  torch.empty(F, dtype=torch.int32, device="cuda"), None, None)
             ms = timed(lambda: dec.decode(llr, L, early_stop=True, out=o), 10, 3)
@@ -496,6 +496,14 @@ def main():
             dec.autotune(F, L)
         else:
             dec.set_tuning(*[int(v) for v in args.tuning.split(",")])
+    elif variant == "stream":  # check-pass staging (codes whose rows have at most 16 edges)
+        if args.tuning == "auto":
+            try:
+                dec.autotune(F, L)
+            except Exception:
+                pass
+        else:
+            dec.set_stream_staging(*[int(v) for v in args.tuning.split(",")])
     x = torch.from_numpy(llr).cuda()
     bits = torch.empty((F, code.N), dtype=torch.uint8, device="cuda")
     iters = torch.empty(F, dtype=torch.int32, device="cuda")
@@ -540,10 +548,13 @@ def main():
     peak, peak_kind = measured_peak_hbm()
     B = edge_message_bytes(code, mode)
     alg_bytes = F * L * B
-    kname = "k_resident" if variant == "resident" else "k_check_staged"
     achieved = alg_bytes / (ms * 1e-3) / 1e9
+    if variant == "resident":  # one launch per step: the step time is the kernel's
+        kname, traffic = "k_resident", ncu_traffic("k_resident", mode, F)
+    else:  # about 2 L + 5 launches per step: the figure is the whole decode's
+        kname, traffic = "the whole decode (check and variable passes, L iterations)", None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(kname, mode, F),
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": kname, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_frame_iteration": B}
 
@@ -562,7 +573,8 @@ def main():
         "config": {"workload": workload_name(code, F, L, args.workload), "frames_per_gpu": F, "iters": L,
                    "early_stop": False, "mode": mode, "variant": variant,
                    "tuning": (dict(zip(("frames_per_tile", "threads", "index_placement"), dec.tuning()))
-                              if variant == "resident" else None),
+                              if variant == "resident" else
+                              dict(zip(("warps_per_cta", "stages", "frames_per_lane"), dec.stream_staging()))),
                    "l2": f"inputs larger than L2 ({llr.nbytes / 1e6:.0f} MB of LLRs per step)"},
         "roofline": roofline,
         "gpu_launches": per_step_kernels * args.steps,

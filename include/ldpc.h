@@ -296,13 +296,18 @@ int ldpc_set_variant(ldpc_t *h, int32_t variant);
 int ldpc_set_tuning(ldpc_t *h, int32_t frames_per_tile, int32_t threads, int32_t index_placement);
 
 /*
- * ldpc_autotune: time the resident kernel's launch shapes (frames per tile x index
- * placement x CTA size)
- * on this device for this code and mode, on min(frames, 16384) frames of max_iter
- * iterations without early stop, and keep the fastest (as ldpc_set_tuning would).
- * Allocates and frees its own temporary device buffers; synchronises the handle's
- * stream. best_ms (nullable) receives the time of one decode of that many frames with
- * the chosen shape. LDPC_ERR_UNSUPPORTED when the code has no resident plan.
+ * ldpc_autotune: time launch shapes on this device for this code and mode, and keep the
+ * fastest.
+ *   - When the next decode runs the resident kernel: its frames per tile x index
+ *     placement x CTA size, on min(frames, 16384) frames (as ldpc_set_tuning would set).
+ *   - When it runs the streaming kernels: the staged check pass's warps per CTA x
+ *     stages, and the unstaged kernel, on min(frames, 2048) frames (as
+ *     ldpc_set_stream_staging would set).
+ * The timing uses max_iter iterations without early stop. Allocates and frees its own
+ * temporary device buffers; synchronises the handle's stream. best_ms (nullable) receives
+ * the time of one decode of that many frames with the chosen shape.
+ * LDPC_ERR_UNSUPPORTED when the code has no resident plan (resident), or no padded row
+ * layout, i.e. rows longer than 16 edges (streaming).
  */
 int ldpc_autotune(ldpc_t *h, int32_t frames, int32_t max_iter, float *best_ms);
 
@@ -327,9 +332,9 @@ int ldpc_set_stream_group(ldpc_t *h, int32_t frames_per_group);
  * bring one row's gathered posteriors s_j and old messages for 32 x frames_per_lane
  * frames, completing on an mbarrier, while the warp computes an earlier row (Section
  * III's row reductions).
- *   warps_per_cta in {0 (automatic: 8), 1..24};
+ *   warps_per_cta in {0 (automatic: 12), 1..12};
  *   stages in {-1 (off: one thread per row and frame vector loads its row itself),
- *              0 (automatic: 3), 2..8};
+ *              0 (automatic: 2), 2..8};
  *   frames_per_lane in {0 (automatic: the mode's 16-byte vector, 4 FP32 or 8 int16 frames),
  *                       1, 2, 4, 8 (at most the automatic width)}.
  * Results do not depend on the shape. A shape whose shared memory does not fit the device

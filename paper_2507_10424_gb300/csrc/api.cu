@@ -630,9 +630,78 @@ int ldpc_set_tuning(ldpc_t* h, int32_t frames_per_tile, int32_t threads, int32_t
     return LDPC_OK;
 }
 
+// Streaming codes: time the staged check pass's shapes (and the unstaged kernel) on
+// min(frames, 2048) frames through the regular decode path, and keep the fastest.
+static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
+    if (!h->dg.ell_D) return fail(LDPC_ERR_UNSUPPORTED);  // only the padded layout has shapes
+    const int32_t F = std::min<int32_t>(frames, 2048);
+    void* llr = nullptr;
+    uint8_t* bits = nullptr;
+    int32_t* iters = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (llr) cudaFree(llr);
+        if (bits) cudaFree(bits);
+        if (iters) cudaFree(iters);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&llr, (size_t)F * h->N * 4) != cudaSuccess ||
+        cudaMalloc((void**)&bits, (size_t)F * h->N) != cudaSuccess ||
+        cudaMalloc((void**)&iters, (size_t)F * 4) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return fail(LDPC_ERR_OOM);
+    }
+    // without early stop the work does not depend on the LLR values
+    if (cudaMemsetAsync(llr, 0, (size_t)F * h->N * 4, h->stream) != cudaSuccess) {
+        cleanup();
+        return fail(LDPC_ERR_CUDA);
+    }
+    const int32_t keep[3] = {h->st_warps, h->st_stages, h->st_vw};
+    static const int32_t shapes[][2] = {{8, 3}, {12, 2}, {6, 3}, {4, 4}, {8, 2}, {0, -1}};
+    float best = -1.0f;
+    int bi = -1;
+    for (int k = 0; k < (int)(sizeof(shapes) / sizeof(shapes[0])); k++) {
+        h->st_warps = shapes[k][0];
+        h->st_stages = shapes[k][1];
+        h->st_vw = 0;
+        float ms = 0.0f;
+        bool bad = ldpc_decode_ex(h, llr, LDPC_LLR_F32, F, max_iter, 0, 1, bits, iters, nullptr, nullptr) != LDPC_OK;
+        bad = bad || cudaEventRecord(e0, h->stream) != cudaSuccess;
+        for (int r = 0; r < 2 && !bad; r++)
+            bad = ldpc_decode_ex(h, llr, LDPC_LLR_F32, F, max_iter, 0, 1, bits, iters, nullptr, nullptr) != LDPC_OK;
+        bad = bad || cudaEventRecord(e1, h->stream) != cudaSuccess ||
+              cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess;
+        if (bad) {
+            cudaGetLastError();
+            continue;
+        }
+        if (best < 0.0f || ms < best) {
+            best = ms;
+            bi = k;
+        }
+    }
+    cleanup();
+    if (bi < 0) {
+        h->st_warps = keep[0];
+        h->st_stages = keep[1];
+        h->st_vw = keep[2];
+        return fail(LDPC_ERR_UNSUPPORTED);
+    }
+    h->st_warps = shapes[bi][0];
+    h->st_stages = shapes[bi][1];
+    h->st_vw = 0;
+    apply_staging(h, h->sw);
+    if (best_ms) *best_ms = best / 2.0f;
+    return LDPC_OK;
+}
+
 int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
     if (frames <= 0 || max_iter < 0) return fail(LDPC_ERR_INVALID_ARG);
+    if (resolved_variant(h) == LDPC_VARIANT_STREAM) return autotune_stream(h, frames, max_iter, best_ms);
     if (!h->dg.sliced || !h->plan[h->mode].ok) return fail(LDPC_ERR_UNSUPPORTED);
     const int32_t F = std::min<int32_t>(frames, 16384);
     void* llr = nullptr;
@@ -768,7 +837,7 @@ int ldpc_set_stream_group(ldpc_t* h, int32_t frames_per_group) {
 
 int ldpc_set_stream_staging(ldpc_t* h, int32_t warps_per_cta, int32_t stages, int32_t frames_per_lane) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
-    if (warps_per_cta < 0 || warps_per_cta > 24 || stages < -1 || stages == 1 || stages > 8 ||
+    if (warps_per_cta < 0 || warps_per_cta > 12 || stages < -1 || stages == 1 || stages > 8 ||
         (frames_per_lane != 0 && frames_per_lane != 1 && frames_per_lane != 2 && frames_per_lane != 4 &&
          frames_per_lane != 8))
         return fail(LDPC_ERR_INVALID_ARG);

@@ -197,7 +197,7 @@ struct StreamWork {
     int32_t num_sms = 0;
 };
 // Default staging of the streaming check pass (the shape chosen on GB300).
-constexpr int32_t kStageWarpsDefault = 8, kStagesDefault = 3;
+constexpr int32_t kStageWarpsDefault = 12, kStagesDefault = 2;
 
 // Launchers; return the number of kernels enqueued, or a negative status.
 // vw: frames per lane (0: a 16-byte vector, 4 fp32 / 8 int16; else 1, 2, 4 or 8 with the

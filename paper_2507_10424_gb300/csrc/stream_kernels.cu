@@ -66,6 +66,24 @@ __device__ __forceinline__ int8_t quantize(float x) {
     return (int8_t)__float2int_rn(t);
 }
 
+// Mark frames f0 + v (bit v of z) as having an unsatisfied check. Every check of a frame
+// reports to the same byte, so the flags are read first and only the missing ones are
+// written: after the first failing row, the other rows find the byte set and leave it
+// (tens of thousands of stores to the same few L2 lines otherwise serialise the pass).
+template <int VW>
+__device__ __forceinline__ void flag_unsat(uint8_t* unsat, int f0, uint32_t z) {
+    if (!z) return;
+    uint32_t have = 0;
+#pragma unroll
+    for (int v = 0; v < VW; v++) have |= (uint32_t)(((volatile const uint8_t*)unsat)[f0 + v] != 0) << v;
+    const uint32_t need = z & ~have;
+    if (need) {
+#pragma unroll
+        for (int v = 0; v < VW; v++)
+            if ((need >> v) & 1) unsat[f0 + v] = 1;
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // Per-frame state
 // ------------------------------------------------------------------------------------
@@ -189,14 +207,7 @@ __global__ void __launch_bounds__(128) k_check(const int32_t* __restrict__ row_p
         }
         if (!SYN_ONLY && longrow) *reinterpret_cast<VT*>(ep) = lv;  // stash lambda in place
     }
-    if (do_syn) {
-        z &= act;
-        if (z) {
-#pragma unroll
-            for (int v = 0; v < V; v++)
-                if ((z >> v) & 1) unsat[f0 + v] = 1;
-        }
-    }
+    if (do_syn) flag_unsat<V>(unsat, f0, z & act);
     if constexpr (!SYN_ONLY) {
     for (int t = 0; t < d; t++) {
         T* ep = eta + (size_t)(e0 + t) * Fp + f0;
@@ -484,14 +495,7 @@ __global__ void __launch_bounds__(128, D <= 8 ? 4 : 2)
     if (!do_syn) z = row_update<MODE, FIRST, false, false, W, VW, D>(row, d, erow, Fp, wt);
     else if (!paper) z = row_update<MODE, FIRST, true, false, W, VW, D>(row, d, erow, Fp, wt);
     else z = row_update<MODE, FIRST, true, true, W, VW, D>(row, d, erow, Fp, wt);
-    if (do_syn) {
-        z &= act;
-        if (z) {
-#pragma unroll
-            for (int v = 0; v < VW; v++)
-                if ((z >> v) & 1) unsat[f0 + v] = 1;
-        }
-    }
+    if (do_syn) flag_unsat<VW>(unsat, f0, z & act);
 }
 
 // ------------------------------------------------------------------------------------
@@ -537,12 +541,7 @@ __global__ void __launch_bounds__(128) k_syn_ell(const int32_t* __restrict__ ell
 #pragma unroll
             for (int v = 0; v < VW; v++) z ^= slice((A)sv[t].x[v], paper) << v;
         }
-    z &= act;
-    if (z) {
-#pragma unroll
-        for (int v = 0; v < VW; v++)
-            if ((z >> v) & 1) unsat[f0 + v] = 1;
-    }
+    flag_unsat<VW>(unsat, f0, z & act);
 }
 
 // ------------------------------------------------------------------------------------
@@ -641,7 +640,8 @@ struct StagedLayout {
 constexpr int kStagedMaxThreads = 384;
 
 // SYN: test the syndrome of the gathered s (the decision of the previous iteration).
-template <int MODE, bool FIRST, bool SYN, bool W, int VW, int D>
+// SYN_ONLY: the final syndrome pass (with FIRST: s copies only, no message update).
+template <int MODE, bool FIRST, bool SYN, bool W, int VW, int D, bool SYN_ONLY = false>
 __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const StagedArgs a,
                                                       const typename Tr<MODE>::T* __restrict__ s,
                                                       typename Tr<MODE>::T* __restrict__ eta,
@@ -683,6 +683,7 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
     int nx_d = 0, nx_c = 0, nx_cls = 0;  // its row data, loaded one step ahead
     uint32_t nx_act = 0;
     uint32_t pend = 0, phase = 0;        // per stage: copies in flight / parity awaited
+    uint32_t zacc = 0;                   // syndrome bits of this lane's frames, this frame block
     const uint64_t keep_s = policy_evict_last(), drop_eta = policy_evict_first();
 
     auto load_row = [&]() {
@@ -746,32 +747,44 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
         const uint32_t act = mw & 0xffu;
         const int d = (int)(mw >> 8);
         unsigned char* const st = buf + (size_t)q * LY::kStage;
-        if (act) {
+        if (SYN_ONLY && act) {  // XOR of the decisions of the row's bits
+            using A = typename Tr<MODE>::A;
+            using VP = Vec<T, VW>;
+            uint32_t z = 0;
+#pragma unroll
+            for (int t = 0; t < D; t++)
+                if (t < d) {
+                    const VP sv = *reinterpret_cast<const VP*>(st + (size_t)t * LY::kChunk + lane * sizeof(VP));
+#pragma unroll
+                    for (int v = 0; v < VW; v++) z ^= slice((A)sv.x[v], a.paper) << v;
+                }
+            zacc |= z & act;
+        } else if (act) {
             const int f0 = cy * FB + lane * VW;
             SmemRow<VT, D> row{st, LY::kChunk, lane,
                                reinterpret_cast<const int*>(meta + (size_t)q * LY::kMeta + 128), walpha,
                                wbeta};
             T* const erow = eta + (size_t)ci * D * a.Fp + f0;
             if constexpr (SYN) {
-                uint32_t z = a.paper ? row_update<MODE, FIRST, true, true, W, VW, D>(row, d, erow, a.Fp, wt)
-                                     : row_update<MODE, FIRST, true, false, W, VW, D>(row, d, erow, a.Fp, wt);
-                z &= act;
-                if (z) {
-#pragma unroll
-                    for (int v = 0; v < VW; v++)
-                        if ((z >> v) & 1) a.unsat[f0 + v] = 1;
-                }
+                const uint32_t z = a.paper ? row_update<MODE, FIRST, true, true, W, VW, D>(row, d, erow, a.Fp, wt)
+                                           : row_update<MODE, FIRST, true, false, W, VW, D>(row, d, erow, a.Fp, wt);
+                zacc |= z & act;
             } else {
                 row_update<MODE, FIRST, false, false, W, VW, D>(row, d, erow, a.Fp, wt);
             }
         }
         __syncwarp();
         issue(q);  // the task S steps ahead into the stage just read
+        const int py = cy;
         ci += di;
         cy += dy;
         if (ci >= M) {
             ci -= M;
             cy++;
+        }
+        if ((SYN || SYN_ONLY) && cy != py) {  // the warp's rows of this frame block are done
+            flag_unsat<VW>(a.unsat, py * FB + lane * VW, zacc);
+            zacc = 0;
         }
     }
 }
@@ -888,7 +901,7 @@ __global__ void k_finish(const int32_t* done_iter, const uint8_t* unsat_final, i
 
 // Launch of the staged check pass; false when the shape does not fit the device or the
 // task count does not fit 32 bits (the caller then runs the unstaged kernel).
-template <int MODE, int V, bool FIRST, bool W, int D>
+template <int MODE, int V, bool FIRST, bool W, int D, bool SYN_ONLY = false>
 bool launch_staged(const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
                    const typename Tr<MODE>::T* s, typename Tr<MODE>::T* eta, uint8_t* un,
                    int test_prev, const IterWeights& wt, cudaStream_t st) {
@@ -898,7 +911,9 @@ bool launch_staged(const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
     if (threads > kStagedMaxThreads) return false;
     const size_t smem = LY::warp_bytes(w.stages) * w.stage_warps + (W ? LY::kWeightBytes : 0);
     if (W && a.n_classes > 256) return false;
-    auto kern = test_prev ? k_check_staged<MODE, FIRST, true, W, V, D> : k_check_staged<MODE, FIRST, false, W, V, D>;
+    auto kern = SYN_ONLY ? k_check_staged<MODE, true, false, false, V, D, true>
+                : test_prev ? k_check_staged<MODE, FIRST, true, W, V, D>
+                            : k_check_staged<MODE, FIRST, false, W, V, D>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -1027,11 +1042,13 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
         launches += 2;
     }
     uint8_t* unf = w.unsat + (size_t)(a.L + 1) * Fp;
-    if (g.ell_D == 8)
-        k_syn_ell<MODE, V, 8><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, Fp, state, unf, a.paper_slicer);
-    else if (g.ell_D == 16)
-        k_syn_ell<MODE, V, 16><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, Fp, state, unf, a.paper_slicer);
-    else
+    if (g.ell_D == 8) {
+        if (!launch_staged<MODE, V, true, false, 8, true>(g, a, w, s, eta, unf, 1, IterWeights(), st))
+            k_syn_ell<MODE, V, 8><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, Fp, state, unf, a.paper_slicer);
+    } else if (g.ell_D == 16) {
+        if (!launch_staged<MODE, V, true, false, 16, true>(g, a, w, s, eta, unf, 1, IterWeights(), st))
+            k_syn_ell<MODE, V, 16><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, Fp, state, unf, a.paper_slicer);
+    } else
         k_check<MODE, false, true, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp, state,
                                                                  unf, 1, w.n_done, a.frames, a.paper_slicer);
     // (frames that stopped early are skipped there: their status is known)

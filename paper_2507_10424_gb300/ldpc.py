@@ -413,7 +413,8 @@ class Decoder:
         _check(load().ldpc_set_weights(self.h, a.shape[0], _host(a), _host(b)), "ldpc_set_weights")
 
     def autotune(self, frames: int, max_iter: int) -> float:
-        """Pick the fastest resident launch shape on this device; returns its time (ms)."""
+        """Pick the fastest launch shape on this device for the variant the next decode runs
+        (resident: tile shape; streaming: check-pass staging); returns its time (ms)."""
         import torch
         _check(load().ldpc_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
                "ldpc_set_stream")

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 # (warps per CTA, stages, frames per lane): unstaged, then staged shapes including the
 # smallest ones and narrower lanes than the mode's vector
-SHAPES = [(0, -1, 0), (1, 2, 0), (4, 3, 0), (8, 3, 0), (2, 8, 0), (24, 2, 2), (12, 2, 1)]
+SHAPES = [(0, -1, 0), (1, 2, 0), (4, 3, 0), (8, 3, 0), (2, 8, 0), (12, 2, 2), (12, 2, 1)]
 
 
 def staged_decode(torch, code, llr, L, mode, shape, early_stop=True, paper_slicer=False):
@@ -68,12 +68,12 @@ def test_staged_paper_slicer_and_random_codewords(torch_cuda, mode):
 def test_staging_settings_round_trip(torch_cuda):
     from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
     dec = Decoder.from_code(inputs.cfg_regular_576())
-    assert dec.stream_staging() == (8, 3, 0)
+    assert dec.stream_staging() == (12, 2, 0)
     dec.set_stream_staging(2, 5, 2)
     assert dec.stream_staging() == (2, 5, 2)
     dec.set_stream_staging(0, -1)
     assert dec.stream_staging()[1] == 0
-    for bad in ((25, 3, 0), (-1, 3, 0), (4, 1, 0), (4, 9, 0), (4, -2, 0), (4, 3, 3), (4, 3, 16)):
+    for bad in ((13, 3, 0), (-1, 3, 0), (4, 1, 0), (4, 9, 0), (4, -2, 0), (4, 3, 3), (4, 3, 16)):
         with pytest.raises(LdpcError):
             dec.set_stream_staging(*bad)
     dec.close()
@@ -100,4 +100,23 @@ def test_wait_that_runs_out_is_reported_and_the_next_decode_is_correct(torch_cud
     dec.check_device()
     got = (bits.cpu().numpy(), iters.cpu().numpy(), ok.cpu().numpy(), soft.cpu().numpy())
     assert_parity(got, oracle_decode(code, llr, 10, mode), mode, "after a timeout")
+    dec.close()
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fixed"])
+def test_autotune_picks_a_staging_and_keeps_results(torch_cuda, mode):
+    from paper_2507_10424_gb300.ldpc import Decoder
+    torch = torch_cuda
+    code = codes()["irregular1200"]
+    llr = inputs.all_zero_awgn_llr(700, code.N, 2.0, code.design_rate, 44)
+    dec = Decoder.from_code(code, mode=mode)
+    dec.set_variant("stream")
+    ms = dec.autotune(700, 12)
+    assert ms > 0
+    w, s, v = dec.stream_staging()
+    assert (s == 0) or (1 <= w <= 12 and 2 <= s <= 8)
+    bits, iters, ok, soft = dec.decode(torch.from_numpy(llr).cuda(), 12, want_ok=True, want_soft=True)
+    dec.check_device()
+    got = (bits.cpu().numpy(), iters.cpu().numpy(), ok.cpu().numpy(), soft.cpu().numpy())
+    assert_parity(got, oracle_decode(code, llr, 12, mode), mode, f"autotuned {(w, s, v)}")
     dec.close()
