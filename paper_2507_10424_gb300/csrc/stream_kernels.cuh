@@ -14,6 +14,8 @@
 //   k_var:   for every bit j and frame: s_j = r_j + sum of eta over M_j, ascending rows
 //            (eq. lambda_j); frames whose previous syndrome was zero are frozen there.
 // A final syndrome-only pass gives the status of frames that never stopped early.
+#pragma once
+
 #include "../../include/ldpc.h"
 #include "ldpc_internal.h"
 #include "packed16.cuh"
@@ -997,14 +999,15 @@ template <int MODE, int V>
 void check_pass(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, dim3 gc,
                 const typename Tr<MODE>::T* s, typename Tr<MODE>::T* eta, uint8_t* un,
                 int test_prev, bool first, const IterWeights& wt, cudaStream_t st) {
-    const bool wgt = MODE == kModeFP32 && wt.alpha != nullptr;
-    if (first) {
-        if (wgt) check_pass_t<MODE, V, true, true>(g, a, w, gc, s, eta, un, test_prev, wt, st);
-        else check_pass_t<MODE, V, true, false>(g, a, w, gc, s, eta, un, test_prev, wt, st);
-    } else {
-        if (wgt) check_pass_t<MODE, V, false, true>(g, a, w, gc, s, eta, un, test_prev, wt, st);
-        else check_pass_t<MODE, V, false, false>(g, a, w, gc, s, eta, un, test_prev, wt, st);
+    if constexpr (MODE == kModeFP32) {  // learned weights exist in FP32 mode only
+        if (wt.alpha != nullptr) {
+            if (first) check_pass_t<MODE, V, true, true>(g, a, w, gc, s, eta, un, test_prev, wt, st);
+            else check_pass_t<MODE, V, false, true>(g, a, w, gc, s, eta, un, test_prev, wt, st);
+            return;
+        }
     }
+    if (first) check_pass_t<MODE, V, true, false>(g, a, w, gc, s, eta, un, test_prev, wt, st);
+    else check_pass_t<MODE, V, false, false>(g, a, w, gc, s, eta, un, test_prev, wt, st);
 }
 
 template <int MODE, int V>
@@ -1063,54 +1066,9 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
 
 }  // namespace
 
-size_t stream_bytes(int mode, int32_t N, int64_t slots, int32_t Fp, int32_t L) {
-    size_t tb = mode == kModeFP32 ? 4 : 2, rb = mode == kModeFP32 ? 4 : 1;
-    return (size_t)slots * Fp * tb + (size_t)N * Fp * (tb + rb) + (size_t)Fp * 5 + (size_t)(L + 2) * Fp + 256;
-}
-
-StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t slots, int32_t Fp, int32_t L) {
-    // Fp is a multiple of 256, so every region below starts 256-byte aligned
-    const size_t tb = mode == kModeFP32 ? 4 : 2, rb = mode == kModeFP32 ? 4 : 1;
-    char* p = (char*)mem;
-    StreamWork w;
-    w.Fp = Fp;
-    w.eta = p;
-    p += (size_t)slots * Fp * tb;
-    w.s = p;
-    p += (size_t)N * Fp * tb;
-    w.r = p;
-    p += (size_t)N * Fp * rb;
-    w.done_iter = (int32_t*)p;
-    p += (size_t)Fp * 4;
-    w.state = (uint8_t*)p;
-    p += (size_t)Fp;
-    w.unsat = (uint8_t*)p;
-    p += (size_t)(L + 2) * Fp;
-    w.n_done = (int32_t*)p;
-    w.err = w.n_done + 1;
-    return w;
-}
-
-int stream_decode(int mode, const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
-                  cudaStream_t st, int vw) {
-    // vw: frames per lane (0 = the 16-byte vector of the mode); w.Fp is a multiple of 32 vw.
-    if (mode == kModeFP32) {
-        switch (vw) {
-            case 1: return run<kModeFP32, 1>(g, a, w, st);
-            case 2: return run<kModeFP32, 2>(g, a, w, st);
-            case 0:
-            case Tr<kModeFP32>::V: return run<kModeFP32, Tr<kModeFP32>::V>(g, a, w, st);
-            default: return LDPC_ERR_INVALID_ARG;
-        }
-    }
-    switch (vw) {
-        case 1: return run<kModeFixed, 1>(g, a, w, st);
-        case 2: return run<kModeFixed, 2>(g, a, w, st);
-        case 4: return run<kModeFixed, 4>(g, a, w, st);
-        case 0:
-        case Tr<kModeFixed>::V: return run<kModeFixed, Tr<kModeFixed>::V>(g, a, w, st);
-        default: return LDPC_ERR_INVALID_ARG;
-    }
-}
+// The streaming decode in one arithmetic mode (stream_fp32.cu, stream_fixed.cu); vw as for
+// stream_decode.
+int stream_decode_fp32(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_t st, int vw);
+int stream_decode_fixed(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_t st, int vw);
 
 }  // namespace ldpc_impl
