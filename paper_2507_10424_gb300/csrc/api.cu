@@ -660,13 +660,16 @@ static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* b
         return fail(LDPC_ERR_CUDA);
     }
     const int32_t keep[3] = {h->st_warps, h->st_stages, h->st_vw};
-    static const int32_t shapes[][2] = {{8, 3}, {12, 2}, {6, 3}, {4, 4}, {8, 2}, {0, -1}};
+    // (warps, stages, frames per lane): full and half-width lanes (half-width stages let rows
+    // of 16 slots fit more warps), and the unstaged kernel
+    static const int32_t shapes[][3] = {{8, 3, 0}, {12, 2, 0}, {6, 3, 0}, {4, 4, 0}, {8, 2, 0},
+                                        {12, 2, 2}, {8, 3, 2}, {0, -1, 0}};
     float best = -1.0f;
     int bi = -1;
     for (int k = 0; k < (int)(sizeof(shapes) / sizeof(shapes[0])); k++) {
         h->st_warps = shapes[k][0];
         h->st_stages = shapes[k][1];
-        h->st_vw = 0;
+        h->st_vw = shapes[k][2] ? (h->mode == kModeFP32 ? 2 : 4) : 0;
         float ms = 0.0f;
         bool bad = ldpc_decode_ex(h, llr, LDPC_LLR_F32, F, max_iter, 0, 1, bits, iters, nullptr, nullptr) != LDPC_OK;
         bad = bad || cudaEventRecord(e0, h->stream) != cudaSuccess;
@@ -692,7 +695,7 @@ static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* b
     }
     h->st_warps = shapes[bi][0];
     h->st_stages = shapes[bi][1];
-    h->st_vw = 0;
+    h->st_vw = shapes[bi][2] ? (h->mode == kModeFP32 ? 2 : 4) : 0;
     apply_staging(h, h->sw);
     if (best_ms) *best_ms = best / 2.0f;
     return LDPC_OK;

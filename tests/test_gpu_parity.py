@@ -431,3 +431,34 @@ def test_full_size_qc_2304_65536_frames_sampled(torch_cuda, mode):
     bn = bits.cpu().numpy()
     for f in rng.choice(F, 200, replace=False):
         assert okn[f] == (oracle.syndrome(g, bn[f])[0] == 0)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_full_size_irregular_64800_4096_frames_sampled(torch_cuda, mode):
+    """The large irregular code at the size `bench.py --workload irregular64800` times (4096
+    all-zero frames at 1.0 dB, 50 iterations without early stop, autotuned check-pass
+    staging), checked on sampled frames against the oracle, and the status flag against the
+    syndrome of the decided bits on more frames."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder
+    code = inputs.cfg_irregular_64800()
+    F = 4096
+    llr = inputs.all_zero_awgn_llr(F, code.N, 1.0, code.design_rate, 1000)
+    dec = Decoder.from_code(code, mode=mode)
+    dec.autotune(F, 50)
+    x = torch.from_numpy(llr).cuda()
+    bits, iters, ok, soft = dec.decode(x, 50, early_stop=False, want_ok=True, want_soft=True)
+    dec.check_device()
+    rng = np.random.default_rng(6)
+    sel = np.sort(np.concatenate([rng.choice(F, 6, replace=False), [0, F - 1]]))
+    want = oracle_decode(code, llr[sel], 50, mode, early_stop=False)
+    got = (bits[sel].cpu().numpy(), iters[sel].cpu().numpy(), ok[sel].cpu().numpy(),
+           soft[sel].cpu().numpy())
+    assert_parity(got, want, mode, f"full-size sample, staging {dec.stream_staging()}")
+    assert (iters == 50).all()
+    g = oracle.Graph.from_code(code)
+    okn = ok.cpu().numpy()
+    bn = bits.cpu().numpy()
+    for f in rng.choice(F, 64, replace=False):
+        assert okn[f] == (oracle.syndrome(g, bn[f])[0] == 0)
+    dec.close()
