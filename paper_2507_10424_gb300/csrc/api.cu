@@ -147,7 +147,7 @@ static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L, int32_t gran
         const size_t tb = 4, rb = 4;  // sized for fp32; the fixed mode uses less
         const size_t eta = (size_t)h->dg.eta_slots * Fp * tb, sb = (size_t)h->N * Fp * tb,
                      rr = (size_t)h->N * Fp * rb;
-        const size_t total = eta + sb + rr + (size_t)Fp * 4 + (size_t)Fp + 1024;
+        const size_t total = eta + sb + rr + (size_t)Fp * 12 + (size_t)Fp + 1024;
         cudaError_t e = cudaMalloc(&h->sw_big, total);
         if (e != cudaSuccess) {
             h->sw_big = nullptr;
@@ -163,7 +163,13 @@ static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L, int32_t gran
         p += (rr + 255) & ~(size_t)255;
         h->sw.done_iter = (int32_t*)p;
         p += (size_t)Fp * 4;
+        h->sw.pos2frame = (int32_t*)p;
+        p += (size_t)Fp * 4;
+        h->sw.new_pos = (int32_t*)p;
+        p += (size_t)Fp * 4;
         h->sw.state = (uint8_t*)p;
+        p += (size_t)Fp;
+        h->sw.comp = (int32_t*)p;  // Fp is a multiple of 32: 16-byte aligned
         h->sw_cap = Fp;
         h->sw_cap_L = -1;  // unsat depends on Fp too
     }

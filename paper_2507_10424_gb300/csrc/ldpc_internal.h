@@ -183,8 +183,13 @@ struct StreamWork {
     void* r = nullptr;         // [N][Fp] float / int8
     void* s = nullptr;         // [N][Fp] float / int16
     void* eta = nullptr;       // [eta_slots][Fp] float / int16
-    int32_t* done_iter = nullptr;  // [Fp]: iteration at which the frame stopped, -1 while running
-    uint8_t* state = nullptr;      // [Fp]: 1 while the frame is being decoded
+    int32_t* done_iter = nullptr;  // [Fp] by frame: iteration at which it stopped, -1 while running
+    uint8_t* state = nullptr;      // [Fp] by position: 1 while the frame there is being decoded
+    // frame compaction (early stop): the frame at each position (-1: none), the new position
+    // of each running frame, and [0] compaction pending, [1] positions in use, [2] frames kept
+    int32_t* pos2frame = nullptr;  // [Fp]
+    int32_t* new_pos = nullptr;    // [Fp]
+    int32_t* comp = nullptr;       // [4]
     uint8_t* unsat = nullptr;      // [(L+2)][Fp]
     int32_t* n_done = nullptr;     // [1]
     // staged check pass (padded row layout only): warps per CTA and shared-memory stages

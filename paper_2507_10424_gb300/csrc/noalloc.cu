@@ -79,7 +79,9 @@ extern "C" int ldpc_decode_noalloc(ldpc_t* h, const void* llr, int32_t llr_dtype
     const size_t o_s = o_eta + al256((size_t)v.dg->eta_slots * Fp * tb);
     const size_t o_r = o_s + al256((size_t)v.N * Fp * tb);
     const size_t o_done = o_r + al256((size_t)v.N * Fp * rb);
-    const size_t o_state = o_done + al256((size_t)Fp * 4);
+    const size_t o_p2f = o_done + al256((size_t)Fp * 4);
+    const size_t o_newpos = o_p2f + al256((size_t)Fp * 4);
+    const size_t o_state = o_newpos + al256((size_t)Fp * 4);
     const size_t o_unsat = o_state + al256((size_t)Fp);
     const size_t o_count = o_unsat + al256((size_t)(max_iter + 2) * Fp);
     const size_t need = o_count + 256;
@@ -96,6 +98,9 @@ extern "C" int ldpc_decode_noalloc(ldpc_t* h, const void* llr, int32_t llr_dtype
     w.state = (uint8_t*)(base + o_state);
     w.unsat = (uint8_t*)(base + o_unsat);
     w.n_done = (int32_t*)(base + o_count);
+    w.pos2frame = (int32_t*)(base + o_p2f);
+    w.new_pos = (int32_t*)(base + o_newpos);
+    w.comp = w.n_done + 4;  // in the 256 bytes after the done counter
     w.err = v.err;  // the handle's device error word (ldpc_check_device)
     w.num_sms = v.num_sms;
     w.stage_warps = v.stage_warps;

@@ -11,7 +11,7 @@ int stream_decode_fixed(const DevGraph& g, const DecodeArgs& a, const StreamWork
 
 size_t stream_bytes(int mode, int32_t N, int64_t slots, int32_t Fp, int32_t L) {
     size_t tb = mode == kModeFP32 ? 4 : 2, rb = mode == kModeFP32 ? 4 : 1;
-    return (size_t)slots * Fp * tb + (size_t)N * Fp * (tb + rb) + (size_t)Fp * 5 + (size_t)(L + 2) * Fp + 256;
+    return (size_t)slots * Fp * tb + (size_t)N * Fp * (tb + rb) + (size_t)Fp * 13 + (size_t)(L + 2) * Fp + 256;
 }
 
 StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t slots, int32_t Fp, int32_t L) {
@@ -28,12 +28,17 @@ StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t slots, int32_t F
     p += (size_t)N * Fp * rb;
     w.done_iter = (int32_t*)p;
     p += (size_t)Fp * 4;
+    w.pos2frame = (int32_t*)p;
+    p += (size_t)Fp * 4;
+    w.new_pos = (int32_t*)p;
+    p += (size_t)Fp * 4;
     w.state = (uint8_t*)p;
     p += (size_t)Fp;
     w.unsat = (uint8_t*)p;
     p += (size_t)(L + 2) * Fp;
-    w.n_done = (int32_t*)p;
+    w.n_done = (int32_t*)p;  // the last 256 bytes: counters
     w.err = w.n_done + 1;
+    w.comp = w.n_done + 4;
     return w;
 }
 

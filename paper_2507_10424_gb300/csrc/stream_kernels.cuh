@@ -89,11 +89,158 @@ __device__ __forceinline__ void flag_unsat(uint8_t* unsat, int f0, uint32_t z) {
 // ------------------------------------------------------------------------------------
 // Per-frame state
 // ------------------------------------------------------------------------------------
-__global__ void k_init_state(uint8_t* state, int32_t* done_iter, int Fp, int frames) {
+__global__ void k_init_state(uint8_t* state, int32_t* done_iter, int32_t* pos2frame, int32_t* comp,
+                             int Fp, int frames) {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f < Fp) {
         state[f] = f < frames;
         done_iter[f] = -1;
+        pos2frame[f] = f < frames ? f : -1;
+    }
+    if (f == 0) {
+        comp[0] = 0;       // no compaction pending
+        comp[1] = frames;  // positions in use
+        comp[2] = frames;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Frame compaction (early stop). Stopped frames leave holes in the frame-interleaved
+// arrays, and a frame block is skipped only when none of its frames runs. When at most half
+// of the positions in use still run, the running frames move to the front, in order, and
+// the blocks behind them go idle (a compaction moves about half an iteration's bytes, so it
+// pays when it halves the work of the iterations left):
+//   k_cmp_scan:  new position of every running frame (a prefix count), and the decision;
+//   k_cmp_emit:  decisions, soft values and status of the stopped frames that are still
+//                in place (their posteriors are about to be overwritten);
+//   k_cmp_rows:  every row of r, s, eta and the position -> frame map compacted in place
+//                (destinations never exceed sources, so a row is compacted chunk by chunk
+//                after reading each chunk whole);
+//   k_cmp_tail:  the frame states of the new layout, and the positions in use.
+// Every kernel returns at once when no compaction is pending.
+// ------------------------------------------------------------------------------------
+constexpr int kCmpThreads = 1024;
+
+__global__ void __launch_bounds__(kCmpThreads) k_cmp_scan(const uint8_t* __restrict__ state,
+                                                          int32_t* __restrict__ new_pos,
+                                                          int32_t* comp) {
+    __shared__ int part[kCmpThreads];
+    const int cur = comp[1];
+    const int per = (cur + kCmpThreads - 1) / kCmpThreads;
+    const int p0 = threadIdx.x * per, p1 = min(cur, p0 + per);
+    int n = 0;
+    for (int p = p0; p < p1; p++) n += state[p] != 0;
+    part[threadIdx.x] = n;
+    __syncthreads();
+    for (int o = 1; o < kCmpThreads; o <<= 1) {  // inclusive scan of the per-thread counts
+        const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const int total = part[kCmpThreads - 1];
+    const bool go = 2 * total <= cur && cur - total >= 64;
+    if (go) {
+        int q = part[threadIdx.x] - n;  // exclusive prefix
+        for (int p = p0; p < p1; p++) new_pos[p] = state[p] != 0 ? q++ : -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        comp[0] = go;
+        comp[2] = total;
+    }
+}
+
+template <int MODE>
+__global__ void k_cmp_emit(const typename Tr<MODE>::T* s, int Fp, int N, const uint8_t* state,
+                           const int32_t* pos2frame, const int32_t* done_iter, const int32_t* comp,
+                           uint8_t* bits, float* soft, int32_t* out_iters, uint8_t* out_ok, int paper) {
+    using A = typename Tr<MODE>::A;
+    if (!comp[0]) return;
+    __shared__ float tile[32][33];
+    __shared__ int32_t fr[32];
+    __shared__ int any;
+    const int cur = comp[1];
+    const int tj = (N + 31) / 32, tp = (cur + 31) / 32;
+    for (long long tt = blockIdx.x; tt < (long long)tj * tp; tt += gridDim.x) {  // 32 x 32 tiles
+        const int j0 = (int)(tt % tj) * 32, p0 = (int)(tt / tj) * 32;
+        __syncthreads();  // the previous tile is written out
+        if (threadIdx.x == 0 && threadIdx.y == 0) any = 0;
+        __syncthreads();
+        if (threadIdx.y == 0) {
+            const int p = p0 + threadIdx.x;
+            const int f = p < cur && state[p] == 0 ? pos2frame[p] : -1;  // stopped, in place
+            fr[threadIdx.x] = f;
+            if (f >= 0) {
+                any = 1;
+                if (j0 == 0) {
+                    out_iters[f] = done_iter[f];
+                    if (out_ok) out_ok[f] = 1;
+                }
+            }
+        }
+        __syncthreads();
+        if (!any) continue;
+        for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+            const int j = j0 + y, p = p0 + threadIdx.x;
+            tile[y][threadIdx.x] = (j < N && p < cur) ? (float)s[(size_t)j * Fp + p] : 0.0f;
+        }
+        __syncthreads();
+        for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+            const int f = fr[y], j = j0 + threadIdx.x;
+            if (f >= 0 && j < N) {
+                const float v = tile[threadIdx.x][y];  // exact for fp32 and int16 values
+                const size_t idx = (size_t)f * N + j;
+                bits[idx] = (uint8_t)slice((A)v, paper);
+                if (soft) soft[idx] = (MODE == kModeFP32) ? v : v * 0.25f;
+            }
+        }
+    }
+}
+
+// rows_deg / D (nullable): rows are padded-row slots, and slot i D + t with t >= deg(i)
+// holds nothing (skipped).
+template <typename E>
+__global__ void __launch_bounds__(256) k_cmp_rows(E* arr, long long n_rows, int Fp,
+                                                  const int32_t* __restrict__ new_pos,
+                                                  const int32_t* comp, const uint8_t* rows_deg = nullptr,
+                                                  int D = 1) {
+    if (!comp[0]) return;
+    constexpr int K = 8, CH = 256 * K;  // positions per chunk
+    const int cur = comp[1];
+    for (long long row = blockIdx.x; row < n_rows; row += gridDim.x) {
+        if (rows_deg && (int)(row % D) >= __ldg(rows_deg + row / D)) continue;
+        E* a = arr + row * Fp;
+        for (int c0 = 0; c0 < cur; c0 += CH) {
+            E v[K];
+            int d[K];
+#pragma unroll
+            for (int q = 0; q < K; q++) {
+                const int p = c0 + q * 256 + (int)threadIdx.x;
+                d[q] = p < cur ? new_pos[p] : -1;
+                if (d[q] >= 0) v[q] = a[p];
+            }
+            __syncthreads();  // the whole chunk is read before any of it is overwritten
+#pragma unroll
+            for (int q = 0; q < K; q++)
+                if (d[q] >= 0) a[d[q]] = v[q];
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kCmpThreads) k_cmp_tail(uint8_t* state, int32_t* pos2frame,
+                                                          int32_t* comp) {
+    if (!comp[0]) return;
+    const int cur = comp[1], kept = comp[2];
+    for (int p = threadIdx.x; p < cur; p += blockDim.x) {
+        state[p] = p < kept;  // every frame moved to the front is running
+        if (p >= kept) pos2frame[p] = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        comp[0] = 0;
+        comp[1] = kept;
     }
 }
 
@@ -802,6 +949,7 @@ __global__ void __launch_bounds__(128) k_var(const int32_t* __restrict__ col_ptr
                                              typename Tr<MODE>::T* s,
                                              const typename Tr<MODE>::T* __restrict__ eta, int Fp,
                                              uint8_t* state, int32_t* done_iter,
+                                             const int32_t* __restrict__ pos2frame,
                                              const uint8_t* __restrict__ unsat, int test_prev,
                                              int k, int* n_done, int frames) {
     using T = typename Tr<MODE>::T;
@@ -833,7 +981,7 @@ __global__ void __launch_bounds__(128) k_var(const int32_t* __restrict__ col_ptr
 #pragma unroll
             for (int v = 0; v < V; v++)
                 if ((conv >> v) & 1) {
-                    done_iter[f0 + v] = k - 1;
+                    done_iter[pos2frame[f0 + v]] = k - 1;
                     state[f0 + v] = 0;
                     atomicAdd(n_done, 1);
                 }
@@ -867,23 +1015,30 @@ __global__ void __launch_bounds__(128) k_var(const int32_t* __restrict__ col_ptr
     }
 }
 
-// s [N][Fp] -> bits (and soft) [frames][N]; 32 x 32 tiles.
+// s [N][Fp] (by position) -> bits (and soft) [frames][N] (by frame); 32 x 32 tiles.
 template <int MODE>
-__global__ void k_store(const typename Tr<MODE>::T* s, int Fp, int N, int frames, uint8_t* bits,
-                        float* soft, int paper) {
+__global__ void k_store(const typename Tr<MODE>::T* s, int Fp, int N, const int32_t* pos2frame,
+                        const int32_t* comp, uint8_t* bits, float* soft, int paper) {
     using A = typename Tr<MODE>::A;
     __shared__ float tile[32][33];
-    const int j0 = blockIdx.x * 32, f0 = blockIdx.y * 32;
+    __shared__ int32_t fr[32];
+    const int cur = comp[1];
+    const int j0 = blockIdx.x * 32, p0 = blockIdx.y * 32;
+    if (p0 >= cur) return;
+    if (threadIdx.y == 0) {
+        const int p = p0 + threadIdx.x;
+        fr[threadIdx.x] = p < cur ? pos2frame[p] : -1;
+    }
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        int j = j0 + y, f = f0 + threadIdx.x;
+        int j = j0 + y, p = p0 + threadIdx.x;
         float v = 0.0f;
-        if (j < N && f < frames) v = (float)s[(size_t)j * Fp + f];
+        if (j < N && p < cur) v = (float)s[(size_t)j * Fp + p];
         tile[y][threadIdx.x] = v;
     }
     __syncthreads();
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        int f = f0 + y, j = j0 + threadIdx.x;
-        if (f < frames && j < N) {
+        const int f = fr[y], j = j0 + threadIdx.x;
+        if (f >= 0 && j < N) {
             float v = tile[threadIdx.x][y];  // exact for fp32 and int16 values
             size_t idx = (size_t)f * N + j;
             bits[idx] = (uint8_t)slice((A)v, paper);
@@ -892,13 +1047,17 @@ __global__ void k_store(const typename Tr<MODE>::T* s, int Fp, int N, int frames
     }
 }
 
-__global__ void k_finish(const int32_t* done_iter, const uint8_t* unsat_final, int frames, int L,
-                         int32_t* out_iters, uint8_t* out_ok) {
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= frames) return;
-    int d = done_iter[f];
+// Status of the frames in the final layout (positions in use).
+__global__ void k_finish(const int32_t* done_iter, const int32_t* pos2frame, const int32_t* comp,
+                         const uint8_t* unsat_final, int Fp, int L, int32_t* out_iters,
+                         uint8_t* out_ok) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Fp || p >= comp[1]) return;
+    const int f = pos2frame[p];
+    if (f < 0) return;
+    const int d = done_iter[f];
     out_iters[f] = d >= 0 ? d : L;
-    if (out_ok) out_ok[f] = d >= 0 ? 1 : (unsat_final[f] == 0);
+    if (out_ok) out_ok[f] = d >= 0 ? 1 : (unsat_final[p] == 0);
 }
 
 // Launch of the staged check pass; false when the shape does not fit the device or the
@@ -1010,6 +1169,28 @@ void check_pass(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, dim
     else check_pass_t<MODE, V, false, false>(g, a, w, gc, s, eta, un, test_prev, wt, st);
 }
 
+// Frame compaction after an iteration (taking effect only when the scan decides so).
+constexpr int kCompactEvery = 4;  // iterations between compaction checks
+
+template <int MODE>
+int compact(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_t st) {
+    using T = typename Tr<MODE>::T;
+    using R = typename Tr<MODE>::R;
+    const int Fp = w.Fp;
+    k_cmp_scan<<<1, kCmpThreads, 0, st>>>(w.state, w.new_pos, w.comp);
+    const int blocks = std::max(1, std::min(65535, w.num_sms > 0 ? 8 * w.num_sms : 1024));
+    k_cmp_emit<MODE><<<blocks, dim3(32, 8), 0, st>>>(
+        (const T*)w.s, Fp, a.N, w.state, w.pos2frame, w.done_iter, w.comp, a.out_bits, a.out_soft,
+        a.out_iters, a.out_ok, a.paper_slicer);
+    k_cmp_rows<T><<<blocks, 256, 0, st>>>((T*)w.eta, (long long)g.eta_slots, Fp, w.new_pos, w.comp,
+                                          g.ell_D ? g.ell_deg : nullptr, g.ell_D ? g.ell_D : 1);
+    k_cmp_rows<T><<<blocks, 256, 0, st>>>((T*)w.s, (long long)a.N, Fp, w.new_pos, w.comp);
+    k_cmp_rows<R><<<blocks, 256, 0, st>>>((R*)w.r, (long long)a.N, Fp, w.new_pos, w.comp);
+    k_cmp_rows<int32_t><<<1, 256, 0, st>>>(w.pos2frame, 1, Fp, w.new_pos, w.comp);
+    k_cmp_tail<<<1, kCmpThreads, 0, st>>>(w.state, w.pos2frame, w.comp);
+    return 7;
+}
+
 template <int MODE, int V>
 int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_t st) {
     using T = typename Tr<MODE>::T;
@@ -1022,7 +1203,8 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
     if (cudaMemsetAsync(w.n_done, 0, sizeof(int32_t), st) != cudaSuccess) return LDPC_ERR_CUDA;
     if (cudaMemsetAsync(w.unsat, 0, (size_t)(a.L + 2) * Fp, st) != cudaSuccess) return LDPC_ERR_CUDA;
     uint8_t* state = w.state;
-    k_init_state<<<(Fp + 255) / 256, 256, 0, st>>>(state, w.done_iter, Fp, a.frames);
+    k_init_state<<<(Fp + 255) / 256, 256, 0, st>>>(state, w.done_iter, w.pos2frame, w.comp, Fp,
+                                                    a.frames);
     launches++;
     k_load<MODE><<<dim3((a.N + 31) / 32, Fp / 32), dim3(32, 8), 0, st>>>(a.llr, a.llr_is_i8, a.frames,
                                                                         a.N, r, s, Fp);
@@ -1041,8 +1223,11 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
         }
         check_pass<MODE, V>(g, a, w, gc, s, eta, un, test_prev, k == 1, wt, st);
         k_var<MODE, V><<<gv, 128, 0, st>>>(g.col_ptr, cslot, a.N, r, s, eta, Fp, state,
-                                        w.done_iter, un, test_prev, k, w.n_done, a.frames);
+                                        w.done_iter, w.pos2frame, un, test_prev, k, w.n_done,
+                                        a.frames);
         launches += 2;
+        if (a.early_stop && k < a.L && k % kCompactEvery == 0 && w.comp)
+            launches += compact<MODE>(g, a, w, st);
     }
     uint8_t* unf = w.unsat + (size_t)(a.L + 1) * Fp;
     if (g.ell_D == 8) {
@@ -1055,10 +1240,10 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
         k_check<MODE, false, true, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp, state,
                                                                  unf, 1, w.n_done, a.frames, a.paper_slicer);
     // (frames that stopped early are skipped there: their status is known)
-    k_store<MODE><<<dim3((a.N + 31) / 32, (a.frames + 31) / 32), dim3(32, 8), 0, st>>>(
-        s, Fp, a.N, a.frames, a.out_bits, a.out_soft, a.paper_slicer);
-    k_finish<<<(a.frames + 255) / 256, 256, 0, st>>>(w.done_iter, unf, a.frames, a.L, a.out_iters,
-                                                     a.out_ok);
+    k_store<MODE><<<dim3((a.N + 31) / 32, Fp / 32), dim3(32, 8), 0, st>>>(
+        s, Fp, a.N, w.pos2frame, w.comp, a.out_bits, a.out_soft, a.paper_slicer);
+    k_finish<<<(Fp + 255) / 256, 256, 0, st>>>(w.done_iter, w.pos2frame, w.comp, unf, Fp, a.L,
+                                               a.out_iters, a.out_ok);
     launches += 3;
     if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
     return launches;
