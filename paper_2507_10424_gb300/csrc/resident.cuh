@@ -179,19 +179,30 @@ __device__ __forceinline__ int snake(int k, int nth) {
     return k * nth + ((k & 1) ? (nth - 1 - (int)threadIdx.x) : (int)threadIdx.x);
 }
 
-// Phase A for every row lane of the CTA's tile. Sweep 1 forms lambda for every edge,
-// keeps min0 and min1 (Observation 1) and the XOR of the sign bits (Observation 2), and
-// stashes lambda in the edge's slot; sweep 2 turns each stashed lambda into the new
-// message: magnitude min1 where |lambda| = min0 (on a tie min1 = min0, so the first
-// location needs no tracking), else min0; sign = total sign x own sign.
-template <int MODE, int FT, bool FIRST, bool SYN, bool UPD, bool PAPER, bool W>
-__device__ __forceinline__ void phase_a(const Idx& ix, VecR<typename RT<MODE>::T, FT>* eta,
-                                        const VecR<typename RT<MODE>::T, FT>* s, int n_rtasks,
-                                        uint32_t* unsat_w) {
+// ---------------------------------------------------------------------------------------
+// The edge-slot array holds lambda after the column pass and the new message after the row
+// pass (each edge belongs to one row and one column, so the passes never touch a slot
+// twice at once):
+//   init       lambda = r of the edge's bit (eta^prev = 0 in the first iteration);
+//   rows       Observation 1 (min0, min1: on a tie min1 = min0, so the first location needs
+//              no tracking) and Observation 2 (XOR of the sign bits) over the row's lambdas,
+//              then eta = +-(min1 where |lambda| = min0, else min0), sign = total x own
+//              (eq. eta_update);
+//   columns    s = r + the column's eta in ascending row order (eq. lambda_j), then
+//              lambda = s - eta (saturated in fixed point) into each of the column's slots;
+//   syndrome   the XOR of the decisions of the row's bits, gathered from s (eq. 1-2), on the
+//              iterations that test it.
+// The row pass reads its slots contiguously: no gather of s and no index read per edge.
+// ---------------------------------------------------------------------------------------
+
+// Row pass, per frame. lambda is read twice (two sweeps) and overwritten by eta.
+template <int MODE, int FT, bool W>
+__device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
+                                          int n_rtasks) {
     using T = typename RT<MODE>::T;
     using A = typename RT<MODE>::A;
     using VT = VecR<T, FT>;
-    constexpr int UNR = FT >= 4 ? 2 : 4;  // unrolling of the edge sweeps, bounded by registers
+    constexpr int UNR = FT >= 4 ? 2 : 4;
     const int nth = blockDim.x;
     for (int k = 0;; k++) {
         const int task = snake(k, nth);  // strictly increasing in k
@@ -200,77 +211,56 @@ __device__ __forceinline__ void phase_a(const Idx& ix, VecR<typename RT<MODE>::T
         if (d == 0) continue;
         const int base = ix.r_base[task >> 5] + (task & 31);
         A min0[FT], min1[FT];
-        uint32_t sx[FT], zx[FT];
+        uint32_t sx[FT];
 #pragma unroll
         for (int f = 0; f < FT; f++) {
             min0[f] = rbig(A());
             min1[f] = rbig(A());
             sx[f] = 0;
-            zx[f] = 0;
+        }
+#pragma unroll UNR
+        for (int t = 0; t < d; t++) {
+            const VT lv = slots[base + 32 * t];
+#pragma unroll
+            for (int f = 0; f < FT; f++) {
+                const A lam = (A)lv.x[f];
+                const A m = rabs(lam);
+                min1[f] = min(min1[f], max(min0[f], m));
+                min0[f] = min(min0[f], m);
+                sx[f] ^= bits_of(lam);
+            }
         }
 #pragma unroll UNR
         for (int t = 0; t < d; t++) {
             const int slot = base + 32 * t;
-            const VT sv = s[ix.r_slot_pos[slot]];
-            if (SYN) {
-#pragma unroll
-                for (int f = 0; f < FT; f++) zx[f] ^= dec_bits<PAPER>((A)sv.x[f]);
+            const VT lv = slots[slot];
+            float wa = 1.0f, wb = 0.0f;
+            if constexpr (W) {
+                const int c = ix.wcls[slot];
+                wa = ix.walpha[c];
+                wb = ix.wbeta[c];
             }
-            if (UPD) {
-                VT ev;
-                if (!FIRST) ev = eta[slot];
-                VT lv;
+            VT out;
 #pragma unroll
-                for (int f = 0; f < FT; f++) {
-                    const A lam = FIRST ? (A)sv.x[f] : lam_sat((A)sv.x[f], (A)ev.x[f]);
-                    const A m = rabs(lam);
-                    min1[f] = min(min1[f], max(min0[f], m));
-                    min0[f] = min(min0[f], m);
-                    sx[f] ^= bits_of(lam);
-                    lv.x[f] = (T)lam;
+            for (int f = 0; f < FT; f++) {
+                const A lam = (A)lv.x[f];
+                A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
+                if constexpr (W) {  // max(fma(alpha, m, -beta), 0)
+                    const float x = __fmaf_rn(wa, (float)m, -wb);
+                    m = (A)(x > 0.0f ? x : 0.0f);
                 }
-                eta[slot] = lv;  // stash lambda for sweep 2
+                out.x[f] = (T)with_sign(m, bits_of(lam) ^ sx[f]);
             }
-        }
-        if (SYN) {
-            uint32_t z = 0;
-#pragma unroll
-            for (int f = 0; f < FT; f++) z |= (zx[f] >> 31) << f;
-            if (z) atomicOr(unsat_w, z);
-        }
-        if (UPD) {
-#pragma unroll UNR
-            for (int t = 0; t < d; t++) {
-                const int slot = base + 32 * t;
-                const VT lv = eta[slot];
-                float wa = 1.0f, wb = 0.0f;
-                if constexpr (W) {
-                    const int c = ix.wcls[slot];
-                    wa = ix.walpha[c];
-                    wb = ix.wbeta[c];
-                }
-                VT out;
-#pragma unroll
-                for (int f = 0; f < FT; f++) {
-                    const A lam = (A)lv.x[f];
-                    A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
-                    if constexpr (W) {  // max(fma(alpha, m, -beta), 0)
-                        const float x = __fmaf_rn(wa, (float)m, -wb);
-                        m = (A)(x > 0.0f ? x : 0.0f);
-                    }
-                    out.x[f] = (T)with_sign(m, bits_of(lam) ^ sx[f]);
-                }
-                eta[slot] = out;
-            }
+            slots[slot] = out;
         }
     }
 }
 
 // ---------------------------------------------------------------------------------------
 // Fixed point with an even number of interleaved frames: the int16 values of two frames
-// share a 32-bit word (frame 2p in the low half, 2p + 1 in the high half) and phase A
-// works on the pair at once with the packed 16-bit min / max / add instructions. Every
-// step is exact, so the results are those of the per-frame code above:
+// share a 32-bit word (frame 2p in the low half, 2p + 1 in the high half) and the passes
+// work on the pair at once with the packed 16-bit min / max / add instructions. Every
+// step is exact, so the results are those of the per-frame code:
 //   lambda = sat(s - eta): two 32-bit differences, saturated and packed by one
 //            conversion (to [-32768, 32767]), then max with -32767 (symmetric limit);
 //   |lambda| = max(lambda, -lambda), -x = ~x + 1 lane by lane;
@@ -279,17 +269,13 @@ __device__ __forceinline__ void phase_a(const Idx& ix, VecR<typename RT<MODE>::T
 //            min(|lambda| - min0, 1) is 0 there and 1 elsewhere), conditional negation
 //            by (m ^ mask) + (mask & 1) with the lane mask of the new sign.
 // ---------------------------------------------------------------------------------------
-
-
-template <int FT, bool FIRST, bool SYN, bool UPD, bool PAPER>
-__device__ __forceinline__ void phase_a_packed(const Idx& ix, VecR<int16_t, FT>* eta_v,
-                                               const VecR<int16_t, FT>* s_v, int n_rtasks,
-                                               uint32_t* unsat_w) {
+template <int FT>
+__device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT>* slots_v,
+                                                 int n_rtasks) {
     constexpr int P = FT / 2;
     using WT = Words<P>;
     constexpr int UNR = FT >= 4 ? 2 : 4;
-    WT* eta = reinterpret_cast<WT*>(eta_v);
-    const WT* s = reinterpret_cast<const WT*>(s_v);
+    WT* slots = reinterpret_cast<WT*>(slots_v);
     const int nth = blockDim.x;
     for (int k = 0;; k++) {
         const int task = snake(k, nth);
@@ -297,167 +283,272 @@ __device__ __forceinline__ void phase_a_packed(const Idx& ix, VecR<int16_t, FT>*
         const int d = ix.r_deg[task];
         if (d == 0) continue;
         const int base = ix.r_base[task >> 5] + (task & 31);
-        uint32_t min0[P], min1[P], sx[P], zx[P];
+        uint32_t min0[P], min1[P], sx[P];
 #pragma unroll
         for (int p = 0; p < P; p++) {
             min0[p] = 0x7fff7fffu;
             min1[p] = 0x7fff7fffu;
             sx[p] = 0;
-            zx[p] = 0;
         }
+#pragma unroll UNR
+        for (int t = 0; t < d; t++) {
+            const WT lv = slots[base + 32 * t];
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                const uint32_t lam = lv.w[p];
+                const uint32_t m = p_max(lam, p_neg(lam));
+                min1[p] = p_min(min1[p], p_max(min0[p], m));
+                min0[p] = p_min(min0[p], m);
+                sx[p] ^= lam;
+            }
+        }
+        uint32_t nmin0[P];
+#pragma unroll
+        for (int p = 0; p < P; p++) nmin0[p] = p_neg(min0[p]);
 #pragma unroll UNR
         for (int t = 0; t < d; t++) {
             const int slot = base + 32 * t;
-            const WT sv = s[ix.r_slot_pos[slot]];
-            if (SYN) {
-#pragma unroll
-                for (int p = 0; p < P; p++) zx[p] ^= PAPER ? p_neg(sv.w[p]) : sv.w[p];
-            }
-            if (UPD) {
-                WT ev;
-                if (!FIRST) ev = eta[slot];
-                WT lv;
-#pragma unroll
-                for (int p = 0; p < P; p++) {
-                    const uint32_t lam =
-                        FIRST ? sv.w[p]
-                              : p_pack_sat(p_lo(sv.w[p]) - p_lo(ev.w[p]), p_hi(sv.w[p]) - p_hi(ev.w[p]));
-                    const uint32_t m = p_max(lam, p_neg(lam));
-                    min1[p] = p_min(min1[p], p_max(min0[p], m));
-                    min0[p] = p_min(min0[p], m);
-                    sx[p] ^= lam;
-                    lv.w[p] = lam;
-                }
-                eta[slot] = lv;  // stash lambda for sweep 2
-            }
-        }
-        if (SYN) {
-            uint32_t z = 0;
-#pragma unroll
-            for (int p = 0; p < P; p++) z |= (((zx[p] >> 15) & 1u) | ((zx[p] >> 30) & 2u)) << (2 * p);
-            if (z) atomicOr(unsat_w, z);
-        }
-        if (UPD) {
-            uint32_t nmin0[P];
-#pragma unroll
-            for (int p = 0; p < P; p++) nmin0[p] = p_neg(min0[p]);
-#pragma unroll UNR
-            for (int t = 0; t < d; t++) {
-                const int slot = base + 32 * t;
-                const WT lv = eta[slot];
-                WT out;
-#pragma unroll
-                for (int p = 0; p < P; p++) {
-                    const uint32_t lam = lv.w[p];
-                    const uint32_t a = p_max(lam, p_neg(lam));
-                    const uint32_t ne = p_spread(p_min(p_add(a, nmin0[p]), 0x00010001u));
-                    const uint32_t m = (min0[p] & ne) | (min1[p] & ~ne);
-                    const uint32_t sb = ((lam ^ sx[p]) >> 15) & 0x00010001u;
-                    out.w[p] = p_add(m ^ p_spread(sb), sb);
-                }
-                eta[slot] = out;
-            }
-        }
-    }
-}
-
-// Phase B of the packed fixed-point form: 32-bit sums, saturated and packed at the end.
-template <int FT>
-__device__ __forceinline__ void phase_b_packed(const Idx& ix, const VecR<int16_t, FT>* eta_v,
-                                               VecR<int16_t, FT>* s_v, const VecR<int16_t, FT>* r_v,
-                                               int N) {
-    constexpr int P = FT / 2;
-    using WT = Words<P>;
-    const WT* eta = reinterpret_cast<const WT*>(eta_v);
-    WT* s = reinterpret_cast<WT*>(s_v);
-    const WT* r = reinterpret_cast<const WT*>(r_v);
-    const int nth = blockDim.x;
-    for (int k = 0;; k++) {
-        const int p0 = snake(k, nth);
-        if (p0 >= N) break;
-        const int d = ix.c_deg[p0];
-        const int base = ix.c_base[p0 >> 5] + (p0 & 31);
-        const WT rv = r[p0];
-        int32_t lo[P], hi[P];
-#pragma unroll
-        for (int p = 0; p < P; p++) {
-            lo[p] = p_lo(rv.w[p]);
-            hi[p] = p_hi(rv.w[p]);
-        }
-#pragma unroll 4
-        for (int t = 0; t < d; t++) {
-            const WT ev = eta[ix.c_slot[base + 32 * t]];
+            const WT lv = slots[slot];
+            WT out;
 #pragma unroll
             for (int p = 0; p < P; p++) {
-                lo[p] += p_lo(ev.w[p]);
-                hi[p] += p_hi(ev.w[p]);
+                const uint32_t lam = lv.w[p];
+                const uint32_t a = p_max(lam, p_neg(lam));
+                const uint32_t ne = p_spread(p_min(p_add(a, nmin0[p]), 0x00010001u));
+                const uint32_t m = (min0[p] & ne) | (min1[p] & ~ne);
+                const uint32_t sb = ((lam ^ sx[p]) >> 15) & 0x00010001u;
+                out.w[p] = p_add(m ^ p_spread(sb), sb);
             }
+            slots[slot] = out;
         }
-        WT out;
-#pragma unroll
-        for (int p = 0; p < P; p++) out.w[p] = p_pack_sat(lo[p], hi[p]);
-        s[p0] = out;
     }
 }
 
-// Phase A in the packed form where it applies (fixed point, even FT), else per frame.
-template <int MODE, int FT, bool FIRST, bool SYN, bool UPD, bool PAPER, bool W>
-__device__ __forceinline__ void phase_a_sel(const Idx& ix, VecR<typename RT<MODE>::T, FT>* eta,
-                                            const VecR<typename RT<MODE>::T, FT>* s, int n_rtasks,
-                                            uint32_t* uw) {
-    if constexpr (MODE == kModeFixed && FT % 2 == 0)
-        phase_a_packed<FT, FIRST, SYN, UPD, PAPER>(ix, eta, s, n_rtasks, uw);
-    else
-        phase_a<MODE, FT, FIRST, SYN, UPD, PAPER, W>(ix, eta, s, n_rtasks, uw);
-}
-
-// One phase A of the iteration, specialised on (first, syndrome, update).
-template <int MODE, int FT, bool PAPER, bool W>
-__device__ __forceinline__ void phase_a_any(bool first, bool syn, bool upd, const Idx& ix,
-                                            VecR<typename RT<MODE>::T, FT>* eta,
-                                            const VecR<typename RT<MODE>::T, FT>* s, int n_rtasks,
-                                            uint32_t* uw) {
-#define LDPC_PHASE_A(F, S, U) phase_a_sel<MODE, FT, F, S, U, PAPER, W>(ix, eta, s, n_rtasks, uw)
-    if (first) {
-        if (!upd) LDPC_PHASE_A(true, true, false);
-        else if (syn) LDPC_PHASE_A(true, true, true);
-        else LDPC_PHASE_A(true, false, true);
-    } else {
-        if (!upd) LDPC_PHASE_A(false, true, false);
-        else if (syn) LDPC_PHASE_A(false, true, true);
-        else LDPC_PHASE_A(false, false, true);
-    }
-#undef LDPC_PHASE_A
-}
-
-// Phase B for every column position of the tile.
-template <int MODE, int FT>
-__device__ __forceinline__ void phase_b(const Idx& ix, const VecR<typename RT<MODE>::T, FT>* eta,
-                                        VecR<typename RT<MODE>::T, FT>* s,
-                                        const VecR<typename RT<MODE>::T, FT>* r, int N) {
+// Syndrome of the current s for every row: bit f of the row's result is set when frame f
+// fails the check; the CTA's word collects them.
+template <int MODE, int FT, bool PAPER>
+__device__ __forceinline__ void syn_pass(const Idx& ix, const VecR<typename RT<MODE>::T, FT>* s,
+                                         int n_rtasks, uint32_t* unsat_w) {
     using T = typename RT<MODE>::T;
     using A = typename RT<MODE>::A;
     using VT = VecR<T, FT>;
+    const int nth = blockDim.x;
+    for (int k = 0;; k++) {
+        const int task = snake(k, nth);
+        if (task >= n_rtasks) break;
+        const int d = ix.r_deg[task];
+        if (d == 0) continue;
+        const int base = ix.r_base[task >> 5] + (task & 31);
+        uint32_t zx[FT];
+#pragma unroll
+        for (int f = 0; f < FT; f++) zx[f] = 0;
+#pragma unroll 4
+        for (int t = 0; t < d; t++) {
+            const VT sv = s[ix.r_slot_pos[base + 32 * t]];
+#pragma unroll
+            for (int f = 0; f < FT; f++) zx[f] ^= dec_bits<PAPER>((A)sv.x[f]);
+        }
+        uint32_t z = 0;
+#pragma unroll
+        for (int f = 0; f < FT; f++) z |= (zx[f] >> 31) << f;
+        if (z) atomicOr(unsat_w, z);
+    }
+}
+
+// First lambda of every edge: the channel value of its bit.
+template <int MODE, int FT>
+__device__ __forceinline__ void init_pass(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
+                                          const VecR<typename RT<MODE>::T, FT>* r, int N) {
     const int nth = blockDim.x;
     for (int k = 0;; k++) {
         const int p = snake(k, nth);
         if (p >= N) break;
         const int d = ix.c_deg[p];
         const int base = ix.c_base[p >> 5] + (p & 31);
-        const VT rv = r[p];
-        A acc[FT];
+        const auto rv = r[p];
+        for (int t = 0; t < d; t++) slots[ix.c_slot[base + 32 * t]] = rv;
+    }
+}
+
+// One column of exactly DC edges, per frame: s = r + sum of eta (ascending rows), then
+// lambda = s - eta into each of its slots. Fully unrolled: slots and messages stay in
+// registers between the two loops, and no predicated-off iteration is issued.
+template <int MODE, int FT, int DC>
+__device__ __forceinline__ void col_fixed(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
+                                          VecR<typename RT<MODE>::T, FT>* s,
+                                          const VecR<typename RT<MODE>::T, FT>& rv, int p, int base) {
+    using T = typename RT<MODE>::T;
+    using A = typename RT<MODE>::A;
+    using VT = VecR<T, FT>;
+    A acc[FT];
 #pragma unroll
-        for (int f = 0; f < FT; f++) acc[f] = (A)rv.x[f];
-#pragma unroll 4
-        for (int t = 0; t < d; t++) {
-            const VT ev = eta[ix.c_slot[base + 32 * t]];
+    for (int f = 0; f < FT; f++) acc[f] = (A)rv.x[f];
+    int sl[DC];
+    VT ev[DC];
 #pragma unroll
-            for (int f = 0; f < FT; f++) acc[f] = acc[f] + (A)ev.x[f];
+    for (int t = 0; t < DC; t++) {
+        sl[t] = ix.c_slot[base + 32 * t];
+        ev[t] = slots[sl[t]];
+#pragma unroll
+        for (int f = 0; f < FT; f++) acc[f] = acc[f] + (A)ev[t].x[f];
+    }
+    VT out;
+#pragma unroll
+    for (int f = 0; f < FT; f++) out.x[f] = (T)rsat_out(acc[f]);
+    s[p] = out;
+#pragma unroll
+    for (int t = 0; t < DC; t++) {
+        VT lv;
+#pragma unroll
+        for (int f = 0; f < FT; f++) lv.x[f] = (T)lam_sat((A)out.x[f], (A)ev[t].x[f]);
+        slots[sl[t]] = lv;
+    }
+}
+
+// A column of any degree: the second loop reads its slots and messages again.
+template <int MODE, int FT>
+__device__ __forceinline__ void col_any(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
+                                        VecR<typename RT<MODE>::T, FT>* s,
+                                        const VecR<typename RT<MODE>::T, FT>& rv, int p, int base,
+                                        int d) {
+    using T = typename RT<MODE>::T;
+    using A = typename RT<MODE>::A;
+    using VT = VecR<T, FT>;
+    A acc[FT];
+#pragma unroll
+    for (int f = 0; f < FT; f++) acc[f] = (A)rv.x[f];
+    for (int t = 0; t < d; t++) {
+        const VT ev = slots[ix.c_slot[base + 32 * t]];
+#pragma unroll
+        for (int f = 0; f < FT; f++) acc[f] = acc[f] + (A)ev.x[f];
+    }
+    VT out;
+#pragma unroll
+    for (int f = 0; f < FT; f++) out.x[f] = (T)rsat_out(acc[f]);
+    s[p] = out;
+    for (int t = 0; t < d; t++) {
+        const int slot = ix.c_slot[base + 32 * t];
+        const VT ev = slots[slot];
+        VT lv;
+#pragma unroll
+        for (int f = 0; f < FT; f++) lv.x[f] = (T)lam_sat((A)out.x[f], (A)ev.x[f]);
+        slots[slot] = lv;
+    }
+}
+
+// Packed fixed point: 32-bit sums, saturated and packed at the end, then the packed
+// saturating differences.
+__device__ __forceinline__ uint32_t p_lam(uint32_t sw, uint32_t ew) {
+    return p_pack_sat(p_lo(sw) - p_lo(ew), p_hi(sw) - p_hi(ew));
+}
+
+template <int FT, int DC>
+__device__ __forceinline__ void col_fixed_packed(const Idx& ix, Words<FT / 2>* slots, Words<FT / 2>* s,
+                                                 const Words<FT / 2>& rv, int p0, int base) {
+    constexpr int P = FT / 2;
+    using WT = Words<P>;
+    int32_t lo[P], hi[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+        lo[p] = p_lo(rv.w[p]);
+        hi[p] = p_hi(rv.w[p]);
+    }
+    int sl[DC];
+    WT ev[DC];
+#pragma unroll
+    for (int t = 0; t < DC; t++) {
+        sl[t] = ix.c_slot[base + 32 * t];
+        ev[t] = slots[sl[t]];
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            lo[p] += p_lo(ev[t].w[p]);
+            hi[p] += p_hi(ev[t].w[p]);
         }
-        VT out;
+    }
+    WT out;
 #pragma unroll
-        for (int f = 0; f < FT; f++) out.x[f] = (T)rsat_out(acc[f]);
-        s[p] = out;
+    for (int p = 0; p < P; p++) out.w[p] = p_pack_sat(lo[p], hi[p]);
+    s[p0] = out;
+#pragma unroll
+    for (int t = 0; t < DC; t++) {
+        WT lv;
+#pragma unroll
+        for (int p = 0; p < P; p++) lv.w[p] = p_lam(out.w[p], ev[t].w[p]);
+        slots[sl[t]] = lv;
+    }
+}
+
+template <int FT>
+__device__ __forceinline__ void col_any_packed(const Idx& ix, Words<FT / 2>* slots, Words<FT / 2>* s,
+                                               const Words<FT / 2>& rv, int p0, int base, int d) {
+    constexpr int P = FT / 2;
+    using WT = Words<P>;
+    int32_t lo[P], hi[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+        lo[p] = p_lo(rv.w[p]);
+        hi[p] = p_hi(rv.w[p]);
+    }
+    for (int t = 0; t < d; t++) {
+        const WT ev = slots[ix.c_slot[base + 32 * t]];
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            lo[p] += p_lo(ev.w[p]);
+            hi[p] += p_hi(ev.w[p]);
+        }
+    }
+    WT out;
+#pragma unroll
+    for (int p = 0; p < P; p++) out.w[p] = p_pack_sat(lo[p], hi[p]);
+    s[p0] = out;
+    for (int t = 0; t < d; t++) {
+        const int slot = ix.c_slot[base + 32 * t];
+        const WT ev = slots[slot];
+        WT lv;
+#pragma unroll
+        for (int p = 0; p < P; p++) lv.w[p] = p_lam(out.w[p], ev.w[p]);
+        slots[slot] = lv;
+    }
+}
+
+// Column pass over every column position of the tile; columns of up to 10 edges take the
+// fully unrolled body of their degree (the degree-sorted slices keep a warp's columns on
+// the same case).
+template <int MODE, int FT>
+__device__ __forceinline__ void cols_pass(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots_v,
+                                          VecR<typename RT<MODE>::T, FT>* s_v,
+                                          const VecR<typename RT<MODE>::T, FT>* r_v, int N) {
+    constexpr bool kPacked = MODE == kModeFixed && FT % 2 == 0;
+    const int nth = blockDim.x;
+    for (int k = 0;; k++) {
+        const int p = snake(k, nth);
+        if (p >= N) break;
+        const int d = ix.c_deg[p];
+        const int base = ix.c_base[p >> 5] + (p & 31);
+        if constexpr (kPacked) {
+            using WT = Words<FT / 2>;
+            WT* slots = reinterpret_cast<WT*>(slots_v);
+            WT* s = reinterpret_cast<WT*>(s_v);
+            const WT rv = reinterpret_cast<const WT*>(r_v)[p];
+#define LDPC_COLP(DC) \
+    case DC: col_fixed_packed<FT, DC>(ix, slots, s, rv, p, base); break;
+            switch (d) {
+                LDPC_COLP(1) LDPC_COLP(2) LDPC_COLP(3) LDPC_COLP(4) LDPC_COLP(5)
+                LDPC_COLP(6) LDPC_COLP(7) LDPC_COLP(8) LDPC_COLP(9) LDPC_COLP(10)
+                default: col_any_packed<FT>(ix, slots, s, rv, p, base, d);
+            }
+#undef LDPC_COLP
+        } else {
+            const auto rv = r_v[p];
+#define LDPC_COL(DC) \
+    case DC: col_fixed<MODE, FT, DC>(ix, slots_v, s_v, rv, p, base); break;
+            switch (d) {
+                LDPC_COL(1) LDPC_COL(2) LDPC_COL(3) LDPC_COL(4) LDPC_COL(5)
+                LDPC_COL(6) LDPC_COL(7) LDPC_COL(8) LDPC_COL(9) LDPC_COL(10)
+                default: col_any<MODE, FT>(ix, slots_v, s_v, rv, p, base, d);
+            }
+#undef LDPC_COL
+        }
     }
 }
 
@@ -501,6 +592,7 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
                                             const float* walpha0, const float* wbeta0,
                                             int n_rtasks) {
     using T = typename RT<MODE>::T;
+    constexpr bool kPacked = MODE == kModeFixed && FT % 2 == 0;
     const int N = a.N;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         VT v;
@@ -513,20 +605,16 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
     }
     uint32_t active = (1u << nf) - 1u;
     __syncthreads();
+    init_pass<MODE, FT>(ix, eta, r, N);  // the edge slots hold lambda from here on
+    __syncthreads();
 
     for (int k = 0;; k++) {
         const int par = k & 1;
         const bool last = (k == a.L);
         const bool syn = last || (a.early_stop && (k % a.check_every == 0));
-        uint32_t* uw = &unsat_w[par];
-        if (W) {  // weights of iteration k + 1 (the last row serves the later iterations)
-            const int row = min(k + 1, a.w_rows) - 1;
-            ix.walpha = walpha0 + row * a.n_classes;
-            ix.wbeta = wbeta0 + row * a.n_classes;
-        }
-        phase_a_any<MODE, FT, PAPER, W>(k == 0, syn, !last, ix, eta, s, n_rtasks, uw);
-        __syncthreads();
-        if (syn) {
+        if (syn) {  // the decisions of the current s: stop the frames that are codewords
+            syn_pass<MODE, FT, PAPER>(ix, s, n_rtasks, &unsat_w[par]);
+            __syncthreads();
             const uint32_t conv = active & ~unsat_w[par];
             if (last) {
                 emit<MODE, FT>(a, ix, s, fbase, active, a.L, conv);
@@ -536,13 +624,19 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
                 emit<MODE, FT>(a, ix, s, fbase, conv, k, conv);
                 active &= ~conv;
                 if (!active) break;
-                __syncthreads();  // the emitted posteriors are read before phase B rewrites them
             }
         }
-        if constexpr (MODE == kModeFixed && FT % 2 == 0)
-            phase_b_packed<FT>(ix, eta, s, r, N);
+        if (W) {  // weights of iteration k + 1 (the last row serves the later iterations)
+            const int row = min(k + 1, a.w_rows) - 1;
+            ix.walpha = walpha0 + row * a.n_classes;
+            ix.wbeta = wbeta0 + row * a.n_classes;
+        }
+        if constexpr (kPacked)
+            rows_pass_packed<FT>(ix, eta, n_rtasks);
         else
-            phase_b<MODE, FT>(ix, eta, s, r, N);
+            rows_pass<MODE, FT, W>(ix, eta, n_rtasks);
+        __syncthreads();  // (also orders emit's reads of s before the column pass rewrites s)
+        cols_pass<MODE, FT>(ix, eta, s, r, N);
         if (threadIdx.x == 0) unsat_w[par ^ 1] = 0;
         __syncthreads();
     }
