@@ -25,6 +25,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "../../include/ldpc.h"
 #include "ldpc_internal.h"
@@ -179,6 +180,22 @@ __device__ __forceinline__ int snake(int k, int nth) {
     return k * nth + ((k & 1) ? (nth - 1 - (int)threadIdx.x) : (int)threadIdx.x);
 }
 
+// Largest row / column degree whose fully unrolled body keeps its operands in registers:
+// about 24 (rows) or 30 (columns: slot ids too) registers of operands, at FT x sizeof(T)
+// / 4 registers per edge vector.
+template <int MODE, int FT>
+__host__ __device__ constexpr int vec_regs() {
+    return (FT * (MODE == kModeFP32 ? 4 : 2) + 3) / 4;
+}
+template <int MODE, int FT>
+__host__ __device__ constexpr int row_body_max() {
+    return 24 / vec_regs<MODE, FT>() < 16 ? 24 / vec_regs<MODE, FT>() : 16;
+}
+template <int MODE, int FT>
+__host__ __device__ constexpr int col_body_max() {
+    return 30 / (1 + vec_regs<MODE, FT>()) < 10 ? 30 / (1 + vec_regs<MODE, FT>()) : 10;
+}
+
 // ---------------------------------------------------------------------------------------
 // The edge-slot array holds lambda after the column pass and the new message after the row
 // pass (each edge belongs to one row and one column, so the passes never touch a slot
@@ -195,8 +212,126 @@ __device__ __forceinline__ int snake(int k, int nth) {
 // The row pass reads its slots contiguously: no gather of s and no index read per edge.
 // ---------------------------------------------------------------------------------------
 
-// Row pass, per frame. lambda is read twice (two sweeps) and overwritten by eta.
-template <int MODE, int FT, bool W>
+// One row of exactly DC edges, per frame: the row's lambdas are read once into registers
+// (fully unrolled), then the new messages are written.
+template <int MODE, int FT, bool W, int DC>
+__device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
+                                          int base) {
+    using T = typename RT<MODE>::T;
+    using A = typename RT<MODE>::A;
+    using VT = VecR<T, FT>;
+    A min0[FT], min1[FT];
+    uint32_t sx[FT];
+#pragma unroll
+    for (int f = 0; f < FT; f++) {
+        min0[f] = rbig(A());
+        min1[f] = rbig(A());
+        sx[f] = 0;
+    }
+    VT lv[DC];
+#pragma unroll
+    for (int t = 0; t < DC; t++) {
+        lv[t] = slots[base + 32 * t];
+#pragma unroll
+        for (int f = 0; f < FT; f++) {
+            const A lam = (A)lv[t].x[f];
+            const A m = rabs(lam);
+            min1[f] = min(min1[f], max(min0[f], m));
+            min0[f] = min(min0[f], m);
+            sx[f] ^= bits_of(lam);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < DC; t++) {
+        const int slot = base + 32 * t;
+        float wa = 1.0f, wb = 0.0f;
+        if constexpr (W) {
+            const int c = ix.wcls[slot];
+            wa = ix.walpha[c];
+            wb = ix.wbeta[c];
+        }
+        VT out;
+#pragma unroll
+        for (int f = 0; f < FT; f++) {
+            const A lam = (A)lv[t].x[f];
+            A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
+            if constexpr (W) {  // max(fma(alpha, m, -beta), 0)
+                const float x = __fmaf_rn(wa, (float)m, -wb);
+                m = (A)(x > 0.0f ? x : 0.0f);
+            }
+            out.x[f] = (T)with_sign(m, bits_of(lam) ^ sx[f]);
+        }
+        slots[slot] = out;
+    }
+}
+
+template <int FT, int DC>
+__device__ __forceinline__ void row_fixed_packed(Words<FT / 2>* slots, int base) {
+    constexpr int P = FT / 2;
+    using WT = Words<P>;
+    uint32_t min0[P], min1[P], sx[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+        min0[p] = 0x7fff7fffu;
+        min1[p] = 0x7fff7fffu;
+        sx[p] = 0;
+    }
+    WT lv[DC];
+#pragma unroll
+    for (int t = 0; t < DC; t++) {
+        lv[t] = slots[base + 32 * t];
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            const uint32_t lam = lv[t].w[p];
+            const uint32_t m = p_max(lam, p_neg(lam));
+            min1[p] = p_min(min1[p], p_max(min0[p], m));
+            min0[p] = p_min(min0[p], m);
+            sx[p] ^= lam;
+        }
+    }
+    uint32_t nmin0[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) nmin0[p] = p_neg(min0[p]);
+#pragma unroll
+    for (int t = 0; t < DC; t++) {
+        WT out;
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            const uint32_t lam = lv[t].w[p];
+            const uint32_t a = p_max(lam, p_neg(lam));
+            const uint32_t ne = p_spread(p_min(p_add(a, nmin0[p]), 0x00010001u));
+            const uint32_t m = (min0[p] & ne) | (min1[p] & ~ne);
+            const uint32_t sb = ((lam ^ sx[p]) >> 15) & 0x00010001u;
+            out.w[p] = p_add(m ^ p_spread(sb), sb);
+        }
+        slots[base + 32 * t] = out;
+    }
+}
+
+// Exact-degree dispatch: rows of 2 .. MAXD edges take the fully unrolled body of their
+// degree (the degree-sorted slices keep a warp's rows on the same case); returns false for
+// longer rows.
+template <int MAXD, typename Body>
+__device__ __forceinline__ bool by_degree(int d, Body&& body) {
+    bool done = true;
+    switch (d) {
+#define LDPC_CASE(DC) \
+    case DC:          \
+        if constexpr (DC <= MAXD) body(std::integral_constant<int, DC>()); \
+        else done = false; \
+        break;
+        LDPC_CASE(1) LDPC_CASE(2) LDPC_CASE(3) LDPC_CASE(4) LDPC_CASE(5) LDPC_CASE(6) LDPC_CASE(7)
+        LDPC_CASE(8) LDPC_CASE(9) LDPC_CASE(10) LDPC_CASE(11) LDPC_CASE(12) LDPC_CASE(13)
+        LDPC_CASE(14) LDPC_CASE(15) LDPC_CASE(16)
+#undef LDPC_CASE
+        default: done = false;
+    }
+    return done;
+}
+
+// Row pass, per frame. Rows too long for an unrolled body read lambda twice (two sweeps);
+// every row's slots end up holding the new messages.
+template <int MODE, int FT, bool W, bool UNROLL = true>
 __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
                                           int n_rtasks) {
     using T = typename RT<MODE>::T;
@@ -210,6 +345,12 @@ __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>:
         const int d = ix.r_deg[task];
         if (d == 0) continue;
         const int base = ix.r_base[task >> 5] + (task & 31);
+        if constexpr (UNROLL) {
+            if (by_degree<row_body_max<MODE, FT>()>(d, [&](auto dc) {
+                    row_fixed<MODE, FT, W, decltype(dc)::value>(ix, slots, base);
+                }))
+                continue;
+        }
         A min0[FT], min1[FT];
         uint32_t sx[FT];
 #pragma unroll
@@ -269,7 +410,7 @@ __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>:
 //            min(|lambda| - min0, 1) is 0 there and 1 elsewhere), conditional negation
 //            by (m ^ mask) + (mask & 1) with the lane mask of the new sign.
 // ---------------------------------------------------------------------------------------
-template <int FT>
+template <int FT, bool UNROLL = true>
 __device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT>* slots_v,
                                                  int n_rtasks) {
     constexpr int P = FT / 2;
@@ -283,6 +424,12 @@ __device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT
         const int d = ix.r_deg[task];
         if (d == 0) continue;
         const int base = ix.r_base[task >> 5] + (task & 31);
+        if constexpr (UNROLL) {
+            if (by_degree<row_body_max<kModeFixed, FT>()>(d, [&](auto dc) {
+                    row_fixed_packed<FT, decltype(dc)::value>(slots, base);
+                }))
+                continue;
+        }
         uint32_t min0[P], min1[P], sx[P];
 #pragma unroll
         for (int p = 0; p < P; p++) {
@@ -511,10 +658,10 @@ __device__ __forceinline__ void col_any_packed(const Idx& ix, Words<FT / 2>* slo
     }
 }
 
-// Column pass over every column position of the tile; columns of up to 10 edges take the
-// fully unrolled body of their degree (the degree-sorted slices keep a warp's columns on
-// the same case).
-template <int MODE, int FT>
+// Column pass over every column position of the tile; columns up to col_body_max edges take
+// the fully unrolled body of their degree (the degree-sorted slices keep a warp's columns
+// on the same case).
+template <int MODE, int FT, bool UNROLL = true>
 __device__ __forceinline__ void cols_pass(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots_v,
                                           VecR<typename RT<MODE>::T, FT>* s_v,
                                           const VecR<typename RT<MODE>::T, FT>* r_v, int N) {
@@ -530,24 +677,16 @@ __device__ __forceinline__ void cols_pass(const Idx& ix, VecR<typename RT<MODE>:
             WT* slots = reinterpret_cast<WT*>(slots_v);
             WT* s = reinterpret_cast<WT*>(s_v);
             const WT rv = reinterpret_cast<const WT*>(r_v)[p];
-#define LDPC_COLP(DC) \
-    case DC: col_fixed_packed<FT, DC>(ix, slots, s, rv, p, base); break;
-            switch (d) {
-                LDPC_COLP(1) LDPC_COLP(2) LDPC_COLP(3) LDPC_COLP(4) LDPC_COLP(5)
-                LDPC_COLP(6) LDPC_COLP(7) LDPC_COLP(8) LDPC_COLP(9) LDPC_COLP(10)
-                default: col_any_packed<FT>(ix, slots, s, rv, p, base, d);
-            }
-#undef LDPC_COLP
+            if (!UNROLL || !by_degree<col_body_max<MODE, FT>()>(d, [&](auto dc) {
+                    col_fixed_packed<FT, decltype(dc)::value>(ix, slots, s, rv, p, base);
+                }))
+                col_any_packed<FT>(ix, slots, s, rv, p, base, d);
         } else {
             const auto rv = r_v[p];
-#define LDPC_COL(DC) \
-    case DC: col_fixed<MODE, FT, DC>(ix, slots_v, s_v, rv, p, base); break;
-            switch (d) {
-                LDPC_COL(1) LDPC_COL(2) LDPC_COL(3) LDPC_COL(4) LDPC_COL(5)
-                LDPC_COL(6) LDPC_COL(7) LDPC_COL(8) LDPC_COL(9) LDPC_COL(10)
-                default: col_any<MODE, FT>(ix, slots_v, s_v, rv, p, base, d);
-            }
-#undef LDPC_COL
+            if (!UNROLL || !by_degree<col_body_max<MODE, FT>()>(d, [&](auto dc) {
+                    col_fixed<MODE, FT, decltype(dc)::value>(ix, slots_v, s_v, rv, p, base);
+                }))
+                col_any<MODE, FT>(ix, slots_v, s_v, rv, p, base, d);
         }
     }
 }
@@ -586,7 +725,9 @@ __device__ __forceinline__ void copy_to_smem(T* dst, const T* src, int n) {
 // Every iteration of one tile of nf frames (frames fbase .. fbase + nf - 1 of a.llr) with
 // eta, s and r at the given addresses (shared memory, or a CTA's slot of global scratch),
 // ending with the decisions of every frame written out. unsat_w: two words reset to 0.
-template <int MODE, int FT, bool PAPER, bool W, typename VT>
+// UNROLL: the fully unrolled row and column bodies (false in kernels that inline several
+// tile shapes and would exceed their register budget).
+template <int MODE, int FT, bool PAPER, bool W, typename VT, bool UNROLL = true>
 __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, VT* s, VT* r,
                                             uint32_t* unsat_w, int fbase, int nf,
                                             const float* walpha0, const float* wbeta0,
@@ -632,11 +773,11 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
             ix.wbeta = wbeta0 + row * a.n_classes;
         }
         if constexpr (kPacked)
-            rows_pass_packed<FT>(ix, eta, n_rtasks);
+            rows_pass_packed<FT, UNROLL>(ix, eta, n_rtasks);
         else
-            rows_pass<MODE, FT, W>(ix, eta, n_rtasks);
+            rows_pass<MODE, FT, W, UNROLL>(ix, eta, n_rtasks);
         __syncthreads();  // (also orders emit's reads of s before the column pass rewrites s)
-        cols_pass<MODE, FT>(ix, eta, s, r, N);
+        cols_pass<MODE, FT, UNROLL>(ix, eta, s, r, N);
         if (threadIdx.x == 0) unsat_w[par ^ 1] = 0;
         __syncthreads();
     }
