@@ -238,7 +238,8 @@ def other_workloads(timed):
         llr = torch.from_numpy(inputs.all_zero_awgn_llr(F, code.N, e, code.design_rate, 17)).cuda()
         for mode in ("fp32", "fixed"):
             dec = Decoder.from_code(code, mode=mode)
-            dec.autotune(F, L)  # resident tile shape, or check-pass staging when streaming
+            # resident tile shape, or check-pass staging when streaming, timed on these frames
+            dec.autotune(F, L, llr=llr, early_stop=True)
             o = (torch.empty((F, code.N), dtype=torch.uint8, device="cuda"),
                  torch.empty(F, dtype=torch.int32, device="cuda"), None, None)
             ms = timed(lambda: dec.decode(llr, L, early_stop=True, out=o), 10, 3)
@@ -302,6 +303,7 @@ def learned_vs_plain_large(timed):
     res = {}
     for name, w, L in (("plain", None, 50), ("learned", (alpha, beta), L_l)):
         dec.set_weights(*(w if w else (None,)))
+        dec.autotune(4096, L, llr=llr, early_stop=True)
         ms = timed(lambda: dec.decode(llr, L, early_stop=True, out=out), 3, 1)
         fer = float((out[0] != bits).any(dim=1).float().mean().item())
         res[name] = {"max_iter": L, "ms_per_call": ms, "Gbit/s": 4096 * code.N / (ms * 1e-3) / 1e9,
@@ -344,7 +346,7 @@ def learned_vs_plain(timed):
     res = {}
     for name, w, L in (("plain", None, 20), ("learned", (alpha, beta), L_l)):
         dec.set_weights(*(w if w else (None,)))
-        dec.autotune(65536, L)
+        dec.autotune(65536, L, llr=llr, early_stop=True)
         ms = timed(lambda: dec.decode(llr, L, early_stop=True, out=out), 10, 3)
         fer = float((out[0] != bits).any(dim=1).float().mean().item())
         res[name] = {"max_iter": L, "ms_per_step": ms, "Gbit/s": 65536 * code.N / (ms * 1e-3) / 1e9,
@@ -389,7 +391,7 @@ def mixed_codes(timed):
     outs = []
     for d, c, F, x in zip(decs, codes, frames, xs):
         try:  # resident tile shape, or streaming check-pass staging (rows of at most 16 edges)
-            d.autotune(F, L)
+            d.autotune(F, L, llr=x, early_stop=True)
         except Exception:
             pass
         outs.append((torch.empty((F, c.N), dtype=torch.uint8, device="cuda"),
@@ -402,11 +404,13 @@ def mixed_codes(timed):
     ms_seq = timed(per_code, 20, 3)
     same = all(bool((batch._keep[k][1] == outs[k][0]).all()) for k in range(len(codes)))
     info = batch.info()
+    cap = batch.tile_frames()
     batch.close()
     return {"codes": [{"N": c.N, "M": c.M, "E": c.E, "frames": F} for c, F in zip(codes, frames)],
             "max_iter": L, "ebn0_db": 2.0, "frames_total": int(sum(frames)),
             "one_launch_graph": {"ms": ms_graph, "Gbit/s": bits_total / (ms_graph * 1e-3) / 1e9,
-                                 "threads": threads, "codes_in_shared_memory": info["codes_in_shared_memory"]},
+                                 "threads": threads, "frames_per_tile_at_most": cap,
+                                 "codes_in_shared_memory": info["codes_in_shared_memory"]},
             "per_code_calls": {"ms": ms_seq, "Gbit/s": bits_total / (ms_seq * 1e-3) / 1e9,
                                "launches": sum(d.last_kernel_count() for d in decs)},
             "identical_bits": same}

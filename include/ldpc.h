@@ -258,9 +258,18 @@ int ldpc_batch_decode(ldpc_batch_t *b, int32_t max_iter, int32_t early_stop);
 int ldpc_batch_capture(ldpc_batch_t *b);
 int ldpc_batch_replay(ldpc_batch_t *b);
 
-/* ldpc_batch_set_threads / ldpc_batch_autotune: CTA size of the batch kernel, given or
- * chosen by timing the prepared decode (prepares it for max_iter / early_stop first). */
+/* ldpc_batch_set_threads: CTA size of the batch kernel (64..1024, a multiple of 32).
+ * ldpc_batch_set_tile_frames: at most 1, 2 or 4 frames interleaved per tile for the codes
+ * kept in shared memory (default 4; a code whose frames do not fit that many uses fewer);
+ * takes effect at the next ldpc_batch_prepare. ldpc_batch_get_tile_frames reads it back.
+ * ldpc_batch_autotune: times the decode prepared for max_iter / early_stop on the buffers
+ * set with ldpc_batch_set_io, for every cap on the frames per tile x CTA size, keeps the
+ * fastest pair and leaves the batch prepared with it; best_threads and best_ms
+ * (nullable) receive the CTA size and the time of one decode. With early stop a tile runs
+ * until its last frame stops, so narrower tiles can win. */
 int ldpc_batch_set_threads(ldpc_batch_t *b, int32_t threads);
+int ldpc_batch_set_tile_frames(ldpc_batch_t *b, int32_t max_frames_per_tile);
+int ldpc_batch_get_tile_frames(const ldpc_batch_t *b, int32_t *max_frames_per_tile);
 int ldpc_batch_autotune(ldpc_batch_t *b, int32_t max_iter, int32_t early_stop,
                         int32_t *best_threads, float *best_ms);
 
@@ -310,6 +319,22 @@ int ldpc_set_tuning(ldpc_t *h, int32_t frames_per_tile, int32_t threads, int32_t
  * layout, i.e. rows longer than 16 edges (streaming).
  */
 int ldpc_autotune(ldpc_t *h, int32_t frames, int32_t max_iter, float *best_ms);
+
+/*
+ * ldpc_autotune_data: as ldpc_autotune, but each shape decodes the caller's frames with the
+ * caller's early-stop settings, so the choice fits workloads whose frames stop at
+ * different iterations (a tile of several frames runs until its last frame stops, which
+ * favours narrower tiles than timing without early stop does).
+ *   llr         device pointer, FP32 [frames][N], frame-major (as ldpc_decode_ex with
+ *               LDPC_LLR_F32); only the first min(frames, 65536) (resident) or
+ *               min(frames, 2048) (streaming) frames are decoded; read only.
+ *   early_stop  0 or 1; check_every >= 1 (as ldpc_decode_ex).
+ * Errors: LDPC_ERR_BAD_POINTER for a null handle or an llr that is not device memory,
+ * LDPC_ERR_INVALID_ARG for frames <= 0, max_iter < 0, check_every < 1 or early_stop not 0/1,
+ * and the errors of ldpc_autotune.
+ */
+int ldpc_autotune_data(ldpc_t *h, const float *llr, int32_t frames, int32_t max_iter,
+                       int32_t early_stop, int32_t check_every, float *best_ms);
 
 /* ldpc_get_tuning: the resident launch shape in force for the current mode. */
 int ldpc_get_tuning(const ldpc_t *h, int32_t *frames_per_tile, int32_t *threads,

@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libldpc.so")
-SOURCES = ["graph.cpp", "api.cu", "stream.cu", "stream_fp32.cu", "stream_fixed.cu", "resident.cu", "resident_fp32.cu",
-           "resident_fixed.cu", "noalloc.cu", "learn_kernels.cu", "batch.cu",
+SOURCES = ["graph.cpp", "api.cu", "stream.cu", "stream_fp32.cu", "stream_fixed.cu", "resident.cu",
+           "resident_fp32.cu", "resident_fp32_es.cu", "resident_fixed.cu", "resident_fixed_es.cu", "noalloc.cu", "learn_kernels.cu", "batch.cu",
            "dense_kernels.cu", "cluster.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

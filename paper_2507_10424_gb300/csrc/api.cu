@@ -636,9 +636,19 @@ int ldpc_set_tuning(ldpc_t* h, int32_t frames_per_tile, int32_t threads, int32_t
     return LDPC_OK;
 }
 
+// What the autotuners time: zeros without early stop (the work then does not depend on
+// the values), or the caller's frames (device FP32 [frames][N]) with its early-stop
+// settings, whose frames stop at different iterations.
+struct TuneData {
+    const float* llr = nullptr;  // nullptr: zeros, no early stop
+    int32_t early_stop = 0;
+    int32_t check_every = 1;
+};
+
 // Streaming codes: time the staged check pass's shapes (and the unstaged kernel) on
 // min(frames, 2048) frames through the regular decode path, and keep the fastest.
-static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
+static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms,
+                           const TuneData& td) {
     if (!h->dg.ell_D) return fail(LDPC_ERR_UNSUPPORTED);  // only the padded layout has shapes
     const int32_t F = std::min<int32_t>(frames, 2048);
     void* llr = nullptr;
@@ -652,7 +662,7 @@ static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* b
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
-    if (cudaMalloc(&llr, (size_t)F * h->N * 4) != cudaSuccess ||
+    if ((!td.llr && cudaMalloc(&llr, (size_t)F * h->N * 4) != cudaSuccess) ||
         cudaMalloc((void**)&bits, (size_t)F * h->N) != cudaSuccess ||
         cudaMalloc((void**)&iters, (size_t)F * 4) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -660,11 +670,11 @@ static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* b
         cudaGetLastError();
         return fail(LDPC_ERR_OOM);
     }
-    // without early stop the work does not depend on the LLR values
-    if (cudaMemsetAsync(llr, 0, (size_t)F * h->N * 4, h->stream) != cudaSuccess) {
+    if (!td.llr && cudaMemsetAsync(llr, 0, (size_t)F * h->N * 4, h->stream) != cudaSuccess) {
         cleanup();
         return fail(LDPC_ERR_CUDA);
     }
+    const void* x = td.llr ? (const void*)td.llr : llr;
     const int32_t keep[3] = {h->st_warps, h->st_stages, h->st_vw};
     // (warps, stages, frames per lane): full and half-width lanes (half-width stages let rows
     // of 16 slots fit more warps), and the unstaged kernel
@@ -677,10 +687,13 @@ static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* b
         h->st_stages = shapes[k][1];
         h->st_vw = shapes[k][2] ? (h->mode == kModeFP32 ? 2 : 4) : 0;
         float ms = 0.0f;
-        bool bad = ldpc_decode_ex(h, llr, LDPC_LLR_F32, F, max_iter, 0, 1, bits, iters, nullptr, nullptr) != LDPC_OK;
+        auto run = [&]() {
+            return ldpc_decode_ex(h, x, LDPC_LLR_F32, F, max_iter, td.early_stop, td.check_every,
+                                  bits, iters, nullptr, nullptr) != LDPC_OK;
+        };
+        bool bad = run();
         bad = bad || cudaEventRecord(e0, h->stream) != cudaSuccess;
-        for (int r = 0; r < 2 && !bad; r++)
-            bad = ldpc_decode_ex(h, llr, LDPC_LLR_F32, F, max_iter, 0, 1, bits, iters, nullptr, nullptr) != LDPC_OK;
+        for (int r = 0; r < 2 && !bad; r++) bad = run();
         bad = bad || cudaEventRecord(e1, h->stream) != cudaSuccess ||
               cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess;
         if (bad) {
@@ -707,12 +720,14 @@ static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* b
     return LDPC_OK;
 }
 
-int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
-    if (!h) return fail(LDPC_ERR_BAD_POINTER);
-    if (frames <= 0 || max_iter < 0) return fail(LDPC_ERR_INVALID_ARG);
-    if (resolved_variant(h) == LDPC_VARIANT_STREAM) return autotune_stream(h, frames, max_iter, best_ms);
+static int autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms,
+                    const TuneData& td) {
+    if (resolved_variant(h) == LDPC_VARIANT_STREAM)
+        return autotune_stream(h, frames, max_iter, best_ms, td);
     if (!h->dg.sliced || !h->plan[h->mode].ok) return fail(LDPC_ERR_UNSUPPORTED);
-    const int32_t F = std::min<int32_t>(frames, 16384);
+    // the caller's frames: up to a full 65536-frame batch (how many tiles fill the SMs
+    // decides the shape); zeros: a quarter of that
+    const int32_t F = std::min<int32_t>(frames, td.llr ? 65536 : 16384);
     void* llr = nullptr;
     uint8_t* bits = nullptr;
     int32_t* iters = nullptr;
@@ -724,7 +739,7 @@ int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
-    if (cudaMalloc(&llr, (size_t)F * h->N * 4) != cudaSuccess ||
+    if ((!td.llr && cudaMalloc(&llr, (size_t)F * h->N * 4) != cudaSuccess) ||
         cudaMalloc((void**)&bits, (size_t)F * h->N) != cudaSuccess ||
         cudaMalloc((void**)&iters, (size_t)F * 4) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -732,8 +747,7 @@ int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
         cudaGetLastError();
         return fail(LDPC_ERR_OOM);
     }
-    // without early stop the work does not depend on the LLR values
-    if (cudaMemsetAsync(llr, 0, (size_t)F * h->N * 4, h->stream) != cudaSuccess) {
+    if (!td.llr && cudaMemsetAsync(llr, 0, (size_t)F * h->N * 4, h->stream) != cudaSuccess) {
         cleanup();
         return fail(LDPC_ERR_CUDA);
     }
@@ -743,11 +757,11 @@ int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
     a.E = (int32_t)h->E;
     a.frames = F;
     a.L = max_iter;
-    a.early_stop = 0;
-    a.check_every = 1;
+    a.early_stop = td.early_stop;
+    a.check_every = td.check_every;
     a.paper_slicer = (h->flags & LDPC_FLAG_PAPER_SLICER) ? 1 : 0;
     a.llr_is_i8 = 0;
-    a.llr = llr;
+    a.llr = td.llr ? (const void*)td.llr : llr;
     a.out_bits = bits;
     a.out_iters = iters;
     a.out_ok = nullptr;
@@ -762,7 +776,7 @@ int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
     ResidentTuning best_t = h->tuning;
     for (int ft : {1, 2, 4})
     for (int ip : {1, 2})
-        for (int th = 0; th <= 1024; th += (th == 0 ? 256 : 64)) {
+        for (int th = 0; th <= 1024; th += 64) {  // 0: the default for the tile
             ResidentTuning t;
             t.FT = ft;
             t.threads = th;
@@ -792,6 +806,25 @@ int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
     replan(h);
     if (best_ms) *best_ms = best / 2.0f;
     return LDPC_OK;
+}
+
+int ldpc_autotune(ldpc_t* h, int32_t frames, int32_t max_iter, float* best_ms) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (frames <= 0 || max_iter < 0) return fail(LDPC_ERR_INVALID_ARG);
+    return autotune(h, frames, max_iter, best_ms, TuneData{});
+}
+
+int ldpc_autotune_data(ldpc_t* h, const float* llr, int32_t frames, int32_t max_iter,
+                       int32_t early_stop, int32_t check_every, float* best_ms) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (frames <= 0 || max_iter < 0 || check_every < 1 || (early_stop != 0 && early_stop != 1))
+        return fail(LDPC_ERR_INVALID_ARG);
+    if (!is_device_ptr(llr)) return fail(LDPC_ERR_BAD_POINTER);
+    TuneData td;
+    td.llr = llr;
+    td.early_stop = early_stop;
+    td.check_every = check_every;
+    return autotune(h, frames, max_iter, best_ms, td);
 }
 
 int ldpc_get_tuning(const ldpc_t* h, int32_t* frames_per_tile, int32_t* threads,

@@ -35,18 +35,19 @@ struct Tile {
 };
 
 // The tile body for FT interleaved frames at `base` (shared memory or a scratch slot).
-template <int FT, bool PAPER>
+template <int FT, bool PAPER, bool ES>
 __device__ __forceinline__ void multi_tile(const ResArgs& a, const Idx& ix, char* base,
                                            uint32_t* unsat_w, int f0) {
     using VT = VecR<float, FT>;
     VT* eta = reinterpret_cast<VT*>(base);
     VT* s = eta + a.E_pad;
     VT* r = s + a.n_csl * 32;
-    decode_tile<kModeFP32, FT, PAPER, false>(a, ix, eta, s, r, unsat_w, f0, min(FT, a.frames - f0),
+    decode_tile<kModeFP32, FT, PAPER, false, VT, true, ES>(a, ix, eta, s, r, unsat_w, f0, min(FT, a.frames - f0),
                                              nullptr, nullptr, a.n_rsl * 32);
 }
 
-template <bool PAPER>
+// ES: the early-stop form of the tile body (the syndrome gathered by the row pass).
+template <bool PAPER, bool ES>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_multi(const CodeDesc* codes, const Tile* tiles,
                                                           int n_tiles, int32_t* counter,
                                                           char* scratch, size_t slot_bytes) {
@@ -71,13 +72,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_multi(const CodeDesc* codes,
                      nullptr, nullptr, nullptr};
         if (cd.in_smem) {
             char* base = reinterpret_cast<char*>(smem_raw);
-            if (cd.ft == 4) multi_tile<4, PAPER>(a, ix, base, unsat_w, tl.f0);
-            else if (cd.ft == 2) multi_tile<2, PAPER>(a, ix, base, unsat_w, tl.f0);
-            else multi_tile<1, PAPER>(a, ix, base, unsat_w, tl.f0);
+            if (cd.ft == 4) multi_tile<4, PAPER, ES>(a, ix, base, unsat_w, tl.f0);
+            else if (cd.ft == 2) multi_tile<2, PAPER, ES>(a, ix, base, unsat_w, tl.f0);
+            else multi_tile<1, PAPER, ES>(a, ix, base, unsat_w, tl.f0);
         } else {
             char* base = scratch + (size_t)blockIdx.x * slot_bytes;
-            if (cd.ft == 2) multi_tile<2, PAPER>(a, ix, base, unsat_w, tl.f0);
-            else multi_tile<1, PAPER>(a, ix, base, unsat_w, tl.f0);
+            if (cd.ft == 2) multi_tile<2, PAPER, ES>(a, ix, base, unsat_w, tl.f0);
+            else multi_tile<1, PAPER, ES>(a, ix, base, unsat_w, tl.f0);
         }
         __syncthreads();
     }
@@ -98,7 +99,11 @@ struct ldpc_batch {
     std::vector<HandleView> views;
     std::vector<CodeDesc> desc;  // host copies
     std::vector<int32_t> frames;
+    std::vector<int32_t> fit_ft;  // most frames per tile that fit shared memory (in_smem codes)
+    std::vector<size_t> fbytes;   // bytes of one frame's eta, s and r
+    int ft_cap = 4;               // frames per tile at most (ldpc_batch_set_tile_frames)
     int paper = 0;
+    int es = 0;                   // the prepared decode tests the syndrome every iteration
     CodeDesc* d_desc = nullptr;
     Tile* d_tiles = nullptr;
     int32_t n_tiles = 0, tiles_cap = 0;
@@ -137,8 +142,17 @@ static void batch_free(ldpc_batch_t* b) {
     delete b;
 }
 
+using MultiKernel = void (*)(const CodeDesc*, const Tile*, int, int32_t*, char*, size_t);
+
+// The standard slicer has the early-stop form; the paper's slicer tests the syndrome in
+// a pass of its own.
+static MultiKernel multi_kernel(const ldpc_batch_t* b) {
+    if (b->paper) return k_multi<true, false>;
+    return b->es ? k_multi<false, true> : k_multi<false, false>;
+}
+
 static int batch_occupancy(ldpc_batch_t* b, int threads, int* grid) {
-    auto kern = b->paper ? k_multi<true> : k_multi<false>;
+    auto kern = multi_kernel(b);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
     int per_sm = 0;
@@ -169,12 +183,9 @@ static int batch_enqueue(ldpc_batch_t* b) {
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), b->stream) != cudaSuccess) return LDPC_ERR_CUDA;
     if (b->n_tiles > 0) {
         const int grid = std::min(b->grid, b->n_tiles);
-        if (b->paper)
-            k_multi<true><<<grid, b->threads, b->smem, b->stream>>>(b->d_desc, b->d_tiles, b->n_tiles,
-                                                                    b->d_counter, b->d_scratch, b->slot_bytes);
-        else
-            k_multi<false><<<grid, b->threads, b->smem, b->stream>>>(b->d_desc, b->d_tiles, b->n_tiles,
-                                                                     b->d_counter, b->d_scratch, b->slot_bytes);
+        multi_kernel(b)<<<grid, b->threads, b->smem, b->stream>>>(b->d_desc, b->d_tiles, b->n_tiles,
+                                                                  b->d_counter, b->d_scratch,
+                                                                  b->slot_bytes);
         launches++;
     }
     if (side && (cudaEventRecord(b->join, b->side) != cudaSuccess ||
@@ -220,7 +231,10 @@ ldpc_batch_t* ldpc_batch_create(int32_t n_codes, ldpc_t* const* codes) {
         if (d.in_smem) {
             d.ft = 4 * fb <= budget ? 4 : (2 * fb <= budget ? 2 : 1);
             b->smem = std::max(b->smem, (size_t)d.ft * fb);
-        } else {
+        }
+        b->fit_ft.push_back(d.ft);
+        b->fbytes.push_back(fb);
+        if (!d.in_smem) {
             d.ft = kScratchFT;
             slot = std::max(slot, (size_t)kScratchFT * fb);
         }
@@ -286,6 +300,16 @@ int ldpc_batch_set_io(ldpc_batch_t* b, int32_t code, const float* llr, int32_t f
 int ldpc_batch_prepare(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
     if (!b) return LDPC_ERR_BAD_POINTER;
     if (max_iter < 0) return LDPC_ERR_INVALID_ARG;
+    const int es = early_stop ? 1 : 0;
+    if (es != b->es) {  // the other kernel form: its occupancy sets the grid
+        const int keep = b->es;
+        b->es = es;
+        const int rc = ldpc_batch_set_threads(b, b->threads);
+        if (rc != LDPC_OK) {
+            b->es = keep;
+            return rc;
+        }
+    }
     std::vector<int32_t> order(b->codes.size());
     for (size_t c = 0; c < order.size(); c++) {
         order[c] = (int32_t)c;
@@ -462,35 +486,80 @@ int ldpc_batch_set_threads(ldpc_batch_t* b, int32_t threads) {
     return LDPC_OK;
 }
 
+int ldpc_batch_set_tile_frames(ldpc_batch_t* b, int32_t max_frames_per_tile) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    const int cap = max_frames_per_tile;
+    if (cap != 1 && cap != 2 && cap != 4) return LDPC_ERR_INVALID_ARG;
+    const int keep_cap = b->ft_cap;
+    const size_t keep_smem = b->smem;
+    std::vector<int32_t> keep_ft;
+    size_t smem = 0;
+    for (size_t c = 0; c < b->desc.size(); c++) {
+        keep_ft.push_back(b->desc[c].ft);
+        if (!b->desc[c].in_smem) continue;
+        b->desc[c].ft = std::min(b->fit_ft[c], cap);
+        smem = std::max(smem, (size_t)b->desc[c].ft * b->fbytes[c]);
+    }
+    b->ft_cap = cap;
+    b->smem = smem;
+    const int rc = ldpc_batch_set_threads(b, b->threads);  // the grid follows the new smem
+    if (rc != LDPC_OK) {
+        b->ft_cap = keep_cap;
+        b->smem = keep_smem;
+        for (size_t c = 0; c < b->desc.size(); c++) b->desc[c].ft = keep_ft[c];
+    }
+    return rc;  // the tiles follow at the next ldpc_batch_prepare
+}
+
+int ldpc_batch_get_tile_frames(const ldpc_batch_t* b, int32_t* max_frames_per_tile) {
+    if (!b || !max_frames_per_tile) return LDPC_ERR_BAD_POINTER;
+    *max_frames_per_tile = b->ft_cap;
+    return LDPC_OK;
+}
+
 int ldpc_batch_autotune(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop, int32_t* best_threads,
                         float* best_ms) {
     if (!b) return LDPC_ERR_BAD_POINTER;
-    int rc = ldpc_batch_prepare(b, max_iter, early_stop);
-    if (rc != LDPC_OK) return rc;
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LDPC_ERR_CUDA;
+    if (cudaEventCreate(&e0) != cudaSuccess) return LDPC_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return LDPC_ERR_CUDA;
+    }
     float best = -1.0f;
-    int best_t = b->threads;
-    for (int th = 256; th <= kMaxThreads; th += 128) {
-        if (ldpc_batch_set_threads(b, th) != LDPC_OK) continue;
-        float ms = 0.0f;
-        bool bad = batch_enqueue(b) < 0 || cudaEventRecord(e0, b->stream) != cudaSuccess;
-        for (int r = 0; r < 2 && !bad; r++) bad = batch_enqueue(b) < 0;
-        bad = bad || cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess;
-        if (bad) {
-            cudaGetLastError();
-            continue;
-        }
-        if (best < 0.0f || ms < best) {
-            best = ms;
-            best_t = th;
+    int best_t = b->threads, best_cap = b->ft_cap;
+    int rc = LDPC_OK;
+    // frames per tile at most x CTA size: with early stop a tile runs until its last frame
+    // stops, so narrower tiles can win although they share less of each index read
+    for (int cap : {4, 2, 1}) {
+        if (ldpc_batch_set_tile_frames(b, cap) != LDPC_OK) continue;
+        rc = ldpc_batch_prepare(b, max_iter, early_stop);
+        if (rc != LDPC_OK) break;
+        for (int th = 128; th <= kMaxThreads; th += 128) {
+            if (ldpc_batch_set_threads(b, th) != LDPC_OK) continue;
+            float ms = 0.0f;
+            bool bad = batch_enqueue(b) < 0 || cudaEventRecord(e0, b->stream) != cudaSuccess;
+            for (int r = 0; r < 2 && !bad; r++) bad = batch_enqueue(b) < 0;
+            bad = bad || cudaEventRecord(e1, b->stream) != cudaSuccess ||
+                  cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess;
+            if (bad) {
+                cudaGetLastError();
+                continue;
+            }
+            if (best < 0.0f || ms < best) {
+                best = ms;
+                best_t = th;
+                best_cap = cap;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc != LDPC_OK) return rc;
     if (best < 0.0f) return LDPC_ERR_UNSUPPORTED;
-    rc = ldpc_batch_set_threads(b, best_t);
+    rc = ldpc_batch_set_tile_frames(b, best_cap);
+    if (rc == LDPC_OK) rc = ldpc_batch_set_threads(b, best_t);
+    if (rc == LDPC_OK) rc = ldpc_batch_prepare(b, max_iter, early_stop);
     if (best_threads) *best_threads = best_t;
     if (best_ms) *best_ms = best / 2.0f;
     return rc;

@@ -91,6 +91,9 @@ int resident_decode(int mode, const DevGraph& dg, const ResidentPlan& p, const D
     ra.out_soft = a.out_soft;
     ra.tile_counter = tile_counter;
     if (cudaMemsetAsync(tile_counter, 0, sizeof(int32_t), st) != cudaSuccess) return LDPC_ERR_CUDA;
+    if (use_es(ra))
+        return mode == kModeFP32 ? dispatch_fp32_es(ra, p, num_sms, st)
+                                 : dispatch_fixed_es(ra, p, num_sms, st);
     return mode == kModeFP32 ? dispatch_fp32(ra, p, num_sms, st) : dispatch_fixed(ra, p, num_sms, st);
 }
 

@@ -212,11 +212,53 @@ __host__ __device__ constexpr int col_body_max() {
 // The row pass reads its slots contiguously: no gather of s and no index read per edge.
 // ---------------------------------------------------------------------------------------
 
+// The syndrome of s gathered by the row pass itself (early-stop kernels, on the iterations
+// that test it): per row, bit 31 of zx[f] is the XOR of frame f's decisions over the row's
+// bits (read from s through the slot's column position); the failing frames of the
+// thread's rows collect in z, and a warp-wide OR reaches the CTA's word once per pass.
+// With ON false every member is empty and the row pass is the plain one.
+template <int MODE, int FT, bool PAPER, bool ON>
+struct RowSyn {
+    const VecR<typename RT<MODE>::T, FT>* s;
+    uint32_t* unsat_w;
+    uint32_t zx[FT];
+    uint32_t z;
+    __device__ __forceinline__ RowSyn(const VecR<typename RT<MODE>::T, FT>* s_, uint32_t* u)
+        : s(s_), unsat_w(u), z(0) {}
+    __device__ __forceinline__ void row_begin() {
+        if constexpr (ON) {
+#pragma unroll
+            for (int f = 0; f < FT; f++) zx[f] = 0;
+        }
+    }
+    __device__ __forceinline__ void add(const Idx& ix, int slot) {
+        if constexpr (ON) {
+            using A = typename RT<MODE>::A;
+            const auto sv = s[ix.r_slot_pos[slot]];
+#pragma unroll
+            for (int f = 0; f < FT; f++) zx[f] ^= dec_bits<PAPER>((A)sv.x[f]);
+        }
+    }
+    __device__ __forceinline__ void row_end() {
+        if constexpr (ON) {
+#pragma unroll
+            for (int f = 0; f < FT; f++) z |= (zx[f] >> 31) << f;
+        }
+    }
+    // every thread of the CTA calls this once, after its last row
+    __device__ __forceinline__ void flush() {
+        if constexpr (ON) {
+            const uint32_t zw = __reduce_or_sync(0xffffffffu, z);
+            if (zw && (threadIdx.x & 31) == 0) atomicOr(unsat_w, zw);
+        }
+    }
+};
+
 // One row of exactly DC edges, per frame: the row's lambdas are read once into registers
 // (fully unrolled), then the new messages are written.
-template <int MODE, int FT, bool W, int DC>
+template <int MODE, int FT, bool W, int DC, typename SY>
 __device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
-                                          int base) {
+                                          int base, SY& sy) {
     using T = typename RT<MODE>::T;
     using A = typename RT<MODE>::A;
     using VT = VecR<T, FT>;
@@ -229,9 +271,11 @@ __device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>:
         sx[f] = 0;
     }
     VT lv[DC];
+    sy.row_begin();
 #pragma unroll
     for (int t = 0; t < DC; t++) {
         lv[t] = slots[base + 32 * t];
+        sy.add(ix, base + 32 * t);
 #pragma unroll
         for (int f = 0; f < FT; f++) {
             const A lam = (A)lv[t].x[f];
@@ -263,10 +307,12 @@ __device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>:
         }
         slots[slot] = out;
     }
+    sy.row_end();
 }
 
-template <int FT, int DC>
-__device__ __forceinline__ void row_fixed_packed(Words<FT / 2>* slots, int base) {
+template <int FT, int DC, typename SY>
+__device__ __forceinline__ void row_fixed_packed(const Idx& ix, Words<FT / 2>* slots, int base,
+                                                 SY& sy) {
     constexpr int P = FT / 2;
     using WT = Words<P>;
     uint32_t min0[P], min1[P], sx[P];
@@ -277,9 +323,11 @@ __device__ __forceinline__ void row_fixed_packed(Words<FT / 2>* slots, int base)
         sx[p] = 0;
     }
     WT lv[DC];
+    sy.row_begin();
 #pragma unroll
     for (int t = 0; t < DC; t++) {
         lv[t] = slots[base + 32 * t];
+        sy.add(ix, base + 32 * t);
 #pragma unroll
         for (int p = 0; p < P; p++) {
             const uint32_t lam = lv[t].w[p];
@@ -306,6 +354,7 @@ __device__ __forceinline__ void row_fixed_packed(Words<FT / 2>* slots, int base)
         }
         slots[base + 32 * t] = out;
     }
+    sy.row_end();
 }
 
 // Exact-degree dispatch: rows of 2 .. MAXD edges take the fully unrolled body of their
@@ -330,10 +379,10 @@ __device__ __forceinline__ bool by_degree(int d, Body&& body) {
 }
 
 // Row pass, per frame. Rows too long for an unrolled body read lambda twice (two sweeps);
-// every row's slots end up holding the new messages.
-template <int MODE, int FT, bool W, bool UNROLL = true>
+// every row's slots end up holding the new messages. sy: the syndrome gather riding along.
+template <int MODE, int FT, bool W, bool UNROLL = true, typename SY>
 __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
-                                          int n_rtasks) {
+                                          int n_rtasks, SY&& sy) {
     using T = typename RT<MODE>::T;
     using A = typename RT<MODE>::A;
     using VT = VecR<T, FT>;
@@ -347,7 +396,7 @@ __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>:
         const int base = ix.r_base[task >> 5] + (task & 31);
         if constexpr (UNROLL) {
             if (by_degree<row_body_max<MODE, FT>()>(d, [&](auto dc) {
-                    row_fixed<MODE, FT, W, decltype(dc)::value>(ix, slots, base);
+                    row_fixed<MODE, FT, W, decltype(dc)::value>(ix, slots, base, sy);
                 }))
                 continue;
         }
@@ -359,9 +408,11 @@ __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>:
             min1[f] = rbig(A());
             sx[f] = 0;
         }
+        sy.row_begin();
 #pragma unroll UNR
         for (int t = 0; t < d; t++) {
             const VT lv = slots[base + 32 * t];
+            sy.add(ix, base + 32 * t);
 #pragma unroll
             for (int f = 0; f < FT; f++) {
                 const A lam = (A)lv.x[f];
@@ -394,7 +445,9 @@ __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>:
             }
             slots[slot] = out;
         }
+        sy.row_end();
     }
+    sy.flush();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -410,9 +463,9 @@ __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>:
 //            min(|lambda| - min0, 1) is 0 there and 1 elsewhere), conditional negation
 //            by (m ^ mask) + (mask & 1) with the lane mask of the new sign.
 // ---------------------------------------------------------------------------------------
-template <int FT, bool UNROLL = true>
+template <int FT, bool UNROLL = true, typename SY>
 __device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT>* slots_v,
-                                                 int n_rtasks) {
+                                                 int n_rtasks, SY&& sy) {
     constexpr int P = FT / 2;
     using WT = Words<P>;
     constexpr int UNR = FT >= 4 ? 2 : 4;
@@ -426,7 +479,7 @@ __device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT
         const int base = ix.r_base[task >> 5] + (task & 31);
         if constexpr (UNROLL) {
             if (by_degree<row_body_max<kModeFixed, FT>()>(d, [&](auto dc) {
-                    row_fixed_packed<FT, decltype(dc)::value>(slots, base);
+                    row_fixed_packed<FT, decltype(dc)::value>(ix, slots, base, sy);
                 }))
                 continue;
         }
@@ -437,9 +490,11 @@ __device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT
             min1[p] = 0x7fff7fffu;
             sx[p] = 0;
         }
+        sy.row_begin();
 #pragma unroll UNR
         for (int t = 0; t < d; t++) {
             const WT lv = slots[base + 32 * t];
+            sy.add(ix, base + 32 * t);
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const uint32_t lam = lv.w[p];
@@ -468,7 +523,9 @@ __device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT
             }
             slots[slot] = out;
         }
+        sy.row_end();
     }
+    sy.flush();
 }
 
 // Syndrome of the current s for every row: bit f of the row's result is set when frame f
@@ -726,8 +783,12 @@ __device__ __forceinline__ void copy_to_smem(T* dst, const T* src, int n) {
 // eta, s and r at the given addresses (shared memory, or a CTA's slot of global scratch),
 // ending with the decisions of every frame written out. unsat_w: two words reset to 0.
 // UNROLL: the fully unrolled row and column bodies (false in kernels that inline several
-// tile shapes and would exceed their register budget).
-template <int MODE, int FT, bool PAPER, bool W, typename VT, bool UNROLL = true>
+// tile shapes and would exceed their register budget). ES (early-stop kernels): the row
+// pass of iteration k + 1 also gathers the syndrome of s after iteration k, which s still
+// holds until the column pass, so a tested iteration costs no pass of its own; the frames
+// that are codewords are written out between the two passes. Without ES the syndrome is a
+// pass of its own before the row pass (one barrier more per tested iteration).
+template <int MODE, int FT, bool PAPER, bool W, typename VT, bool UNROLL = true, bool ES = false>
 __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, VT* s, VT* r,
                                             uint32_t* unsat_w, int fbase, int nf,
                                             const float* walpha0, const float* wbeta0,
@@ -753,7 +814,7 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
         const int par = k & 1;
         const bool last = (k == a.L);
         const bool syn = last || (a.early_stop && (k % a.check_every == 0));
-        if (syn) {  // the decisions of the current s: stop the frames that are codewords
+        if (syn && (!ES || last)) {  // the decisions of the current s: stop the codewords
             syn_pass<MODE, FT, PAPER>(ix, s, n_rtasks, &unsat_w[par]);
             __syncthreads();
             const uint32_t conv = active & ~unsat_w[par];
@@ -772,18 +833,37 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
             ix.walpha = walpha0 + row * a.n_classes;
             ix.wbeta = wbeta0 + row * a.n_classes;
         }
-        if constexpr (kPacked)
-            rows_pass_packed<FT, UNROLL>(ix, eta, n_rtasks);
-        else
-            rows_pass<MODE, FT, W, UNROLL>(ix, eta, n_rtasks);
-        __syncthreads();  // (also orders emit's reads of s before the column pass rewrites s)
+        if (ES && syn) {
+            if constexpr (kPacked)
+                rows_pass_packed<FT, UNROLL>(ix, eta, n_rtasks,
+                                             RowSyn<MODE, FT, PAPER, true>(s, &unsat_w[par]));
+            else
+                rows_pass<MODE, FT, W, UNROLL>(ix, eta, n_rtasks,
+                                               RowSyn<MODE, FT, PAPER, true>(s, &unsat_w[par]));
+            __syncthreads();
+            const uint32_t conv = active & ~unsat_w[par];
+            if (conv) {  // s still holds the decisions of iteration k
+                emit<MODE, FT>(a, ix, s, fbase, conv, k, conv);
+                active &= ~conv;
+                if (!active) break;
+                __syncthreads();  // emit's reads of s before the column pass rewrites s
+            }
+        } else {
+            if constexpr (kPacked)
+                rows_pass_packed<FT, UNROLL>(ix, eta, n_rtasks,
+                                             RowSyn<MODE, FT, PAPER, false>(s, nullptr));
+            else
+                rows_pass<MODE, FT, W, UNROLL>(ix, eta, n_rtasks,
+                                               RowSyn<MODE, FT, PAPER, false>(s, nullptr));
+            __syncthreads();  // (also orders emit's reads of s before the column pass rewrites s)
+        }
         cols_pass<MODE, FT, UNROLL>(ix, eta, s, r, N);
         if (threadIdx.x == 0) unsat_w[par ^ 1] = 0;
         __syncthreads();
     }
 }
 
-template <int MODE, int FT, bool IDX_SMEM, bool PAPER, bool W>
+template <int MODE, int FT, bool IDX_SMEM, bool PAPER, bool W, bool ES>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
     using T = typename RT<MODE>::T;
     using VT = VecR<T, FT>;
@@ -841,15 +921,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
         const int tile = tile_sh;
         if (tile >= a.n_tiles) break;
         const int fbase = tile * FT;
-        decode_tile<MODE, FT, PAPER, W>(a, ix, eta, s, r, unsat_w, fbase, min(FT, a.frames - fbase),
-                                        walpha0, wbeta0, n_rtasks);
+        decode_tile<MODE, FT, PAPER, W, VT, true, ES>(a, ix, eta, s, r, unsat_w, fbase,
+                                                      min(FT, a.frames - fbase), walpha0, wbeta0,
+                                                      n_rtasks);
         __syncthreads();
     }
 }
 
-template <int MODE, int FT, bool IDX, bool PAPER, bool W>
+template <int MODE, int FT, bool IDX, bool PAPER, bool W, bool ES>
 int launch(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
-    auto kern = k_resident<MODE, FT, IDX, PAPER, W>;
+    auto kern = k_resident<MODE, FT, IDX, PAPER, W, ES>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
     int per_sm = 0;
@@ -862,38 +943,53 @@ int launch(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t s
 }
 
 // Instantiations: index arrays in shared memory with FT in {1, 2, 4}; in global memory
-// with FT in {1, 2}; each with the standard and the paper's slicer.
-template <int MODE, bool IDX, bool PAPER, bool W>
+// with FT in {1, 2}; each with the standard and the paper's slicer, and, for the standard
+// slicer, the early-stop form (ES) too.
+template <int MODE, bool IDX, bool PAPER, bool W, bool ES>
 int launch_ft(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
     switch (p.FT) {
-        case 1: return launch<MODE, 1, IDX, PAPER, W>(ra, p, num_sms, st);
-        case 2: return launch<MODE, 2, IDX, PAPER, W>(ra, p, num_sms, st);
+        case 1: return launch<MODE, 1, IDX, PAPER, W, ES>(ra, p, num_sms, st);
+        case 2: return launch<MODE, 2, IDX, PAPER, W, ES>(ra, p, num_sms, st);
         case 4:
-            if constexpr (IDX) return launch<MODE, 4, IDX, PAPER, W>(ra, p, num_sms, st);
+            if constexpr (IDX) return launch<MODE, 4, IDX, PAPER, W, ES>(ra, p, num_sms, st);
             break;
     }
     return LDPC_ERR_INVALID_ARG;
 }
 
-template <int MODE, bool W>
+// ES = true: decodes that test the syndrome during the iterations, standard slicer.
+template <int MODE, bool W, bool ES>
 int dispatch_w(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
-    if (p.idx_smem)
-        return ra.paper ? launch_ft<MODE, true, true, W>(ra, p, num_sms, st)
-                        : launch_ft<MODE, true, false, W>(ra, p, num_sms, st);
-    return ra.paper ? launch_ft<MODE, false, true, W>(ra, p, num_sms, st)
-                    : launch_ft<MODE, false, false, W>(ra, p, num_sms, st);
+    if constexpr (ES) {
+        return p.idx_smem ? launch_ft<MODE, true, false, W, true>(ra, p, num_sms, st)
+                          : launch_ft<MODE, false, false, W, true>(ra, p, num_sms, st);
+    } else {
+        if (p.idx_smem)
+            return ra.paper ? launch_ft<MODE, true, true, W, false>(ra, p, num_sms, st)
+                            : launch_ft<MODE, true, false, W, false>(ra, p, num_sms, st);
+        return ra.paper ? launch_ft<MODE, false, true, W, false>(ra, p, num_sms, st)
+                        : launch_ft<MODE, false, false, W, false>(ra, p, num_sms, st);
+    }
 }
+
+// Whether a decode takes the early-stop kernels.
+inline bool use_es(const ResArgs& ra) { return ra.early_stop && !ra.paper && ra.L > 0; }
 
 // Learned weights exist in FP32 mode only.
-template <int MODE>
+template <int MODE, bool ES>
 int dispatch(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
     if constexpr (MODE == kModeFP32)
-        if (ra.w_rows > 0) return dispatch_w<MODE, true>(ra, p, num_sms, st);
-    return dispatch_w<MODE, false>(ra, p, num_sms, st);
+        if (ra.w_rows > 0) return dispatch_w<MODE, true, ES>(ra, p, num_sms, st);
+    return dispatch_w<MODE, false, ES>(ra, p, num_sms, st);
 }
 
+// resident_fp32.cu / resident_fixed.cu hold the kernels without ES, resident_fp32_es.cu /
+// resident_fixed_es.cu those with it (translation units of their own: the build runs them
+// in parallel).
 int dispatch_fp32(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st);
 int dispatch_fixed(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st);
+int dispatch_fp32_es(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st);
+int dispatch_fixed_es(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st);
 
 }  // namespace resident
 }  // namespace ldpc_impl

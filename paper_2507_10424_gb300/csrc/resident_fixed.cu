@@ -1,10 +1,11 @@
-// Fixed-point instantiations of the resident kernel (see resident.cuh).
+// Fixed-point instantiations of the resident kernel (see resident.cuh), without the
+// early-stop form.
 #include "resident.cuh"
 
 namespace ldpc_impl {
 namespace resident {
 int dispatch_fixed(const ResArgs& ra, const ResidentPlan& p, int num_sms, cudaStream_t st) {
-    return dispatch<kModeFixed>(ra, p, num_sms, st);
+    return dispatch<kModeFixed, false>(ra, p, num_sms, st);
 }
 }  // namespace resident
 }  // namespace ldpc_impl

@@ -58,6 +58,8 @@ SIGNATURES = {
     "ldpc_batch_capture": (ctypes.c_int, [P]),
     "ldpc_batch_replay": (ctypes.c_int, [P]),
     "ldpc_batch_set_threads": (ctypes.c_int, [P, I32]),
+    "ldpc_batch_set_tile_frames": (ctypes.c_int, [P, I32]),
+    "ldpc_batch_get_tile_frames": (ctypes.c_int, [P, PI32]),
     "ldpc_batch_autotune": (ctypes.c_int, [P, I32, I32, PI32, ctypes.POINTER(ctypes.c_float)]),
     "ldpc_batch_info": (ctypes.c_int, [P, PI32, PI32, PI32, PI32]),
     "ldpc_batch_set_large_codes": (ctypes.c_int, [P, I32]),
@@ -75,6 +77,7 @@ SIGNATURES = {
     "ldpc_set_tuning": (ctypes.c_int, [P, I32, I32, I32]),
     "ldpc_get_tuning": (ctypes.c_int, [P, PI32, PI32, PI32]),
     "ldpc_autotune": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(ctypes.c_float)]),
+    "ldpc_autotune_data": (ctypes.c_int, [P, P, I32, I32, I32, I32, ctypes.POINTER(ctypes.c_float)]),
     "ldpc_classes": (ctypes.c_int, [P, PI32, PI32]),
     "ldpc_set_weights": (ctypes.c_int, [P, I32, P, P]),
     "ldpc_train_workspace_size": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(ctypes.c_uint64)]),
@@ -221,6 +224,13 @@ def ldpc_get_tuning(h):
 def ldpc_autotune(h, frames, max_iter):
     ms = ctypes.c_float()
     _check(load().ldpc_autotune(h, frames, max_iter, ctypes.byref(ms)), "ldpc_autotune")
+    return ms.value
+
+
+def ldpc_autotune_data(h, llr_ptr, frames, max_iter, early_stop, check_every):
+    ms = ctypes.c_float()
+    _check(load().ldpc_autotune_data(h, ctypes.c_void_p(llr_ptr), frames, max_iter, early_stop,
+                                     check_every, ctypes.byref(ms)), "ldpc_autotune_data")
     return ms.value
 
 
@@ -412,13 +422,23 @@ class Decoder:
             raise ValueError("alpha and beta must be [rows][n_classes]")
         _check(load().ldpc_set_weights(self.h, a.shape[0], _host(a), _host(b)), "ldpc_set_weights")
 
-    def autotune(self, frames: int, max_iter: int) -> float:
+    def autotune(self, frames: int, max_iter: int, llr=None, early_stop: bool = True,
+                 check_every: int = 1) -> float:
         """Pick the fastest launch shape on this device for the variant the next decode runs
-        (resident: tile shape; streaming: check-pass staging); returns its time (ms)."""
+        (resident: tile shape; streaming: check-pass staging); returns its time (ms).
+        Without llr the shapes are timed without early stop (the work then does not depend
+        on the values); with llr (a contiguous CUDA FP32 tensor [F][N]) they decode those
+        frames with the given early-stop settings."""
         import torch
         _check(load().ldpc_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
                "ldpc_set_stream")
-        return ldpc_autotune(self.h, frames, max_iter)
+        if llr is None:
+            return ldpc_autotune(self.h, frames, max_iter)
+        if (not llr.is_cuda or not llr.is_contiguous() or llr.dtype != torch.float32
+                or llr.dim() != 2 or llr.shape[1] != self.N):
+            raise ValueError("llr must be a contiguous CUDA float32 tensor [F][N]")
+        return ldpc_autotune_data(self.h, llr.data_ptr(), min(frames, llr.shape[0]), max_iter,
+                                  int(bool(early_stop)), check_every)
 
     def variant(self) -> str:
         return {LDPC_VARIANT_STREAM: "stream", LDPC_VARIANT_RESIDENT: "resident",
@@ -550,7 +570,20 @@ class Batch:
     def replay(self):
         _check(load().ldpc_batch_replay(self.b), "ldpc_batch_replay")
 
+    def set_tile_frames(self, max_frames_per_tile: int):
+        """At most 1, 2 or 4 frames per tile for the codes in shared memory; takes effect
+        at the next prepare."""
+        _check(load().ldpc_batch_set_tile_frames(self.b, max_frames_per_tile),
+               "ldpc_batch_set_tile_frames")
+
+    def tile_frames(self) -> int:
+        v = ctypes.c_int32()
+        _check(load().ldpc_batch_get_tile_frames(self.b, ctypes.byref(v)), "ldpc_batch_get_tile_frames")
+        return v.value
+
     def autotune(self, max_iter, early_stop=True):
+        """Time every cap on the frames per tile x CTA size on the prepared buffers, keep the
+        fastest and leave the batch prepared with it; returns (threads, ms)."""
         t, ms = ctypes.c_int32(), ctypes.c_float()
         _check(load().ldpc_batch_autotune(self.b, max_iter, int(early_stop), ctypes.byref(t),
                                           ctypes.byref(ms)), "ldpc_batch_autotune")

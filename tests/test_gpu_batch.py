@@ -26,10 +26,10 @@ def mixed_small():
     return codes, frames
 
 
-def check_code(code, llr, out, L, label):
+def check_code(code, llr, out, L, label, early_stop=True):
     bits, iters, ok, soft = [t.cpu().numpy() for t in out]
     g = oracle.Graph.from_code(code)
-    wb, wi, wok, ws = oracle.decode_f32(g, llr, L)
+    wb, wi, wok, ws = oracle.decode_f32(g, llr, L, early_stop)
     assert (iters == wi).all(), label
     assert (ok == wok).all(), label
     assert (bits == wb).all(), label
@@ -98,4 +98,38 @@ def test_batch_autotune_and_per_code_path_agree(torch_cuda):
         b, it, _, sf = decs[k].decode(xs[k], 20, want_soft=True)
         torch.cuda.synchronize()
         assert (b == outs[k][0]).all() and (it == outs[k][1]).all() and (sf == outs[k][3]).all()
+    batch.close()
+
+
+@pytest.mark.parametrize("cap", [1, 2, 4])
+def test_batch_frames_per_tile_caps_and_both_kernel_forms(torch_cuda, cap):
+    """Every cap on the frames per tile, with early stop (the kernel form that tests the
+    syndrome in the row pass) and without, gives the oracle's results; invalid caps are
+    refused and leave the cap as it was."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Batch, Decoder, LdpcError
+    codes, frames = mixed_small()
+    decs = [Decoder.from_code(c) for c in codes]
+    batch = Batch(decs)
+    L = 25
+    ins, outs = [], []
+    for k, (c, F) in enumerate(zip(codes, frames)):
+        llr = inputs.all_zero_awgn_llr(max(F, 1), c.N, 2.0, c.design_rate, 70 + k)[:F]
+        x = torch.from_numpy(np.ascontiguousarray(llr)).cuda()
+        ins.append(llr)
+        outs.append(batch.set_io(k, x, want_ok=True, want_soft=True))
+    assert batch.tile_frames() == 4
+    batch.set_tile_frames(cap)
+    assert batch.tile_frames() == cap
+    for bad in (0, 3, 8):
+        with pytest.raises(LdpcError):
+            batch.set_tile_frames(bad)
+    assert batch.tile_frames() == cap
+    for es in (True, False, True):
+        batch.decode(L, early_stop=es)
+        batch.stream.synchronize()
+        assert batch.info()["n_tiles"] >= sum(frames[:3]) // cap
+        for k, c in enumerate(codes):
+            if frames[k]:
+                check_code(c, ins[k], outs[k], L, f"cap {cap} early_stop={es} code {k}", es)
     batch.close()

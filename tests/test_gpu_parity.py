@@ -278,13 +278,20 @@ def test_edge_cases(torch_cuda, mode, variant):
 
 @pytest.mark.parametrize("mode", MODES)
 def test_every_resident_launch_shape(torch_cuda, mode):
-    """Results must not depend on the launch shape: frames per tile and CTA size."""
+    """Results must not depend on the launch shape: frames per tile and CTA size, each with
+    early stop (the kernels that test the syndrome inside the row pass; frames of one tile
+    stop at different iterations) and without (the syndrome after the last iteration)."""
     torch = torch_cuda
     from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
     code = inputs.cfg_qc_2304()
-    cw = inputs.Encoder(code).random_codewords(67, 5)
-    llr = inputs.bpsk_awgn_llr(cw, 2.5, code.design_rate, 6)
-    want = oracle_decode(code, llr, 8, mode)
+    F = 67
+    cw = inputs.Encoder(code).random_codewords(F, 5)
+    snr = np.random.default_rng(7).permutation(np.linspace(2.5, 8.0, F))
+    llr = np.concatenate([inputs.bpsk_awgn_llr(cw[k:k + 1], float(snr[k]), code.design_rate, 600 + k)
+                          for k in range(F)])
+    llr[[3, 40]] = (1 - 2 * cw[[3, 40]].astype(np.float32)) * 4.0  # codewords at the input
+    want = {es: oracle_decode(code, llr, 8, mode, early_stop=es) for es in (True, False)}
+    assert len(np.unique(want[True][1])) >= 7  # tiles mix frames that stop at k = 0 .. 8
     x = torch.from_numpy(llr).cuda()
     tried = 0
     for ft in (1, 2, 4):
@@ -297,10 +304,11 @@ def test_every_resident_launch_shape(torch_cuda, mode):
                 except LdpcError:
                     continue
                 assert dec.tuning()[2] == ip
-                b, it, ok, sf = dec.decode(x, 8, want_ok=True, want_soft=True)
-                torch.cuda.synchronize()
-                got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
-                assert_parity(got, want, mode, f"FT={ft} threads={th} index={ip}")
+                for es in (True, False):
+                    b, it, ok, sf = dec.decode(x, 8, early_stop=es, want_ok=True, want_soft=True)
+                    torch.cuda.synchronize()
+                    got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
+                    assert_parity(got, want[es], mode, f"FT={ft} threads={th} index={ip} es={es}")
                 tried += 1
                 dec.close()
     assert tried >= 12
@@ -320,6 +328,40 @@ def test_autotune_keeps_results(torch_cuda, mode):
     torch.cuda.synchronize()
     got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
     assert_parity(got, oracle_decode(code, llr, 20, mode), mode, "after autotune")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_autotune_on_the_callers_frames(torch_cuda, mode):
+    """ldpc_autotune_data times the shapes on the caller's frames with early stop; the
+    decode after it must still equal the oracle, the frames must be left as they were,
+    and invalid arguments must be refused before any work."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300 import ldpc
+    from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
+    code = inputs.cfg_regular_576()
+    llr = inputs.all_zero_awgn_llr(700, code.N, 2.0, code.design_rate, 92)
+    x = torch.from_numpy(llr).cuda()
+    dec = Decoder.from_code(code, mode=mode)
+    ms = dec.autotune(700, 20, llr=x, early_stop=True)
+    ft, th, ip = dec.tuning()
+    assert ms > 0 and ft in (1, 2, 4) and th % 32 == 0 and 64 <= th <= 1024 and ip in (1, 2)
+    assert np.array_equal(x.cpu().numpy(), llr)
+    b, it, ok, sf = dec.decode(x, 20, want_ok=True, want_soft=True)
+    torch.cuda.synchronize()
+    got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
+    assert_parity(got, oracle_decode(code, llr, 20, mode), mode, "after autotune on data")
+    for args, status in (((x.data_ptr(), 700, 20, 2, 1), ldpc.LDPC_ERR_INVALID_ARG),
+                         ((x.data_ptr(), 700, 20, 1, 0), ldpc.LDPC_ERR_INVALID_ARG),
+                         ((x.data_ptr(), 0, 20, 1, 1), ldpc.LDPC_ERR_INVALID_ARG),
+                         ((x.data_ptr(), 700, -1, 1, 1), ldpc.LDPC_ERR_INVALID_ARG),
+                         ((llr.ctypes.data, 700, 20, 1, 1), ldpc.LDPC_ERR_BAD_POINTER)):
+        with pytest.raises(LdpcError) as e:
+            ldpc.ldpc_autotune_data(dec.h, *args)
+        assert e.value.status == status
+    assert dec.tuning() == (ft, th, ip)
+    with pytest.raises(ValueError):
+        dec.autotune(700, 20, llr=x.double())
+    dec.close()
 
 
 def test_errors_on_device_arguments(torch_cuda):

@@ -104,14 +104,15 @@ def test_wait_that_runs_out_is_reported_and_the_next_decode_is_correct(torch_cud
 
 
 @pytest.mark.parametrize("mode", ["fp32", "fixed"])
-def test_autotune_picks_a_staging_and_keeps_results(torch_cuda, mode):
+@pytest.mark.parametrize("on_data", [False, True])
+def test_autotune_picks_a_staging_and_keeps_results(torch_cuda, mode, on_data):
     from paper_2507_10424_gb300.ldpc import Decoder
     torch = torch_cuda
     code = codes()["irregular1200"]
     llr = inputs.all_zero_awgn_llr(700, code.N, 2.0, code.design_rate, 44)
     dec = Decoder.from_code(code, mode=mode)
     dec.set_variant("stream")
-    ms = dec.autotune(700, 12)
+    ms = dec.autotune(700, 12, llr=torch.from_numpy(llr).cuda() if on_data else None)
     assert ms > 0
     w, s, v = dec.stream_staging()
     assert (s == 0) or (1 <= w <= 12 and 2 <= s <= 8)
