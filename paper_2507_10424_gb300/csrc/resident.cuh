@@ -783,11 +783,14 @@ __device__ __forceinline__ void copy_to_smem(T* dst, const T* src, int n) {
 // eta, s and r at the given addresses (shared memory, or a CTA's slot of global scratch),
 // ending with the decisions of every frame written out. unsat_w: two words reset to 0.
 // UNROLL: the fully unrolled row and column bodies (false in kernels that inline several
-// tile shapes and would exceed their register budget). ES (early-stop kernels): the row
-// pass of iteration k + 1 also gathers the syndrome of s after iteration k, which s still
-// holds until the column pass, so a tested iteration costs no pass of its own; the frames
-// that are codewords are written out between the two passes. Without ES the syndrome is a
-// pass of its own before the row pass (one barrier more per tested iteration).
+// tile shapes and would exceed their register budget). Weighted rows always take the loop
+// form: unrolled, their per-edge class and weight loads raised the early-stop kernels to
+// the 64-register bound, which costs small tiles resident CTAs per SM.
+// ES (early-stop kernels): the row pass of iteration k + 1 also gathers the syndrome of s
+// after iteration k, which s still holds until the column pass, so a tested iteration
+// costs no pass of its own; the frames that are codewords are written out between the
+// two passes. Without ES the syndrome is a pass of its own before the row pass (one
+// barrier more per tested iteration).
 template <int MODE, int FT, bool PAPER, bool W, typename VT, bool UNROLL = true, bool ES = false>
 __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, VT* s, VT* r,
                                             uint32_t* unsat_w, int fbase, int nf,
@@ -838,7 +841,7 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
                 rows_pass_packed<FT, UNROLL>(ix, eta, n_rtasks,
                                              RowSyn<MODE, FT, PAPER, true>(s, &unsat_w[par]));
             else
-                rows_pass<MODE, FT, W, UNROLL>(ix, eta, n_rtasks,
+                rows_pass<MODE, FT, W, UNROLL && !W>(ix, eta, n_rtasks,
                                                RowSyn<MODE, FT, PAPER, true>(s, &unsat_w[par]));
             __syncthreads();
             const uint32_t conv = active & ~unsat_w[par];
@@ -853,7 +856,7 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
                 rows_pass_packed<FT, UNROLL>(ix, eta, n_rtasks,
                                              RowSyn<MODE, FT, PAPER, false>(s, nullptr));
             else
-                rows_pass<MODE, FT, W, UNROLL>(ix, eta, n_rtasks,
+                rows_pass<MODE, FT, W, UNROLL && !W>(ix, eta, n_rtasks,
                                                RowSyn<MODE, FT, PAPER, false>(s, nullptr));
             __syncthreads();  // (also orders emit's reads of s before the column pass rewrites s)
         }
