@@ -272,6 +272,75 @@ def other_workloads(timed):
     return out
 
 
+def early_stop_latency(timed, code, x, cw, L, mode):
+    """The headline batch (same LLRs: random codewords at every Eb/N0 of the mix) decoded
+    with early stop: launch-to-completion time of the whole batch and the decoded rate,
+    on a decoder whose launch shape is tuned on these frames."""
+    import torch
+    from paper_2507_10424_gb300.ldpc import Decoder
+    F = x.shape[0]
+    dec = Decoder.from_code(code, mode=mode)
+    dec.autotune(F, L, llr=x, early_stop=True)
+    o = (torch.empty((F, code.N), dtype=torch.uint8, device="cuda"),
+         torch.empty(F, dtype=torch.int32, device="cuda"), None, None)
+    ms = timed(lambda: dec.decode(x, L, early_stop=True, out=o), 10, 3)
+    it = o[1].float()
+    res = {"frames": F, "max_iter": L, "ms_per_batch": ms,
+           "Gbit/s": F * code.N / (ms * 1e-3) / 1e9, "mean_iter": float(it.mean().item()),
+           "max_iter_used": int(it.max().item()),
+           "fer": float((o[0] != torch.from_numpy(cw).cuda()).any(dim=1).float().mean().item()),
+           "tuning": dict(zip(("frames_per_tile", "threads", "index_placement"), dec.tuning()))}
+    dec.close()
+    return res
+
+
+def paper_shaped(timed):
+    """The paper's decoding protocol on a stand-in with its code's dimensions (N=8176,
+    M=1022: a 2x16 base of 511x511 blocks, each the sum of two seeded circulant
+    permutations; the paper's matrix is not available): 50 random codewords at each Eb/N0
+    of 3.0, 3.2, 3.4 and 3.6 dB (200 frames), at most 60 iterations, the syndrome tested
+    every 6 iterations as in the paper's runs. Device-resident time per call, and end to
+    end through ldpc_decode_host with pinned host buffers. The paper reports 48.31 s for
+    this protocol on its code (about 33.8 kbit/s), given beside as context only."""
+    import torch
+    from paper_2507_10424_gb300 import inputs
+    from paper_2507_10424_gb300.ldpc import Decoder
+    code = inputs.cfg_paper_shaped()
+    cw = inputs.Encoder(code).random_codewords(200, 21)
+    llr = np.concatenate([inputs.bpsk_awgn_llr(cw[50 * k:50 * k + 50], e, code.design_rate, 40 + k)
+                          for k, e in enumerate((3.0, 3.2, 3.4, 3.6))])
+    x = torch.from_numpy(llr).cuda()
+    xh = torch.from_numpy(llr).pin_memory()
+    F, L, CE = 200, 60, 6
+    paper_bits_per_s = F * code.N / 48.31
+    out = {"code": f"N={code.N} M={code.M} E={code.E}, column weight 4, row weight 32",
+           "frames": F, "max_iter": L, "check_every": CE,
+           "paper_reported_Gbit/s": paper_bits_per_s / 1e9}
+    for mode in ("fp32", "fixed"):
+        dec = Decoder.from_code(code, mode=mode)
+        dec.autotune(F, L, llr=x, early_stop=True, check_every=CE)
+        o = (torch.empty((F, code.N), dtype=torch.uint8, device="cuda"),
+             torch.empty(F, dtype=torch.int32, device="cuda"), None, None)
+        ms = timed(lambda: dec.decode(x, L, early_stop=True, check_every=CE, out=o), 20, 3)
+        ho = (torch.empty((F, code.N), dtype=torch.uint8).pin_memory(),
+              torch.empty(F, dtype=torch.int32).pin_memory(), None, None)
+        for _ in range(3):
+            dec.decode_host(xh, L, early_stop=True, check_every=CE, out=ho)
+        t = time.perf_counter()
+        for _ in range(20):
+            dec.decode_host(xh, L, early_stop=True, check_every=CE, out=ho)
+        te = (time.perf_counter() - t) / 20
+        assert (ho[0] == o[0].cpu()).all()
+        gbit = F * code.N / (ms * 1e-3) / 1e9
+        out[mode] = {"variant": dec.variant(), "ms_per_call": ms, "Gbit/s": gbit,
+                     "e2e_ms_per_call": te * 1e3, "e2e_Gbit/s": F * code.N / te / 1e9,
+                     "mean_iter": float(o[1].float().mean().item()),
+                     "fer": float((o[0] != torch.from_numpy(cw).cuda()).any(dim=1).float().mean().item()),
+                     "e2e_vs_paper_reported": F * code.N / te / paper_bits_per_s}
+        dec.close()
+    return out
+
+
 # ------------------------------------------------------------------ learned decoder
 
 def learned_vs_plain_large(timed):
@@ -637,8 +706,10 @@ def main():
                                          "identical_bits": bool((od[0] == bits[:Fd]).all())}
         dd.close()
         result["other_paths"] = others
+        result["early_stop_latency"] = early_stop_latency(timed, code, x, cw, L, mode)
         if rank == 0:
             result["other_workloads"] = other_workloads(timed)
+            result["paper_shaped"] = paper_shaped(timed)
             result["learned"] = learned_vs_plain(timed)
             result["learned_large"] = learned_vs_plain_large(timed)
             result["mixed_codes"] = mixed_codes(timed)

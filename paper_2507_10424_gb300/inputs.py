@@ -283,6 +283,24 @@ def cfg_irregular_64800(seed: int = 5) -> Code:
     return irregular_code(64800, 32400, [2, 3, 8], [0.5, 0.375, 0.125], seed)
 
 
+def cfg_paper_shaped(seed: int = 4) -> Code:
+    """Stand-in with the dimensions of the paper's code (N=8176, M=1022), whose matrix is
+    not available: a 2x16 base of 511x511 blocks, each block the sum of two circulant
+    permutations with distinct seeded shifts, so every column has weight 4 and every row
+    weight 32 (E=32704)."""
+    rng = np.random.default_rng(seed)
+    mb, nb, Z = 2, 16, 511
+    rows, cols = [], []
+    z = np.arange(Z)
+    for r in range(mb):
+        for c in range(nb):
+            for sh in rng.choice(Z, size=2, replace=False):
+                rows.append(r * Z + z)
+                cols.append(c * Z + (z + int(sh)) % Z)
+    return _make_code(mb * Z, nb * Z, np.concatenate(rows), np.concatenate(cols),
+                      f"paper-shaped 2x16 Z=511 weight-2 circulants seed={seed}")
+
+
 MIXED_N = (256, 512, 1024, 2048, 4096, 8192, 12288, 16200)
 MIXED_RATES = (1 / 2, 2 / 3, 3 / 4, 5 / 6)
 

@@ -331,6 +331,22 @@ def test_autotune_keeps_results(torch_cuda, mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
+def test_paper_shaped_code_with_check_every_6(torch_cuda, mode):
+    """The stand-in with the paper's code dimensions (rows of 32 edges, columns of 4), at
+    most 60 iterations and the syndrome tested every 6 as in the paper's runs; Eb/N0 from
+    the paper's 3.0 dB up to 6.5 dB so that frames stop at 6, 12 and 60 iterations."""
+    code = inputs.cfg_paper_shaped()
+    cw = inputs.Encoder(code).random_codewords(24, 31)
+    snr = np.linspace(3.0, 6.5, 24)
+    llr = np.concatenate([inputs.bpsk_awgn_llr(cw[k:k + 1], float(snr[k]), code.design_rate, 50 + k)
+                          for k in range(24)])
+    want = oracle_decode(code, llr, 60, mode, check_every=6)
+    assert len(np.unique(want[1])) >= 3
+    got = gpu_decode(torch_cuda, code, llr, 60, mode, check_every=6)
+    assert_parity(got, want, mode, "paper-shaped")
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_autotune_on_the_callers_frames(torch_cuda, mode):
     """ldpc_autotune_data times the shapes on the caller's frames with early stop; the
     decode after it must still equal the oracle, the frames must be left as they were,

@@ -34,6 +34,21 @@ def test_qc_code_structure():
                 assert (blk == np.roll(np.eye(96, dtype=np.uint8), base[r, col], axis=1)).all()
 
 
+def test_paper_shaped_code_structure():
+    c = inputs.cfg_paper_shaped()
+    assert (c.M, c.N, c.E) == (1022, 8176, 32704)
+    assert (c.row_weights() == 32).all() and (c.col_weights() == 4).all()
+    assert no_duplicate_edges(c)
+    # block (r, b) of the 2x16 base holds exactly two ones in every row and column
+    H = c.dense().astype(np.int64)
+    for r in range(2):
+        for b in range(16):
+            blk = H[r * 511:(r + 1) * 511, b * 511:(b + 1) * 511]
+            assert (blk.sum(axis=0) == 2).all() and (blk.sum(axis=1) == 2).all()
+    cw = inputs.Encoder(c).random_codewords(8, 3)
+    assert not ((H @ cw.T.astype(np.int64)) % 2).any()
+
+
 def test_irregular_code_degree_counts():
     c = inputs.cfg_irregular_64800()
     assert (c.M, c.N, c.E) == (32400, 64800, 202500)
