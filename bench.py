@@ -678,6 +678,26 @@ def main():
                          "h2d_bytes_per_step": int(xh.numel() * 4),
                          "d2h_bytes_per_step": int(bh.numel() + ih.numel() * 4),
                          "ms_per_step": te * 1e3}
+
+        # the host link alone, outside the timed region: the same bytes copied between the
+        # pinned buffers and the device with no decode (the pipelined e2e step cannot beat
+        # its input copy)
+        def link_ms(dst, src, n=5):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0.record(stream)
+            for _ in range(n):
+                dst.copy_(src, non_blocking=True)
+            l1.record(stream)
+            torch.cuda.synchronize()
+            return l0.elapsed_time(l1) / n
+
+        xd = torch.empty_like(x)
+        h2d_ms, d2h_ms = link_ms(xd, xh), link_ms(bh, bits)
+        del xd
+        result["e2e"]["link"] = {"h2d_ms": h2d_ms, "h2d_GBs": xh.numel() * 4 / h2d_ms / 1e6,
+                                 "d2h_ms": d2h_ms, "d2h_GBs": bh.numel() / d2h_ms / 1e6}
     if not args.quick and args.workload == "qc2304":
         # the other arithmetic mode and the other kernel variant, same workload
         others = {}

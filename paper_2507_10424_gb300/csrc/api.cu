@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/ldpc.h"
 #include "ldpc_internal.h"
@@ -543,6 +544,34 @@ int ldpc_decode_host(ldpc_t* h, const void* llr_host, int32_t llr_dtype, int32_t
     // chunk so that several chunks are in flight and each still fills the GPU
     int32_t chunk = std::max<int32_t>(1024, std::min<int32_t>(frames, (frames + 3) / 4));
     chunk = std::min<int32_t>(chunk, std::max<int32_t>(1024, (int32_t)((512ull << 20) / (N * in_b))));
+    // Chunk sizes: nothing overlaps the first chunk's input copy or the last chunk's output
+    // copy, so the schedule ramps up from an eighth of the chunk (doubling: the next
+    // chunk's input copy still hides behind the decode of the current one) and back down
+    // at the end.
+    std::vector<int32_t> sizes;
+    {
+        const int32_t first = std::max<int32_t>(1024, chunk / 8);  // still fills the GPU
+        std::vector<int32_t> ramp;  // first, 2 first, ... up to half a chunk
+        for (int32_t c = first; 2 * c <= chunk; c *= 2) ramp.push_back(c);
+        int64_t ramp_sum = 0;
+        for (int32_t c : ramp) ramp_sum += c;
+        int32_t left = frames;
+        if ((int64_t)frames >= 2 * ramp_sum + chunk) {
+            for (int32_t c : ramp) sizes.push_back(c);
+            left -= (int32_t)ramp_sum;
+            while (left > ramp_sum) {
+                const int32_t c = (int32_t)std::min<int64_t>(chunk, left - ramp_sum);
+                sizes.push_back(c);
+                left -= c;
+            }
+            for (auto it = ramp.rbegin(); it != ramp.rend(); ++it) {
+                sizes.push_back(*it);
+                left -= *it;
+            }
+        } else {  // too few frames for a ramp: even chunks
+            for (; left > 0; left -= std::min(chunk, left)) sizes.push_back(std::min(chunk, left));
+        }
+    }
     const size_t per_frame = (size_t)N * in_b + (size_t)N + 4 + 1 + (soft_host ? (size_t)N * 4 : 0);
     const size_t need = ((size_t)chunk * per_frame + 4096);
     if (!h->h2d) {
@@ -571,10 +600,10 @@ int ldpc_decode_host(ldpc_t* h, const void* llr_host, int32_t llr_dtype, int32_t
         h->stage_bytes = need;
     }
     int launches = 0;
-    const int nchunks = (frames + chunk - 1) / chunk;
-    for (int c = 0; c < nchunks; c++) {
+    int32_t f0 = 0;
+    for (int c = 0; c < (int)sizes.size(); f0 += sizes[c], c++) {
         const int s = c & 1;
-        const int32_t f0 = c * chunk, nf = std::min(chunk, frames - f0);
+        const int32_t nf = sizes[c];
         char* base = (char*)h->stage[s];
         void* d_llr = base;
         uint8_t* d_bits = (uint8_t*)(base + (((size_t)chunk * N * in_b + 255) & ~(size_t)255));

@@ -442,11 +442,13 @@ def test_workspace_too_large_is_an_error_not_a_crash(torch_cuda):
 
 
 @pytest.mark.parametrize("mode", MODES)
-def test_host_buffer_pipeline_matches_device_path(torch_cuda, mode):
+@pytest.mark.parametrize("F", [2500, 9000])
+def test_host_buffer_pipeline_matches_device_path(torch_cuda, mode, F):
+    """2500 frames: even chunks with a ragged last one; 9000 frames: chunk sizes that ramp
+    up from and back down to 1024 frames, with a short chunk between."""
     torch = torch_cuda
     from paper_2507_10424_gb300.ldpc import Decoder
     code = inputs.cfg_qc_2304()
-    F = 2500  # several chunks of the host pipeline with a ragged last one
     llr = inputs.all_zero_awgn_llr(F, code.N, 1.5, code.design_rate, 77)
     dec = Decoder.from_code(code, mode=mode)
     xh = torch.from_numpy(llr).pin_memory()
