@@ -50,6 +50,7 @@ typedef struct ldpc ldpc_t; /* opaque handle */
 #define LDPC_ERR_OOM (-4)          /* device or host allocation failed */
 #define LDPC_ERR_CUDA (-5)         /* a CUDA runtime call failed; see ldpc_last_cuda_error */
 #define LDPC_ERR_TIMEOUT (-6)      /* a bounded wait inside a kernel ran out (ldpc_check_device) */
+#define LDPC_ERR_DEVICE_CHECK (-7) /* the debug checks (ldpc_set_debug) found a NaN LLR or an index out of range */
 #define LDPC_ERR_UNSUPPORTED (-8)  /* the request needs a feature this build or device lacks */
 
 /* Arithmetic modes. */
@@ -67,6 +68,7 @@ typedef struct ldpc ldpc_t; /* opaque handle */
 
 /* Flags for ldpc_create_ex. */
 #define LDPC_FLAG_PAPER_SLICER 1 /* b_j = [s_j > 0], the slicer as printed in eq. (slice) */
+#define LDPC_FLAG_DEBUG 2        /* device-side debug checks before every decode (ldpc_set_debug) */
 
 /* Kernel variants (ldpc_set_variant). */
 #define LDPC_VARIANT_AUTO 0     /* resident when a frame fits in shared memory, else streaming */
@@ -335,6 +337,31 @@ int ldpc_autotune(ldpc_t *h, int32_t frames, int32_t max_iter, float *best_ms);
  */
 int ldpc_autotune_data(ldpc_t *h, const float *llr, int32_t frames, int32_t max_iter,
                        int32_t early_stop, int32_t check_every, float *best_ms);
+
+/*
+ * ldpc_set_debug: device-side debug checks on (1) or off (0). While on, ldpc_decode,
+ * ldpc_decode_i8, ldpc_decode_ex and ldpc_decode_host first run checking kernels on the
+ * handle's stream over every index array the decode kernels read through (CSR/CSC
+ * offsets and indices, the sliced and padded layouts' slot ids, column positions, slice
+ * degrees and weight classes: each within the array it indexes) and over the caller's FP32
+ * LLRs (no NaN: the decoder does not define it), then synchronise the stream and read the
+ * result. A violation returns LDPC_ERR_DEVICE_CHECK and no decode kernel is launched; the
+ * outputs are left untouched. Slow (a stream synchronisation per call): for testing and
+ * diagnosis. Also switched on at create by LDPC_FLAG_DEBUG, or by the environment variable
+ * LDPC_DEBUG=1 (read by ldpc_create / ldpc_create_ex). Errors: LDPC_ERR_INVALID_ARG for
+ * on not 0/1; LDPC_ERR_OOM if the report buffer cannot be allocated.
+ *
+ * ldpc_debug_report: the first violation of the last decode that the checks refused, then
+ * clears it. what: 0 none, 1 a NaN LLR (where = frame * N + bit), 2 an index array (where
+ * = array id << 40 | entry; ids: 1 row offsets, 2 column offsets, 3 column index of an
+ * edge, 4 edge of a CSC entry, 5 column class, 6 row slice offsets, 7 column slice
+ * offsets, 8 row slice degree, 9 column slice degree, 10 column position of a row slot,
+ * 11 row slot of a column entry, 12 column position of a bit, 13 class of a row slot,
+ * 14 column of a padded row slot, 15 padded row degree, 16 padded slot of an edge, 17 class
+ * of a padded row slot). what and where are host pointers.
+ */
+int ldpc_set_debug(ldpc_t *h, int32_t on);
+int ldpc_debug_report(ldpc_t *h, int32_t *what, int64_t *where);
 
 /* ldpc_get_tuning: the resident launch shape in force for the current mode. */
 int ldpc_get_tuning(const ldpc_t *h, int32_t *frames_per_tile, int32_t *threads,

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libldpc.so")
 SOURCES = ["graph.cpp", "api.cu", "stream.cu", "stream_fp32.cu", "stream_fixed.cu", "resident.cu",
            "resident_fp32.cu", "resident_fp32_es.cu", "resident_fixed.cu", "resident_fixed_es.cu", "noalloc.cu", "learn_kernels.cu", "batch.cu",
-           "dense_kernels.cu", "cluster.cu"]
+           "dense_kernels.cu", "cluster.cu", "debug.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -76,7 +76,11 @@ struct ldpc {
     int32_t stream_group = -1;   // streaming: -1 no frame groups, 0 L2-sized groups, > 0 group size
     int l2_bytes = 0;
     int32_t* counters = nullptr;  // [0] resident / cluster tile counter, [1] streaming done
-                                  // count, [2] device error word (bounded waits that ran out)
+                                  // count, [2] device error word (bounded waits that ran out),
+                                  // [4..7] the debug checks' report (two 64-bit words)
+    int debug = 0;                // ldpc_set_debug
+    int32_t dbg_what = 0;         // the last refused decode's first violation
+    int64_t dbg_where = 0;
     // staged streaming check pass: requested warps per CTA and stages (0 = automatic,
     // stages -1 = off) and the tries of each bounded wait
     int32_t st_warps = 0, st_stages = 0, st_vw = 0;
@@ -281,6 +285,8 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
     }
     h->mode = mode;
     h->flags = flags;
+    const char* dbg_env = std::getenv("LDPC_DEBUG");
+    h->debug = ((flags & LDPC_FLAG_DEBUG) || (dbg_env && dbg_env[0] == '1' && dbg_env[1] == 0)) ? 1 : 0;
     h->M = hg.M;
     h->N = hg.N;
     h->E = hg.E;
@@ -356,9 +362,9 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
         h->plan[kModeFP32] = resident_plan(kModeFP32, d, hg.N, h->device);
         h->plan[kModeFixed] = resident_plan(kModeFixed, d, hg.N, h->device);
     }
-    e = cudaMalloc((void**)&h->counters, 4 * sizeof(int32_t));
+    e = cudaMalloc((void**)&h->counters, 8 * sizeof(int32_t));
     if (e != cudaSuccess) return bail(alloc_fail(e));
-    e = cudaMemset(h->counters, 0, 4 * sizeof(int32_t));
+    e = cudaMemset(h->counters, 0, 8 * sizeof(int32_t));
     if (e != cudaSuccess) return bail(cuda_fail(e));
     h->hg = std::move(hg);
     g_last_error = LDPC_OK;
@@ -387,7 +393,7 @@ ldpc_t* ldpc_create_ex(int32_t M, int32_t N, int32_t h_format, const void* h_a, 
         fail(LDPC_ERR_INVALID_ARG);
         return nullptr;
     }
-    if (flags & ~LDPC_FLAG_PAPER_SLICER) {
+    if (flags & ~(LDPC_FLAG_PAPER_SLICER | LDPC_FLAG_DEBUG)) {
         fail(LDPC_ERR_INVALID_ARG);
         return nullptr;
     }
@@ -414,6 +420,24 @@ ldpc_t* ldpc_create(int32_t M, int32_t N, const uint8_t* H) {
     return ldpc_create_ex(M, N, LDPC_H_DENSE_U8, H, nullptr, LDPC_MODE_FP32, 0);
 }
 
+// The debug checks of one decode (ldpc_set_debug): enqueue them, wait, read the report.
+static int debug_checks(ldpc_t* h, const void* llr, int llr_is_i8, int32_t frames) {
+    auto* rep = reinterpret_cast<unsigned long long*>(h->counters + 4);
+    int rc = debug_check_launch(h->dg, h->M, h->N, h->E, llr, llr_is_i8, frames, rep, h->stream);
+    if (rc != LDPC_OK) return rc;
+    unsigned long long r[2];
+    cudaError_t e = cudaMemcpyAsync(r, rep, sizeof(r), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        return LDPC_ERR_CUDA;
+    }
+    if (r[0] == ~0ull && r[1] == ~0ull) return LDPC_OK;
+    h->dbg_what = r[0] != ~0ull ? 1 : 2;
+    h->dbg_where = (int64_t)(r[0] != ~0ull ? r[0] : r[1]);
+    return LDPC_ERR_DEVICE_CHECK;
+}
+
 int ldpc_decode_ex(ldpc_t* h, const void* llr, int32_t llr_dtype, int32_t frames, int32_t max_iter,
                    int32_t early_stop, int32_t check_every, uint8_t* out_bits, int32_t* out_iters,
                    uint8_t* out_ok, float* out_soft) {
@@ -427,6 +451,10 @@ int ldpc_decode_ex(ldpc_t* h, const void* llr, int32_t llr_dtype, int32_t frames
     if (!is_device_ptr(llr) || !is_device_ptr(out_bits) || !is_device_ptr(out_iters) ||
         (out_ok && !is_device_ptr(out_ok)) || (out_soft && !is_device_ptr(out_soft)))
         return fail(LDPC_ERR_BAD_POINTER);
+    if (h->debug) {
+        const int rc = debug_checks(h, llr, llr_dtype == LDPC_LLR_I8, frames);
+        if (rc != LDPC_OK) return fail(rc);
+    }
     DecodeArgs a;
     a.M = h->M;
     a.N = h->N;
@@ -941,6 +969,22 @@ int ldpc_check_device(ldpc_t* h) {
     return fail(LDPC_ERR_TIMEOUT);
 }
 
+int ldpc_set_debug(ldpc_t* h, int32_t on) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (on != 0 && on != 1) return fail(LDPC_ERR_INVALID_ARG);
+    h->debug = on;
+    return LDPC_OK;
+}
+
+int ldpc_debug_report(ldpc_t* h, int32_t* what, int64_t* where) {
+    if (!h || !what || !where) return fail(LDPC_ERR_BAD_POINTER);
+    *what = h->dbg_what;
+    *where = h->dbg_where;
+    h->dbg_what = 0;
+    h->dbg_where = 0;
+    return LDPC_OK;
+}
+
 int ldpc_set_wait_limit(ldpc_t* h, int32_t tries) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
     if (tries < 0) return fail(LDPC_ERR_INVALID_ARG);
@@ -1026,6 +1070,7 @@ const char* ldpc_strerror(int status) {
         case LDPC_ERR_OOM: return "out of memory";
         case LDPC_ERR_CUDA: return "CUDA runtime error";
         case LDPC_ERR_TIMEOUT: return "a bounded wait inside a kernel ran out";
+        case LDPC_ERR_DEVICE_CHECK: return "the debug checks found a NaN LLR or an index out of range";
         case LDPC_ERR_UNSUPPORTED: return "unsupported for this code or device";
     }
     return "unknown status";

@@ -154,6 +154,17 @@ struct DevGraph {
     int64_t eta_slots = 0;
 };
 
+// Index arrays the debug checks cover (ids in the report of ldpc_debug_report).
+enum class DebugArray : int {
+    kRowPtr = 1, kColPtr, kColIdx, kColEdge, kColClass, kRowBase, kColBase, kRowDeg, kColDeg,
+    kRowSlotPos, kColSlot, kColPos, kRowSlotCls, kEllCol, kEllDeg, kEllCslot, kEllCls
+};
+// Enqueue the debug checks of a decode on st (debug.cu): rep[0] receives the smallest flat
+// index of a NaN FP32 LLR, rep[1] the smallest (array id << 40 | entry) of an index out of
+// range; both stay all ones when nothing is found.
+int debug_check_launch(const DevGraph& g, int32_t M, int32_t N, int64_t E, const void* llr, int llr_is_i8,
+                       int64_t frames, unsigned long long* rep, cudaStream_t st);
+
 // ---------------------------------------------------------------------------------------
 // Launch parameters shared by the variants.
 // ---------------------------------------------------------------------------------------

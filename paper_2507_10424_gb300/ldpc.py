@@ -22,6 +22,7 @@ LDPC_ERR_BAD_POINTER = -3
 LDPC_ERR_OOM = -4
 LDPC_ERR_CUDA = -5
 LDPC_ERR_TIMEOUT = -6
+LDPC_ERR_DEVICE_CHECK = -7
 LDPC_ERR_UNSUPPORTED = -8
 LDPC_MODE_FP32 = 0
 LDPC_MODE_FIXED = 1
@@ -31,6 +32,7 @@ LDPC_H_CSR = 2
 LDPC_LLR_F32 = 0
 LDPC_LLR_I8 = 1
 LDPC_FLAG_PAPER_SLICER = 1
+LDPC_FLAG_DEBUG = 2
 LDPC_VARIANT_AUTO = 0
 LDPC_VARIANT_STREAM = 1
 LDPC_VARIANT_RESIDENT = 2
@@ -72,6 +74,8 @@ SIGNATURES = {
     "ldpc_get_stream_staging": (ctypes.c_int, [P, PI32, PI32, PI32]),
     "ldpc_check_device": (ctypes.c_int, [P]),
     "ldpc_set_wait_limit": (ctypes.c_int, [P, I32]),
+    "ldpc_set_debug": (ctypes.c_int, [P, I32]),
+    "ldpc_debug_report": (ctypes.c_int, [P, PI32, PI64]),
     "ldpc_set_cluster_shape": (ctypes.c_int, [P, I32, I32, I32]),
     "ldpc_get_cluster_shape": (ctypes.c_int, [P, PI32, PI32, PI32, PI32]),
     "ldpc_set_tuning": (ctypes.c_int, [P, I32, I32, I32]),
@@ -316,10 +320,10 @@ class Decoder:
     """
 
     def __init__(self, H=None, *, M=None, N=None, csr=None, packed=None, mode="fp32",
-                 paper_slicer=False):
+                 paper_slicer=False, debug=False):
         lib = load()
         m = {"fp32": LDPC_MODE_FP32, "fixed": LDPC_MODE_FIXED}[mode]
-        flags = LDPC_FLAG_PAPER_SLICER if paper_slicer else 0
+        flags = (LDPC_FLAG_PAPER_SLICER if paper_slicer else 0) | (LDPC_FLAG_DEBUG if debug else 0)
         keep = []
         if H is not None:
             Hn = np.ascontiguousarray(H, dtype=np.uint8)
@@ -395,6 +399,20 @@ class Decoder:
         """Wait for the handle's stream and raise LdpcError(LDPC_ERR_TIMEOUT) if a bounded
         wait inside a kernel ran out since the last check."""
         _check(load().ldpc_check_device(self.h), "ldpc_check_device")
+
+    def set_debug(self, on: bool):
+        """Device-side debug checks before every decode (index arrays in range, no NaN LLR);
+        a decode they refuse raises LdpcError(LDPC_ERR_DEVICE_CHECK)."""
+        _check(load().ldpc_set_debug(self.h, int(bool(on))), "ldpc_set_debug")
+
+    def debug_report(self):
+        """(what, where) of the last refused decode's first violation, then cleared: what 0
+        none, 1 a NaN LLR (where = frame * N + bit), 2 an index array (where = id << 40 |
+        entry)."""
+        what, where = ctypes.c_int32(), ctypes.c_int64()
+        _check(load().ldpc_debug_report(self.h, ctypes.byref(what), ctypes.byref(where)),
+               "ldpc_debug_report")
+        return what.value, where.value
 
     def set_wait_limit(self, tries: int):
         """Tries of each bounded wait in the staged kernels (0: give up at once)."""

@@ -46,7 +46,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_strerror_and_status_codes(lib):
     from paper_2507_10424_gb300 import ldpc
-    for code in (0, -1, -2, -3, -4, -5, -8):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
         assert ldpc.ldpc_strerror(code) != "unknown status"
     assert ldpc.ldpc_strerror(12345) == "unknown status"
 
