@@ -640,11 +640,25 @@ __device__ __forceinline__ void col_any(const Idx& ix, VecR<typename RT<MODE>::T
     }
 }
 
-// Packed fixed point: 32-bit sums, saturated and packed at the end, then the packed
-// saturating differences.
-__device__ __forceinline__ uint32_t p_lam(uint32_t sw, uint32_t ew) {
-    return p_pack_sat(p_lo(sw) - p_lo(ew), p_hi(sw) - p_hi(ew));
-}
+// Packed fixed point: 32-bit sums, saturated and packed at the end, then lambda =
+// sat(s - eta) lane by lane without leaving the packed form. With s, eta in [-32767, 32767],
+// clamping eta to [max(s, 0) - 32767, min(s, 0) + 32767] (both bounds representable) makes
+// s - eta' equal to sat(s - eta) exactly: eta is raised only when s >= 0 and
+// s - eta > 32767, lowered only when s <= 0 and s - eta < -32767, and otherwise the
+// difference is already within the limits. s - eta' = (s + 1) + ~eta' is formed with
+// wrapping adds, exact because the result is in range. Per column: the bounds and s + 1;
+// per edge: max, min, not, add.
+struct PackedLam {
+    uint32_t lo = 0, hi = 0, s1 = 0;
+    __device__ __forceinline__ void set(uint32_t sw) {
+        lo = p_add(p_max(sw, 0u), 0x80018001u);  // max(s, 0) - 32767
+        hi = p_add(p_min(sw, 0u), 0x7fff7fffu);  // min(s, 0) + 32767
+        s1 = p_add(sw, 0x00010001u);
+    }
+    __device__ __forceinline__ uint32_t operator()(uint32_t ew) const {
+        return p_add(s1, ~p_min(p_max(ew, lo), hi));
+    }
+};
 
 template <int FT, int DC>
 __device__ __forceinline__ void col_fixed_packed(const Idx& ix, Words<FT / 2>* slots, Words<FT / 2>* s,
@@ -673,11 +687,14 @@ __device__ __forceinline__ void col_fixed_packed(const Idx& ix, Words<FT / 2>* s
 #pragma unroll
     for (int p = 0; p < P; p++) out.w[p] = p_pack_sat(lo[p], hi[p]);
     s[p0] = out;
+    PackedLam lam[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) lam[p].set(out.w[p]);
 #pragma unroll
     for (int t = 0; t < DC; t++) {
         WT lv;
 #pragma unroll
-        for (int p = 0; p < P; p++) lv.w[p] = p_lam(out.w[p], ev[t].w[p]);
+        for (int p = 0; p < P; p++) lv.w[p] = lam[p](ev[t].w[p]);
         slots[sl[t]] = lv;
     }
 }
@@ -705,12 +722,15 @@ __device__ __forceinline__ void col_any_packed(const Idx& ix, Words<FT / 2>* slo
 #pragma unroll
     for (int p = 0; p < P; p++) out.w[p] = p_pack_sat(lo[p], hi[p]);
     s[p0] = out;
+    PackedLam lam[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) lam[p].set(out.w[p]);
     for (int t = 0; t < d; t++) {
         const int slot = ix.c_slot[base + 32 * t];
         const WT ev = slots[slot];
         WT lv;
 #pragma unroll
-        for (int p = 0; p < P; p++) lv.w[p] = p_lam(out.w[p], ev.w[p]);
+        for (int p = 0; p < P; p++) lv.w[p] = lam[p](ev.w[p]);
         slots[slot] = lv;
     }
 }
