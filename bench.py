@@ -51,6 +51,9 @@ def parse():
                     help="launch shape instead of the autotuner: resident 'FT,threads[,index "
                          "placement]'; streaming 'warps per CTA,stages[,frames per lane]'")
     ap.add_argument("--quick", action="store_true", help="skip the extra measurements")
+    ap.add_argument("--part", choices=sorted(PARTS), default=None,
+                    help="run one of the extra measurements alone and print its record (for "
+                         "profiling it); no headline step")
     ap.add_argument("--workload", choices=["qc2304", "irregular64800"], default="qc2304",
                     help="qc2304: the headline batch; irregular64800: the large irregular code "
                          "(all-zero codeword at Eb/N0 1.0 dB, decoded by the streaming kernels)")
@@ -486,6 +489,12 @@ def mixed_codes(timed):
             "identical_bits": same}
 
 
+# the extra measurements that --part runs alone (name -> function)
+PARTS = {"mixed_codes": "mixed_codes", "learned": "learned_vs_plain",
+         "learned_large": "learned_vs_plain_large", "other_workloads": "other_workloads",
+         "paper_shaped": "paper_shaped"}
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args):
@@ -549,6 +558,21 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.part:  # one extra measurement alone, timed like the others
+        def part_timed(fn, K, W, sampler=None, st=None):
+            st = st or torch.cuda.current_stream()
+            for _ in range(W):
+                fn()
+            torch.cuda.synchronize()
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(st)
+            for _ in range(K):
+                fn()
+            p1.record(st)
+            torch.cuda.synchronize()
+            return p0.elapsed_time(p1) / K
+        print(json.dumps({"part": args.part, args.part: globals()[PARTS[args.part]](part_timed)}))
+        return 0
     if world > 1:
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
