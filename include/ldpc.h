@@ -267,8 +267,9 @@ int ldpc_batch_replay(ldpc_batch_t *b);
  * ldpc_batch_autotune: times the decode prepared for max_iter / early_stop on the buffers
  * set with ldpc_batch_set_io, for every cap on the frames per tile x CTA size, keeps the
  * fastest pair and leaves the batch prepared with it; best_threads and best_ms
- * (nullable) receive the CTA size and the time of one decode. With early stop a tile runs
- * until its last frame stops, so narrower tiles can win. */
+ * (nullable) receive the CTA size and the time of one decode; on an error the cap and CTA
+ * size the batch had stay in force (prepare it again before launching). With early stop a
+ * tile runs until its last frame stops, so narrower tiles can win. */
 int ldpc_batch_set_threads(ldpc_batch_t *b, int32_t threads);
 int ldpc_batch_set_tile_frames(ldpc_batch_t *b, int32_t max_frames_per_tile);
 int ldpc_batch_get_tile_frames(const ldpc_batch_t *b, int32_t *max_frames_per_tile);

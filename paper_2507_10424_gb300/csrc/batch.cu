@@ -527,7 +527,8 @@ int ldpc_batch_autotune(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop, i
         return LDPC_ERR_CUDA;
     }
     float best = -1.0f;
-    int best_t = b->threads, best_cap = b->ft_cap;
+    const int keep_t = b->threads, keep_cap = b->ft_cap;
+    int best_t = keep_t, best_cap = keep_cap;
     int rc = LDPC_OK;
     // frames per tile at most x CTA size: with early stop a tile runs until its last frame
     // stops, so narrower tiles can win although they share less of each index read
@@ -555,8 +556,11 @@ int ldpc_batch_autotune(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop, i
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc != LDPC_OK) return rc;
-    if (best < 0.0f) return LDPC_ERR_UNSUPPORTED;
+    if (rc != LDPC_OK || best < 0.0f) {  // leave the shape the caller had
+        ldpc_batch_set_tile_frames(b, keep_cap);
+        ldpc_batch_set_threads(b, keep_t);
+        return rc != LDPC_OK ? rc : LDPC_ERR_UNSUPPORTED;
+    }
     rc = ldpc_batch_set_tile_frames(b, best_cap);
     if (rc == LDPC_OK) rc = ldpc_batch_set_threads(b, best_t);
     if (rc == LDPC_OK) rc = ldpc_batch_prepare(b, max_iter, early_stop);
