@@ -134,8 +134,13 @@ int ldpc_decode_ex(ldpc_t *h, const void *llr, int32_t llr_dtype, int32_t frames
 /*
  * ldpc_decode_host: ldpc_decode_ex with HOST buffers (preferably pinned): the LLRs are
  * copied to the device in chunks, decoded and the results copied back, with the copies
- * of one chunk overlapping the decoding of another. Synchronous: returns when the
- * results are in the host buffers. out_ok and out_soft may be NULL.
+ * of one chunk overlapping the decoding of another (two device staging slots, kept by
+ * the handle and grown as needed). Chunks are about a quarter of the frames (at least
+ * 1024, at most 512 MiB of LLRs); with enough frames their sizes ramp up from an eighth
+ * of a chunk, doubling, and back down at the end, since nothing overlaps the first
+ * chunk's input copy or the last chunk's output copy. Synchronous: returns when the
+ * results are in the host buffers. out_ok and out_soft may be NULL. Errors: those of
+ * ldpc_decode_ex, and LDPC_ERR_BAD_POINTER for a null llr_host, bits_host or iters_host.
  */
 int ldpc_decode_host(ldpc_t *h, const void *llr_host, int32_t llr_dtype, int32_t frames,
                      int32_t max_iter, int32_t early_stop, int32_t check_every,
