@@ -4,8 +4,10 @@ Tolerances (from the specification of the two modes):
 * fixed point (int8 LLR, saturating int16 messages): bit-exact -- bits, iterations,
   status and every posterior;
 * FP32: decoded bits, iteration counts and status identical; posteriors within 1e-5
-  relative (the kernels add in the oracle's order, so they are in fact expected to be
-  bit-identical, and the tests also report any inexact element).
+  relative (the contract), and, since every kernel adds in the oracle's order (r_j first,
+  then the column's messages by ascending check) with one binary32 rounding per operation,
+  also bit-identical: ``assert_parity`` checks both, so a change of summation order shows
+  up as a failure even while it stays within the tolerance.
 """
 import numpy as np
 import pytest
@@ -63,6 +65,8 @@ def assert_parity(got, want, mode, label=""):
         assert (gs == ws).all(), f"{label}: fixed-point posteriors differ"
     else:
         np.testing.assert_allclose(gs, ws, rtol=RTOL, atol=0, err_msg=label)
+        inexact = int((gs != ws).sum())
+        assert inexact == 0, f"{label}: {inexact} FP32 posteriors within tolerance but not identical"
 
 
 def tanner_code():
@@ -295,7 +299,7 @@ def test_every_resident_launch_shape(torch_cuda, mode):
     x = torch.from_numpy(llr).cuda()
     tried = 0
     for ft in (1, 2, 4):
-        for th in (0, 96, 256, 640, 1024):
+        for th in (0, 96, 256, 640, 768, 1024):
             for ip in (1, 2):
                 dec = Decoder.from_code(code, mode=mode)
                 dec.set_variant("resident")
@@ -467,7 +471,11 @@ def test_host_buffer_pipeline_matches_device_path(torch_cuda, mode, F):
 @pytest.mark.parametrize("mode", MODES)
 def test_full_size_qc_2304_65536_frames_sampled(torch_cuda, mode):
     """The benchmark's workload at full size (65536 random codewords, 10 iterations without
-    early stop, the launch configuration the benchmark times), checked on sampled frames."""
+    early stop) in the launch configuration the benchmark times: ``autotune(65536, 10)``
+    picks the resident launch shape as the benchmark does, and the decode writes the
+    decisions and iteration counts only (no status, no posteriors), as the timed step
+    does. A second decode with status and posteriors must give the same decisions; sampled
+    frames are compared with the oracle, the status flag with the syndrome on more frames."""
     torch = torch_cuda
     from paper_2507_10424_gb300.ldpc import Decoder
     code = inputs.cfg_qc_2304()
@@ -475,15 +483,20 @@ def test_full_size_qc_2304_65536_frames_sampled(torch_cuda, mode):
     cw = inputs.Encoder(code).random_codewords(F, 123)
     llr = inputs.bpsk_awgn_llr(cw, 2.0, code.design_rate, 124)
     dec = Decoder.from_code(code, mode=mode)
+    dec.autotune(F, 10)
+    shape = dec.tuning()
+    assert dec.variant() == "resident"
     x = torch.from_numpy(llr).cuda()
+    timed_bits, timed_iters, _, _ = dec.decode(x, 10, early_stop=False)
     bits, iters, ok, soft = dec.decode(x, 10, early_stop=False, want_ok=True, want_soft=True)
     torch.cuda.synchronize()
+    assert torch.equal(timed_bits, bits) and torch.equal(timed_iters, iters)
     rng = np.random.default_rng(5)
-    sel = np.sort(np.concatenate([rng.choice(F, 60, replace=False), [0, F - 1]]))
+    sel = np.sort(np.concatenate([rng.choice(F, 60, replace=False), [0, 1, F - 2, F - 1]]))
     want = oracle_decode(code, llr[sel], 10, mode, early_stop=False)
     got = (bits[sel].cpu().numpy(), iters[sel].cpu().numpy(), ok[sel].cpu().numpy(),
            soft[sel].cpu().numpy())
-    assert_parity(got, want, mode, "full-size sample")
+    assert_parity(got, want, mode, f"full-size sample, tuning {shape}")
     assert (iters == 10).all()
     # decoded bits are codewords of H for every frame flagged ok (syndrome property at any size)
     g = oracle.Graph.from_code(code)
@@ -491,6 +504,42 @@ def test_full_size_qc_2304_65536_frames_sampled(torch_cuda, mode):
     bn = bits.cpu().numpy()
     for f in rng.choice(F, 200, replace=False):
         assert okn[f] == (oracle.syndrome(g, bn[f])[0] == 0)
+    dec.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("shape", ["resident 2,768,1", "resident 4,768,1", "resident 1,1024,2",
+                                   "stream", "cluster"])
+def test_posteriors_after_every_iteration(torch_cuda, mode, shape):
+    """Decodes stopped after k = 1 .. 10 iterations (no early stop) return the posteriors
+    s of iteration k; each must equal the oracle's (bit for bit in both modes), so every
+    iteration's messages enter the comparison, not only the last one's. The resident shapes
+    include the benchmark's (2 frames per tile, 768 threads, index arrays in shared memory)."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
+    code = inputs.cfg_qc_2304()
+    F = 45
+    cw = inputs.Encoder(code).random_codewords(F, 77)
+    llr = np.concatenate([inputs.bpsk_awgn_llr(cw[k * 9:(k + 1) * 9], e, code.design_rate, 90 + k)
+                          for k, e in enumerate([1.0, 1.5, 2.0, 2.5, 3.0])])
+    dec = Decoder.from_code(code, mode=mode)
+    if shape.startswith("resident"):
+        dec.set_variant("resident")
+        ft, th, ip = (int(v) for v in shape.split()[1].split(","))
+        try:
+            dec.set_tuning(ft, th, ip)
+        except LdpcError:
+            pytest.skip(f"{shape} does not fit this code in {mode}")
+    else:
+        dec.set_variant(shape)
+    x = torch.from_numpy(llr).cuda()
+    for k in range(1, 11):
+        b, it, ok, sf = dec.decode(x, k, early_stop=False, want_ok=True, want_soft=True)
+        torch.cuda.synchronize()
+        got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
+        assert_parity(got, oracle_decode(code, llr, k, mode, early_stop=False), mode,
+                      f"{shape} after iteration {k}")
+    dec.close()
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -521,4 +570,41 @@ def test_full_size_irregular_64800_4096_frames_sampled(torch_cuda, mode):
     bn = bits.cpu().numpy()
     for f in rng.choice(F, 64, replace=False):
         assert okn[f] == (oracle.syndrome(g, bn[f])[0] == 0)
+    dec.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("which", ["qc2304 (padded rows)", "paper-shaped (rows of 32: CSR slots)"])
+def test_messages_after_the_last_iteration(torch_cuda, mode, which):
+    """The check-to-bit messages eta themselves (eq. eta_update), read back from the
+    streaming workspace after k iterations without early stop, against the oracle's trace
+    of the same frames: bit-exact in fixed point; in FP32 within 1e-5 relative, and
+    identical (the check update only compares and selects)."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300 import ldpc
+    from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
+    code = inputs.cfg_qc_2304() if which.startswith("qc") else inputs.cfg_paper_shaped()
+    F = 21
+    cw = inputs.Encoder(code).random_codewords(F, 44)
+    llr = inputs.bpsk_awgn_llr(cw, 2.0 if which.startswith("qc") else 3.2, code.design_rate, 45)
+    g = oracle.Graph.from_code(code)
+    dec = Decoder.from_code(code, mode=mode)
+    dec.set_variant("stream")
+    x = torch.from_numpy(llr).cuda()
+    for k in (1, 3, 7):
+        dec.decode(x, k, early_stop=False)
+        eta = dec.read_messages(F).cpu().numpy()
+        for f in range(F):
+            if mode == "fp32":
+                want = oracle.trace_f32(g, llr[f], k)[3][k - 1]
+                np.testing.assert_allclose(eta[f], want, rtol=RTOL, atol=0, err_msg=f"k={k} f={f}")
+                assert (eta[f] == want).all(), f"k={k} frame {f}: messages not identical"
+            else:
+                want = oracle.trace_fixed(g, oracle.quantize(llr[f]), k)[3][k - 1]
+                assert (eta[f] * 4 == want).all(), f"k={k} frame {f}"
+    # no messages after an early-stop decode, nor after a resident one
+    dec.decode(x, 3, early_stop=True)
+    with pytest.raises(LdpcError) as e:
+        dec.read_messages(1)
+    assert e.value.status == ldpc.LDPC_ERR_UNSUPPORTED
     dec.close()
