@@ -154,16 +154,21 @@ int ldpc_decode_host(ldpc_t *h, const void *llr_host, int32_t llr_dtype, int32_t
  * must not stall on the allocator (cudaMalloc/cudaFree may synchronise the device), a
  * process whose device memory is already held by another allocator, or an embedding
  * that forbids allocation after start-up. It runs the streaming kernels with their
- * scratch taken from one static device array of LDPC_NOALLOC_SCRATCH_BYTES (32 MiB),
- * which every GPU that loads the library keeps until the process exits.
+ * scratch taken from one static device array of LDPC_NOALLOC_SCRATCH_BYTES (32 MiB).
+ * The array is mapped on a device when the first handle is created there (ldpc_create /
+ * ldpc_create_ex fail with LDPC_ERR_OOM if it cannot be) and stays until the process
+ * exits; this entry point itself maps and allocates nothing. The kernels' code is loaded
+ * by the CUDA runtime on first use (lazy module loading, its default): a caller that can
+ * allocate nothing at all after start-up makes one decode in each mode it uses at
+ * start-up, or runs with CUDA_MODULE_LOADING=EAGER.
  *
- * Arguments and results are those of ldpc_decode_ex (device pointers). The scratch
- * needed is about frames_padded * (E*m + N*(m + r) + max_iter + 7) bytes, with
- * frames_padded = frames rounded up to 256, m = 4 (FP32) or 2 (fixed) and r = 4 or 1;
- * a larger request returns LDPC_ERR_INVALID_ARG without launching anything. The current
- * device must be the handle's device (else LDPC_ERR_INVALID_ARG).
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
+ * Arguments and results are those of ldpc_decode_ex (device pointers). The scratch a
+ * call needs is Fp * (S * m + N * (m + r) + max_iter + 15) + 256 bytes, with Fp = frames
+ * rounded up to a multiple of 256, m = 4 (FP32) or 2 (fixed), r = 4 or 1, and S message
+ * slots per frame: 8 M when no row has more than 8 edges, 16 M when none has more than 16,
+ * else E. A larger request returns LDPC_ERR_INVALID_ARG without launching anything. The
+ * current device must be the handle's device (else LDPC_ERR_INVALID_ARG). The handle's
+ * debug checks (ldpc_set_debug) do not run on this entry point.
  * Every call uses the same array and each clears what must start from zero; calls whose
  * work overlaps on the GPU (other streams, or other handles) race on it and must be
  * serialised by the caller. It does not set ldpc_last_error().
@@ -404,6 +409,22 @@ int ldpc_set_stream_staging(ldpc_t *h, int32_t warps_per_cta, int32_t stages, in
  * automatic). */
 int ldpc_get_stream_staging(const ldpc_t *h, int32_t *warps_per_cta, int32_t *stages,
                             int32_t *frames_per_lane);
+
+/*
+ * ldpc_read_messages: the check-to-bit messages eta_ij of eq. (eta_update) after the last
+ * iteration of the handle's last decode, for tests and diagnosis. They are available when
+ * that decode (ldpc_decode_ex or a function built on it) ran the streaming variant without
+ * early stop and without frame groups, since its messages then remain in the handle's
+ * workspace; the resident, cluster and dense variants keep them on chip and discard them.
+ *   frames  how many frames to read (the first ones of that decode), 0 .. its frame count;
+ *   out     device float [frames][E], frame-major; edge e in CSR order (rows ascending, the
+ *           columns of a row ascending); values in LLR units (fixed mode: eta / 4, exact).
+ * Asynchronous on the handle's stream. Errors: LDPC_ERR_UNSUPPORTED when the last decode
+ * left no messages, LDPC_ERR_INVALID_ARG for frames < 0 or more frames than it decoded,
+ * LDPC_ERR_BAD_POINTER for a null handle or an out that is not device memory. frames = 0 is
+ * a no-op.
+ */
+int ldpc_read_messages(ldpc_t *h, int32_t frames, float *out);
 
 /*
  * ldpc_check_device: waits for the handle's stream, then reads and clears the handle's

@@ -94,6 +94,10 @@ struct ldpc {
     mutable ClusterPlan cl_plan[2];
     mutable int cl_valid[2] = {};
     int32_t last_launches = 0;
+    // frames whose messages the streaming workspace holds after the last decode (a
+    // streaming decode without early stop or frame groups), and that decode's mode; 0 when
+    // the last decode left none (ldpc_read_messages)
+    int32_t msg_frames = 0, msg_mode = kModeFP32;
     // host pipeline staging (2 slots)
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
@@ -306,6 +310,9 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
     if (e != cudaSuccess) return bail(cuda_fail(e));
     e = cudaDeviceGetAttribute(&h->l2_bytes, cudaDevAttrL2CacheSize, h->device);
     if (e != cudaSuccess) return bail(cuda_fail(e));
+    // the static scratch array of ldpc_decode_noalloc is mapped now, so that the entry
+    // point never maps or allocates anything itself
+    if ((rc = noalloc_setup(h->device)) != LDPC_OK) return bail(fail(rc));
     // CSR / CSC
     if ((rc = upload(&h->dg.row_ptr, hg.row_ptr.data(), hg.row_ptr.size())) ||
         (rc = upload(&h->dg.col_idx, hg.col_idx.data(), hg.col_idx.size())) ||
@@ -447,6 +454,7 @@ int ldpc_decode_ex(ldpc_t* h, const void* llr, int32_t llr_dtype, int32_t frames
     if (llr_dtype == LDPC_LLR_I8 && h->mode != kModeFixed) return fail(LDPC_ERR_INVALID_ARG);
     if (h->w_rows > 0 && h->mode != kModeFP32) return fail(LDPC_ERR_UNSUPPORTED);
     h->last_launches = 0;
+    h->msg_frames = 0;
     if (frames == 0) return LDPC_OK;
     if (!is_device_ptr(llr) || !is_device_ptr(out_bits) || !is_device_ptr(out_iters) ||
         (out_ok && !is_device_ptr(out_ok)) || (out_soft && !is_device_ptr(out_soft)))
@@ -536,6 +544,10 @@ int ldpc_decode_ex(ldpc_t* h, const void* llr, int32_t llr_dtype, int32_t frames
             int rc = ensure_stream_work(h, frames, max_iter);
             if (rc != LDPC_OK) return rc;
             n = stream_decode(h->mode, h->dg, a, h->sw, h->stream);
+            if (n >= 0 && !a.early_stop) {  // no compaction: position = frame
+                h->msg_frames = frames;
+                h->msg_mode = h->mode;
+            }
         }
     }
     if (n < 0) {
@@ -953,6 +965,21 @@ int ldpc_get_stream_staging(const ldpc_t* h, int32_t* warps_per_cta, int32_t* st
     if (warps_per_cta) *warps_per_cta = h->st_warps > 0 ? h->st_warps : kStageWarpsDefault;
     if (stages) *stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
     if (frames_per_lane) *frames_per_lane = h->st_vw;
+    return LDPC_OK;
+}
+
+int ldpc_read_messages(ldpc_t* h, int32_t frames, float* out) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (frames < 0) return fail(LDPC_ERR_INVALID_ARG);
+    if (frames == 0) return LDPC_OK;
+    if (h->msg_frames == 0) return fail(LDPC_ERR_UNSUPPORTED);
+    if (frames > h->msg_frames) return fail(LDPC_ERR_INVALID_ARG);
+    if (!is_device_ptr(out)) return fail(LDPC_ERR_BAD_POINTER);
+    const int n = stream_read_messages(h->msg_mode, h->dg, h->M, h->E, h->sw, frames, out, h->stream);
+    if (n < 0) {
+        cudaError_t e = cudaGetLastError();
+        return e != cudaSuccess ? cuda_fail(e) : fail(n);
+    }
     return LDPC_OK;
 }
 

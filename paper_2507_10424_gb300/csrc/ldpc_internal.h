@@ -220,6 +220,11 @@ constexpr int32_t kStageWarpsDefault = 12, kStagesDefault = 2;
 // frame stride w.Fp a multiple of 32 vw)
 int stream_decode(int mode, const DevGraph& dg, const DecodeArgs& a, const StreamWork& w,
                   cudaStream_t st, int vw = 0);
+// The messages eta of the first `frames` frames held in w (a decode without early stop or
+// frame groups: positions are frames) -> out, device float [frames][E] in CSR edge order,
+// in LLR units. Returns the kernels enqueued (1) or a negative status.
+int stream_read_messages(int mode, const DevGraph& g, int32_t M, int64_t E, const StreamWork& w,
+                         int32_t frames, float* out, cudaStream_t st);
 // slots: the graph's eta_slots (message slots per frame).
 size_t stream_bytes(int mode, int32_t N, int64_t slots, int32_t Fp, int32_t L);
 // The workspace of stream_bytes(mode, N, slots, Fp, L) bytes at mem (Fp a multiple of 256).
@@ -277,5 +282,9 @@ struct HandleView {
     uint32_t wait_limit = 0;
 };
 int handle_view(::ldpc_t* h, HandleView* v);
+
+// Maps the static scratch array of ldpc_decode_noalloc on `device` (the current device)
+// and caches its address; handle creation calls it. LDPC_OK or a negative status.
+int noalloc_setup(int device);
 
 }  // namespace ldpc_impl

@@ -10,7 +10,10 @@
 //
 // The array is a file-scope __device__ variable: in host code its name is only a
 // stand-in, so its device address is looked up with cudaGetSymbolAddress once per
-// device, with that device current, on the first call on that device.
+// device, with that device current. The lookup is what maps the array (under CUDA's lazy
+// module loading this translation unit's module, and the array with it, is loaded on its
+// first use), so it runs when a handle is created on the device (noalloc_setup, called
+// by ldpc_create / ldpc_create_ex), never inside ldpc_decode_noalloc itself.
 #include <mutex>
 
 #include "../../include/ldpc.h"
@@ -39,6 +42,22 @@ cudaError_t scratch_address(int device, void** out) {
     *out = g_scratch_addr[device];
     return cudaSuccess;
 }
+
+}  // namespace
+
+// Maps the scratch array on `device` (current) and caches its address: called once per
+// handle creation. Returns LDPC_OK, LDPC_ERR_OOM when the array cannot be mapped for lack
+// of memory, or LDPC_ERR_CUDA; the runtime's pending error is cleared on failure.
+int ldpc_impl::noalloc_setup(int device) {
+    if (device < 0 || device >= kMaxDevices) return LDPC_OK;  // the entry point refuses these
+    void* p = nullptr;
+    const cudaError_t e = scratch_address(device, &p);
+    if (e == cudaSuccess) return LDPC_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? LDPC_ERR_OOM : LDPC_ERR_CUDA;
+}
+
+namespace {
 
 int is_device(const void* p) {
     if (!p) return 0;
@@ -87,8 +106,11 @@ extern "C" int ldpc_decode_noalloc(ldpc_t* h, const void* llr, int32_t llr_dtype
     const size_t need = o_count + 256;
     if (need > kScratchBytes) return LDPC_ERR_INVALID_ARG;  // request larger than the array
     char* base = nullptr;
-    cudaError_t e = scratch_address(device, (void**)&base);
-    if (e != cudaSuccess) return LDPC_ERR_CUDA;
+    {  // set at handle creation on this device (noalloc_setup); no lookup happens here
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        base = (char*)g_scratch_addr[device];
+    }
+    if (!base) return LDPC_ERR_UNSUPPORTED;
     StreamWork w;
     w.Fp = Fp;
     w.eta = base + o_eta;
@@ -130,7 +152,10 @@ extern "C" int ldpc_decode_noalloc(ldpc_t* h, const void* llr, int32_t llr_dtype
     }
     // the kernels clear the done counter and the syndrome flags and set the frame state
     const int n = stream_decode(v.mode, *v.dg, a, w, v.stream);
-    if (n < 0) return n;
+    if (n < 0) {  // a failed launch leaves its error pending: clear it and report it
+        const cudaError_t e = cudaGetLastError();
+        return e != cudaSuccess ? LDPC_ERR_CUDA : n;
+    }
     *v.last_launches = n;
     return LDPC_OK;
 }

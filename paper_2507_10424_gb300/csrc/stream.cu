@@ -1,6 +1,8 @@
 // Streaming variant, host side: workspace size and layout, and the decode entry that
 // dispatches to the FP32 and fixed-point instantiations (stream_fp32.cu, stream_fixed.cu)
 // of the kernels in stream_kernels.cuh.
+#include <algorithm>
+
 #include "../../include/ldpc.h"
 #include "ldpc_internal.h"
 
@@ -40,6 +42,46 @@ StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t slots, int32_t F
     w.err = w.n_done + 1;
     w.comp = w.n_done + 4;
     return w;
+}
+
+// Messages of a streaming workspace, frame-major in CSR edge order: out[f E + e] = the
+// message of edge e (slot: e, or i D + t on the padded row layout, for the t-th edge of row
+// i) of frame f, times `scale` (1 in FP32, 1/4 in fixed point: exact). The row of an edge
+// is found by binary search over the row offsets (a diagnostic path, not a hot one).
+template <typename T>
+__global__ void k_read_messages(const T* __restrict__ eta, int32_t Fp, const int32_t* __restrict__ row_ptr,
+                                int32_t M, int32_t D, int32_t frames, int64_t E, float scale,
+                                float* __restrict__ out) {
+    const int64_t total = (int64_t)frames * E;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t f = (int32_t)(k / E);
+        const int32_t e = (int32_t)(k - (int64_t)f * E);
+        int64_t slot = e;
+        if (D > 0) {
+            int32_t lo = 0, hi = M;  // the last row whose offset is <= e
+            while (hi - lo > 1) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (row_ptr[mid] <= e) lo = mid;
+                else hi = mid;
+            }
+            slot = (int64_t)lo * D + (e - row_ptr[lo]);
+        }
+        out[k] = (float)eta[slot * Fp + f] * scale;
+    }
+}
+
+int stream_read_messages(int mode, const DevGraph& g, int32_t M, int64_t E, const StreamWork& w,
+                         int32_t frames, float* out, cudaStream_t st) {
+    const int64_t total = (int64_t)frames * E;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 65535);
+    if (mode == kModeFP32)
+        k_read_messages<float><<<grid, 256, 0, st>>>((const float*)w.eta, w.Fp, g.row_ptr, M, g.ell_D,
+                                                     frames, E, 1.0f, out);
+    else
+        k_read_messages<int16_t><<<grid, 256, 0, st>>>((const int16_t*)w.eta, w.Fp, g.row_ptr, M,
+                                                       g.ell_D, frames, E, 0.25f, out);
+    return cudaGetLastError() == cudaSuccess ? 1 : LDPC_ERR_CUDA;
 }
 
 int stream_decode(int mode, const DevGraph& g, const DecodeArgs& a, const StreamWork& w,

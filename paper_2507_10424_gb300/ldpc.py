@@ -72,6 +72,7 @@ SIGNATURES = {
     "ldpc_set_stream_group": (ctypes.c_int, [P, I32]),
     "ldpc_set_stream_staging": (ctypes.c_int, [P, I32, I32, I32]),
     "ldpc_get_stream_staging": (ctypes.c_int, [P, PI32, PI32, PI32]),
+    "ldpc_read_messages": (ctypes.c_int, [P, I32, P]),
     "ldpc_check_device": (ctypes.c_int, [P]),
     "ldpc_set_wait_limit": (ctypes.c_int, [P, I32]),
     "ldpc_set_debug": (ctypes.c_int, [P, I32]),
@@ -189,6 +190,10 @@ def ldpc_get_stream_staging(h):
     _check(load().ldpc_get_stream_staging(h, ctypes.byref(w), ctypes.byref(s), ctypes.byref(v)),
            "ldpc_get_stream_staging")
     return w.value, s.value, v.value
+
+
+def ldpc_read_messages(h, frames, out_ptr):
+    return load().ldpc_read_messages(h, frames, out_ptr)
 
 
 def ldpc_check_device(h):
@@ -394,6 +399,16 @@ class Decoder:
         """(warps per CTA, stages, frames per lane) in force; stages 0 when the staged kernel
         is off, frames per lane 0 when automatic."""
         return ldpc_get_stream_staging(self.h)
+
+    def read_messages(self, frames: int):
+        """Messages eta after the last iteration of the last decode (streaming variant, no
+        early stop): a CUDA float32 tensor [frames][E], edges in CSR order, LLR units."""
+        import torch
+        E = self.info()["E"]
+        out = torch.empty((frames, E), dtype=torch.float32, device="cuda")
+        _check(load().ldpc_read_messages(self.h, frames, ctypes.c_void_p(out.data_ptr())),
+               "ldpc_read_messages")
+        return out
 
     def check_device(self):
         """Wait for the handle's stream and raise LdpcError(LDPC_ERR_TIMEOUT) if a bounded
