@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -200,6 +201,40 @@ def ncu_traffic(kernel, mode, F):
     if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return e["dram_bytes_per_launch"] * F / e["frames"]
+
+
+def ncu_counters(kernel, mode):
+    """Per-unit counters of `kernel` from the committed ncu summary (unit: one edge of one
+    frame in one iteration): warp instructions issued, ALU-pipe warp instructions and
+    shared-memory wavefronts; None when the kernel sources changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    e = t.get(f"{kernel}:{mode}")
+    if not e or e.get("source_hash") != kernel_source_hash(kernel) or "warp_inst_per_unit" not in e:
+        return None
+    return e
+
+
+def onchip_roofline(c, units, ms, sm_mhz, n_sms):
+    """Fractions of the on-chip limits a frame-resident kernel runs into, from per-unit ncu
+    counts scaled to this step's units and the step time measured here: instruction issue
+    (one warp instruction per clock per scheduler, 4 schedulers per SM), the ALU pipe (16
+    lanes per scheduler: a warp instruction every 2 clocks) and the shared-memory pipe (one
+    128-byte wavefront per clock per SM), at the SM clock sampled during the step."""
+    cycles = sm_mhz * 1e6 * ms * 1e-3
+    issue = c["warp_inst_per_unit"] * units / (4 * n_sms * cycles)
+    alu = 2 * c["alu_inst_per_unit"] * units / (4 * n_sms * cycles)
+    smem = c["smem_wavefronts_per_unit"] * units / (n_sms * cycles)
+    fr = {"issue": issue, "alu_pipe": alu, "shared_memory_pipe": smem}
+    bound = max(fr, key=fr.get)
+    return {"bound": bound, "frac": fr[bound], "fractions": fr, "sm_mhz": sm_mhz, "sms": n_sms,
+            "per_unit": {k: c[k] for k in ("warp_inst_per_unit", "alu_inst_per_unit",
+                                             "smem_wavefronts_per_unit")},
+            "unit": "one edge of one frame in one iteration",
+            "counters_from": c.get("capture")}
 
 
 def cpu_threads():
@@ -651,6 +686,11 @@ def main():
     achieved = alg_bytes / (ms * 1e-3) / 1e9
     if variant == "resident":  # one launch per step: the step time is the kernel's
         kname, traffic = "k_resident", ncu_traffic("k_resident", mode, F)
+        c = ncu_counters("k_resident", mode)
+        onchip = None
+        if c and clocks and clocks.get("sm_mhz"):
+            onchip = onchip_roofline(c, code.E * F * L, ms, clocks["sm_mhz"],
+                                     torch.cuda.get_device_properties(local).multi_processor_count)
     else:  # about 2 L + 5 launches per step: the figure is the whole decode's
         kname, traffic = "the whole decode (check and variable passes, L iterations)", None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -659,13 +699,28 @@ def main():
                 "algorithmic_bytes_per_frame_iteration": B,
                 # the same against the nominal HBM3e bandwidth the targets are quoted at
                 "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS}
+    if variant == "resident":
+        # the edge messages never leave shared memory, so the HBM fraction above is an
+        # effective rate; this is the fraction of the limit the kernel actually runs into
+        roofline["onchip"] = onchip
 
-    # frame error rate per SNR point (outside the timed region)
+    # error rates per SNR point (outside the timed region): frame and bit error rates of
+    # the decoded bits, beside the channel's own hard decisions (the uncoded rate) and its
+    # closed form Q(sqrt(2 R Eb/N0)); below the code's threshold failed decodes end with
+    # more bit errors than the channel made
     ber_fer = {}
-    wrong = (bits != torch.from_numpy(cw).cuda()).any(dim=1).cpu().numpy()
+    cw_dev = torch.from_numpy(cw).cuda()
+    wrong_bits = bits != cw_dev
+    wrong = wrong_bits.any(dim=1).cpu().numpy()
+    bit_err = wrong_bits.float().mean(dim=1).cpu().numpy()
+    raw_err = ((x < 0) != cw_dev.bool()).float().mean(dim=1).cpu().numpy()
     for k, e in enumerate(snrs):
         a, b = bounds[k], bounds[k + 1]
-        ber_fer[f"{e:.1f}dB"] = float(wrong[a:b].mean())
+        ber_fer[f"{e:.1f}dB"] = {
+            "fer": float(wrong[a:b].mean()), "ber": float(bit_err[a:b].mean()),
+            "channel_ber": float(raw_err[a:b].mean()),
+            "uncoded_ber": 0.5 * math.erfc(math.sqrt(code.design_rate * 10.0 ** (e / 10.0)))}
+    del wrong_bits, cw_dev
 
     result = {
         "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world,
