@@ -37,5 +37,16 @@ __device__ __forceinline__ uint32_t p_pack_sat(int32_t lo, int32_t hi) {
 }
 // Lanes of all ones where bit 0 / bit 16 of b01 is set (b01 has no other bits).
 __device__ __forceinline__ uint32_t p_spread(uint32_t b01) { return b01 * 0xffffu; }
+// Lanes of all ones where the lane is negative, else zero: a byte permute that replicates
+// the sign bit of byte 1 over bytes 0-1 and that of byte 3 over bytes 2-3.
+__device__ __forceinline__ uint32_t p_signmask(uint32_t a) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(d) : "r"(a));
+    return d;
+}
+// a negated in the lanes where mask is all ones (mask lanes 0 or 0xffff): (a ^ -1) + 1.
+__device__ __forceinline__ uint32_t p_cneg(uint32_t a, uint32_t mask) {
+    return p_add(a ^ mask, mask & 0x00010001u);
+}
 
 }  // namespace ldpc_impl

@@ -174,6 +174,28 @@ __device__ __forceinline__ int32_t with_sign(int32_t m, uint32_t sgn) { return (
 __device__ __forceinline__ float lam_sat(float s, float e) { return s - e; }
 __device__ __forceinline__ int32_t lam_sat(int32_t s, int32_t e) { return rsat16(s - e); }
 
+// min(a, b, c) in one three-input instruction (binary32; no NaN reaches it).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+// Observation 1 over two more magnitudes a0, a1: the smallest of the pair may become min0,
+// and the second smallest of {min0, min1, a0, a1} is min(max(min0, lo), min1, hi) for the
+// sorted pair lo <= hi (the second smallest of two sorted pairs).
+__device__ __forceinline__ void two_min_pair(float& min0, float& min1, float a0, float a1) {
+    const float lo = fminf(a0, a1), hi = fmaxf(a0, a1);
+    min1 = fmin3(min1, fmaxf(min0, lo), hi);
+    min0 = fminf(min0, lo);
+}
+// Second sweep of a row (FP32, plain Min-Sum), with the row's total sign folded into the
+// two candidate magnitudes once: the message to an edge is p1 where |lambda| = min0, else
+// p0, with lambda's own sign bit XORed in (Observation 2).
+__device__ __forceinline__ float signed_pick(float lam, float min0, float p0, float p1) {
+    const float v = (fabsf(lam) == min0) ? p1 : p0;
+    return __uint_as_float(__float_as_uint(v) ^ (__float_as_uint(lam) & 0x80000000u));
+}
+
 // Task of round k for this thread: rounds alternate direction so that the work of a
 // thread's tasks (sorted by decreasing degree) evens out. Strictly increasing in k.
 __device__ __forceinline__ int snake(int k, int nth) {
@@ -181,15 +203,18 @@ __device__ __forceinline__ int snake(int k, int nth) {
 }
 
 // Largest row / column degree whose fully unrolled body keeps its operands in registers:
-// about 24 (rows) or 30 (columns: slot ids too) registers of operands, at FT x sizeof(T)
-// / 4 registers per edge vector.
+// about 32 (FP32 rows), 24 (fixed-point rows: the packed sweeps need more temporaries) or
+// 30 (columns: slot ids too) registers of operands, at FT x sizeof(T) / 4 registers per
+// edge vector. (Within the 64 registers of a 1024-thread CTA, without spills.)
 template <int MODE, int FT>
 __host__ __device__ constexpr int vec_regs() {
     return (FT * (MODE == kModeFP32 ? 4 : 2) + 3) / 4;
 }
 template <int MODE, int FT>
 __host__ __device__ constexpr int row_body_max() {
-    return 24 / vec_regs<MODE, FT>() < 16 ? 24 / vec_regs<MODE, FT>() : 16;
+    return (MODE == kModeFP32 ? 32 : 24) / vec_regs<MODE, FT>() < 16
+               ? (MODE == kModeFP32 ? 32 : 24) / vec_regs<MODE, FT>()
+               : 16;
 }
 template <int MODE, int FT>
 __host__ __device__ constexpr int col_body_max() {
@@ -276,6 +301,19 @@ __device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>:
     for (int t = 0; t < DC; t++) {
         lv[t] = slots[base + 32 * t];
         sy.add(ix, base + 32 * t);
+    }
+    if constexpr (MODE == kModeFP32) {  // the magnitudes two at a time
+#pragma unroll
+        for (int t = 0; t + 1 < DC; t += 2) {
+#pragma unroll
+            for (int f = 0; f < FT; f++) {
+                two_min_pair(min0[f], min1[f], fabsf(lv[t].x[f]), fabsf(lv[t + 1].x[f]));
+                sx[f] ^= bits_of((A)lv[t].x[f]) ^ bits_of((A)lv[t + 1].x[f]);
+            }
+        }
+    }
+#pragma unroll
+    for (int t = MODE == kModeFP32 ? DC - DC % 2 : 0; t < DC; t++) {
 #pragma unroll
         for (int f = 0; f < FT; f++) {
             const A lam = (A)lv[t].x[f];
@@ -284,6 +322,23 @@ __device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>:
             min0[f] = min(min0[f], m);
             sx[f] ^= bits_of(lam);
         }
+    }
+    if constexpr (MODE == kModeFP32 && !W) {
+        float p0[FT], p1[FT];
+#pragma unroll
+        for (int f = 0; f < FT; f++) {
+            p0[f] = with_sign((float)min0[f], sx[f]);
+            p1[f] = with_sign((float)min1[f], sx[f]);
+        }
+#pragma unroll
+        for (int t = 0; t < DC; t++) {
+            VT out;
+#pragma unroll
+            for (int f = 0; f < FT; f++) out.x[f] = (T)signed_pick((float)lv[t].x[f], (float)min0[f], p0[f], p1[f]);
+            slots[base + 32 * t] = out;
+        }
+        sy.row_end();
+        return;
     }
 #pragma unroll
     for (int t = 0; t < DC; t++) {
@@ -309,6 +364,25 @@ __device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>:
     }
     sy.row_end();
 }
+
+// Second sweep of a packed row: the row's sign parity is folded into the two candidate
+// magnitudes once (n0, n1: min0 and min1 negated in the lanes whose parity is odd); per
+// edge, |lambda| = min0 exactly where |lambda| - min0 - 1 is negative (|lambda| >= min0),
+// that lane takes n1, the others n0, and lanes where lambda < 0 are negated (Observation 2).
+struct PackedPick {
+    uint32_t n0 = 0, n1 = 0, m0p1 = 0;  // m0p1 = -(min0 + 1) lane by lane
+    __device__ __forceinline__ void set(uint32_t min0, uint32_t min1, uint32_t sx) {
+        const uint32_t pm = p_signmask(sx);
+        n0 = p_cneg(min0, pm);
+        n1 = p_cneg(min1, pm);
+        m0p1 = p_neg(p_add(min0, 0x00010001u));
+    }
+    __device__ __forceinline__ uint32_t operator()(uint32_t lam) const {
+        const uint32_t sm = p_signmask(lam);
+        const uint32_t eq = p_signmask(p_add(p_cneg(lam, sm), m0p1));
+        return p_cneg((n1 & eq) | (n0 & ~eq), sm);
+    }
+};
 
 template <int FT, int DC, typename SY>
 __device__ __forceinline__ void row_fixed_packed(const Idx& ix, Words<FT / 2>* slots, int base,
@@ -337,21 +411,14 @@ __device__ __forceinline__ void row_fixed_packed(const Idx& ix, Words<FT / 2>* s
             sx[p] ^= lam;
         }
     }
-    uint32_t nmin0[P];
+    PackedPick pk[P];
 #pragma unroll
-    for (int p = 0; p < P; p++) nmin0[p] = p_neg(min0[p]);
+    for (int p = 0; p < P; p++) pk[p].set(min0[p], min1[p], sx[p]);
 #pragma unroll
     for (int t = 0; t < DC; t++) {
         WT out;
 #pragma unroll
-        for (int p = 0; p < P; p++) {
-            const uint32_t lam = lv[t].w[p];
-            const uint32_t a = p_max(lam, p_neg(lam));
-            const uint32_t ne = p_spread(p_min(p_add(a, nmin0[p]), 0x00010001u));
-            const uint32_t m = (min0[p] & ne) | (min1[p] & ~ne);
-            const uint32_t sb = ((lam ^ sx[p]) >> 15) & 0x00010001u;
-            out.w[p] = p_add(m ^ p_spread(sb), sb);
-        }
+        for (int p = 0; p < P; p++) out.w[p] = pk[p](lv[t].w[p]);
         slots[base + 32 * t] = out;
     }
     sy.row_end();
@@ -421,6 +488,25 @@ __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>:
                 min0[f] = min(min0[f], m);
                 sx[f] ^= bits_of(lam);
             }
+        }
+        if constexpr (MODE == kModeFP32 && !W) {
+            float p0[FT], p1[FT];
+#pragma unroll
+            for (int f = 0; f < FT; f++) {
+                p0[f] = with_sign((float)min0[f], sx[f]);
+                p1[f] = with_sign((float)min1[f], sx[f]);
+            }
+#pragma unroll UNR
+            for (int t = 0; t < d; t++) {
+                const int slot = base + 32 * t;
+                const VT lv = slots[slot];
+                VT out;
+#pragma unroll
+                for (int f = 0; f < FT; f++) out.x[f] = (T)signed_pick((float)lv.x[f], (float)min0[f], p0[f], p1[f]);
+                slots[slot] = out;
+            }
+            sy.row_end();
+            continue;
         }
 #pragma unroll UNR
         for (int t = 0; t < d; t++) {
@@ -504,23 +590,16 @@ __device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT
                 sx[p] ^= lam;
             }
         }
-        uint32_t nmin0[P];
+        PackedPick pk[P];
 #pragma unroll
-        for (int p = 0; p < P; p++) nmin0[p] = p_neg(min0[p]);
+        for (int p = 0; p < P; p++) pk[p].set(min0[p], min1[p], sx[p]);
 #pragma unroll UNR
         for (int t = 0; t < d; t++) {
             const int slot = base + 32 * t;
             const WT lv = slots[slot];
             WT out;
 #pragma unroll
-            for (int p = 0; p < P; p++) {
-                const uint32_t lam = lv.w[p];
-                const uint32_t a = p_max(lam, p_neg(lam));
-                const uint32_t ne = p_spread(p_min(p_add(a, nmin0[p]), 0x00010001u));
-                const uint32_t m = (min0[p] & ne) | (min1[p] & ~ne);
-                const uint32_t sb = ((lam ^ sx[p]) >> 15) & 0x00010001u;
-                out.w[p] = p_add(m ^ p_spread(sb), sb);
-            }
+            for (int p = 0; p < P; p++) out.w[p] = pk[p](lv.w[p]);
             slots[slot] = out;
         }
         sy.row_end();
