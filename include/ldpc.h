@@ -196,8 +196,10 @@ int ldpc_classes(const ldpc_t *h, int32_t *n_classes, int32_t *degrees);
 int ldpc_set_weights(ldpc_t *h, int32_t n_rows, const float *alpha, const float *beta);
 
 /* ldpc_train_workspace_size: device bytes that ldpc_train_forward/backward need for
- * `frames` frames and `iters` unrolled iterations (about frames x (16 N + 8 E + iters x
- * (E + 12 M)) bytes). */
+ * `frames` frames and `iters` unrolled iterations: about frames x (12 N + 8 E + iters x 12 M)
+ * bytes when no row of H has more than 16 edges (each check keeps min0, min1 and one word
+ * holding its minimum locations, sign parity and sign bits per iteration), plus frames x
+ * iters x E bytes (a sign byte per edge) for codes with longer rows. */
 int ldpc_train_workspace_size(ldpc_t *h, int32_t frames, int32_t iters, uint64_t *bytes);
 
 /* ldpc_train_forward: `iters` flooding iterations (no early stop) of the learned decoder
@@ -404,6 +406,21 @@ int ldpc_set_stream_group(ldpc_t *h, int32_t frames_per_group);
  * falls back to the unstaged kernel. LDPC_ERR_INVALID_ARG for other values.
  */
 int ldpc_set_stream_staging(ldpc_t *h, int32_t warps_per_cta, int32_t stages, int32_t frames_per_lane);
+
+/*
+ * ldpc_set_stream_messages: how the streaming variant keeps the check-to-bit messages of
+ * FP32 codes whose rows have at most 16 edges. compressed = 1 (default): per row and frame
+ * only the two smallest magnitudes min0 <= min1 of Observation 1, the first location of
+ * min0 and the signs of Observation 2 (12 bytes per row; every message eta_ij of eq.
+ * (eta_update) is rebuilt from them exactly), so the per-edge messages never travel
+ * through DRAM; it needs the staged check pass (ldpc_set_stream_staging with stages >= 2).
+ * compressed = 0: one stored message per edge slot. Results do not depend on the choice.
+ * Fixed-point mode and rows longer than 16 edges always keep per-edge messages.
+ * ldpc_autotune also chooses this for FP32 codes. LDPC_ERR_INVALID_ARG for other values.
+ * ldpc_get_stream_messages: 1 when the next streaming decode keeps compressed messages.
+ */
+int ldpc_set_stream_messages(ldpc_t *h, int32_t compressed);
+int ldpc_get_stream_messages(const ldpc_t *h, int32_t *compressed);
 
 /* ldpc_get_stream_staging: the staging in force (stages 0 when off; frames_per_lane 0 when
  * automatic). */

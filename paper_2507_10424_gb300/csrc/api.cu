@@ -98,6 +98,8 @@ struct ldpc {
     // streaming decode without early stop or frame groups), and that decode's mode; 0 when
     // the last decode left none (ldpc_read_messages)
     int32_t msg_frames = 0, msg_mode = kModeFP32;
+    int32_t msg_cmp = 0, msg_L = 0;  // that decode kept compressed messages; its iterations
+    int32_t st_msg = 1;              // ldpc_set_stream_messages
     // host pipeline staging (2 slots)
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
@@ -142,6 +144,7 @@ static void apply_staging(const ldpc_t* h, StreamWork& w) {
     w.stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
     w.stage_vw = h->st_vw;
     w.wait_limit = h->wait_limit;
+    w.msg_compressed = h->st_msg;
 }
 
 static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L, int32_t granule = 256) {
@@ -388,6 +391,7 @@ int ldpc_impl::handle_view(ldpc_t* h, HandleView* v) {
     v->stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
     v->stage_vw = h->st_vw;
     v->wait_limit = h->wait_limit;
+    v->msg_compressed = h->st_msg;
     return LDPC_OK;
 }
 
@@ -543,10 +547,15 @@ int ldpc_decode_ex(ldpc_t* h, const void* llr, int32_t llr_dtype, int32_t frames
         } else {
             int rc = ensure_stream_work(h, frames, max_iter);
             if (rc != LDPC_OK) return rc;
-            n = stream_decode(h->mode, h->dg, a, h->sw, h->stream);
+            int32_t used_cmp = 0;
+            StreamWork w = h->sw;
+            w.used_compressed = &used_cmp;
+            n = stream_decode(h->mode, h->dg, a, w, h->stream);
             if (n >= 0 && !a.early_stop) {  // no compaction: position = frame
                 h->msg_frames = frames;
                 h->msg_mode = h->mode;
+                h->msg_cmp = used_cmp;
+                h->msg_L = max_iter;
             }
         }
     }
@@ -747,14 +756,23 @@ static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* b
     const int32_t keep[3] = {h->st_warps, h->st_stages, h->st_vw};
     // (warps, stages, frames per lane): full and half-width lanes (half-width stages let rows
     // of 16 slots fit more warps), and the unstaged kernel
+    // (shapes whose shared memory does not fit run the unstaged kernel and lose)
     static const int32_t shapes[][3] = {{8, 3, 0}, {12, 2, 0}, {6, 3, 0}, {4, 4, 0}, {8, 2, 0},
-                                        {12, 2, 2}, {8, 3, 2}, {0, -1, 0}};
+                                        {12, 3, 0}, {8, 4, 0}, {12, 2, 2}, {8, 3, 2}, {0, -1, 0}};
+    constexpr int n_shapes = (int)(sizeof(shapes) / sizeof(shapes[0]));
+    // FP32 on the padded layout: every staged shape with compressed and with per-edge
+    // messages (the unstaged kernel keeps per-edge messages)
+    const int n_fmt = h->mode == kModeFP32 ? 2 : 1;
+    const int32_t keep_msg = h->st_msg;
     float best = -1.0f;
     int bi = -1;
-    for (int k = 0; k < (int)(sizeof(shapes) / sizeof(shapes[0])); k++) {
-        h->st_warps = shapes[k][0];
-        h->st_stages = shapes[k][1];
-        h->st_vw = shapes[k][2] ? (h->mode == kModeFP32 ? 2 : 4) : 0;
+    for (int k = 0; k < n_shapes * n_fmt; k++) {
+        const int sh = k % n_shapes;
+        if (k >= n_shapes && shapes[sh][1] < 0) continue;
+        h->st_msg = n_fmt == 2 ? (k < n_shapes ? 1 : 0) : keep_msg;
+        h->st_warps = shapes[sh][0];
+        h->st_stages = shapes[sh][1];
+        h->st_vw = shapes[sh][2] ? (h->mode == kModeFP32 ? 2 : 4) : 0;
         float ms = 0.0f;
         auto run = [&]() {
             return ldpc_decode_ex(h, x, LDPC_LLR_F32, F, max_iter, td.early_stop, td.check_every,
@@ -779,11 +797,14 @@ static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* b
         h->st_warps = keep[0];
         h->st_stages = keep[1];
         h->st_vw = keep[2];
+        h->st_msg = keep_msg;
+        apply_staging(h, h->sw);
         return fail(LDPC_ERR_UNSUPPORTED);
     }
-    h->st_warps = shapes[bi][0];
-    h->st_stages = shapes[bi][1];
-    h->st_vw = shapes[bi][2] ? (h->mode == kModeFP32 ? 2 : 4) : 0;
+    h->st_msg = n_fmt == 2 ? (bi < n_shapes ? 1 : 0) : keep_msg;
+    h->st_warps = shapes[bi % n_shapes][0];
+    h->st_stages = shapes[bi % n_shapes][1];
+    h->st_vw = shapes[bi % n_shapes][2] ? (h->mode == kModeFP32 ? 2 : 4) : 0;
     apply_staging(h, h->sw);
     if (best_ms) *best_ms = best / 2.0f;
     return LDPC_OK;
@@ -959,6 +980,33 @@ int ldpc_set_stream_staging(ldpc_t* h, int32_t warps_per_cta, int32_t stages, in
     return LDPC_OK;
 }
 
+int ldpc_set_stream_messages(ldpc_t* h, int32_t compressed) {
+    if (!h) return fail(LDPC_ERR_BAD_POINTER);
+    if (compressed != 0 && compressed != 1) return fail(LDPC_ERR_INVALID_ARG);
+    h->st_msg = compressed;
+    apply_staging(h, h->sw);
+    return LDPC_OK;
+}
+
+int ldpc_get_stream_messages(const ldpc_t* h, int32_t* compressed) {
+    if (!h || !compressed) return fail(LDPC_ERR_BAD_POINTER);
+    *compressed = 0;
+    if (!h->st_msg || h->mode != kModeFP32 || h->dg.ell_D == 0 || h->st_stages < 0) return LDPC_OK;
+    if (h->w_rows > 0 && h->dg.n_classes > 256) return LDPC_OK;
+    // the staged kernel must fit (else the decode keeps per-edge messages)
+    StreamWork w;
+    apply_staging(h, w);
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
+        cudaGetLastError();
+        return LDPC_OK;
+    }
+    const size_t need = staged_smem_bytes(kModeFP32, w.stage_vw ? w.stage_vw : 4, h->dg.ell_D, true,
+                                          w.stage_warps, w.stages, h->w_rows > 0);
+    *compressed = need <= (size_t)optin ? 1 : 0;
+    return LDPC_OK;
+}
+
 int ldpc_get_stream_staging(const ldpc_t* h, int32_t* warps_per_cta, int32_t* stages,
                             int32_t* frames_per_lane) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
@@ -975,7 +1023,14 @@ int ldpc_read_messages(ldpc_t* h, int32_t frames, float* out) {
     if (h->msg_frames == 0) return fail(LDPC_ERR_UNSUPPORTED);
     if (frames > h->msg_frames) return fail(LDPC_ERR_INVALID_ARG);
     if (!is_device_ptr(out)) return fail(LDPC_ERR_BAD_POINTER);
-    const int n = stream_read_messages(h->msg_mode, h->dg, h->M, h->E, h->sw, frames, out, h->stream);
+    const float *wa = nullptr, *wb = nullptr;  // weights of the decode's last iteration
+    if (h->msg_cmp && h->w_rows > 0 && h->msg_L > 0) {
+        const int row = std::min(h->msg_L, h->w_rows) - 1;
+        wa = h->w_alpha + (size_t)row * h->dg.n_classes;
+        wb = h->w_alpha + (size_t)h->w_rows * h->dg.n_classes + (size_t)row * h->dg.n_classes;
+    }
+    const int n = stream_read_messages(h->msg_mode, h->dg, h->M, h->E, h->sw, frames, out, h->stream,
+                                       h->msg_cmp, wa, wb);
     if (n < 0) {
         cudaError_t e = cudaGetLastError();
         return e != cudaSuccess ? cuda_fail(e) : fail(n);

@@ -359,6 +359,7 @@ int ldpc_batch_prepare(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
             x.w.stages = v.stages;
             x.w.stage_vw = v.stage_vw;
             x.w.wait_limit = v.wait_limit;
+            x.w.msg_compressed = v.msg_compressed;
             DecodeArgs& a = x.a;
             a = DecodeArgs();
             a.M = v.M;

@@ -211,9 +211,26 @@ struct StreamWork {
     int32_t stage_vw = 0;  // frames per lane of the staged kernel (0: the run's vector width)
     uint32_t wait_limit = 1u << 16;
     int32_t num_sms = 0;
+    // FP32 codes on the padded row layout: keep each row's messages compressed (min0,
+    // min1, location and signs; cmsg.cuh) when the staged check pass runs (1), or keep one
+    // message per edge slot (0); used_compressed (host, nullable) receives the choice made
+    int32_t msg_compressed = 1;
+    int32_t* used_compressed = nullptr;
 };
 // Default staging of the streaming check pass (the shape chosen on GB300).
 constexpr int32_t kStageWarpsDefault = 12, kStagesDefault = 2;
+
+// Shared memory of the staged check pass: per warp, `stages` stages of chunks of 32 vw
+// elements of the mode's message type (2 D chunks with per-edge messages: the gathered s
+// and the old messages; D + 3 with compressed ones: s and the row's three state arrays),
+// per stage a 4-byte word per lane and D weight classes and an 8-byte mbarrier; with
+// learned weights, two 256-entry tables for the CTA.
+inline size_t staged_smem_bytes(int mode, int vw, int D, bool cmp, int warps, int stages, bool weights) {
+    const size_t chunk = (size_t)32 * vw * (mode == kModeFP32 ? 4 : 2);
+    const size_t stage = (size_t)(cmp ? D + 3 : 2 * D) * chunk;
+    const size_t meta = (size_t)32 * 4 + (size_t)D * 4;
+    return (size_t)warps * stages * (stage + meta + 8) + (weights ? (size_t)2 * 256 * 4 : 0);
+}
 
 // Launchers; return the number of kernels enqueued, or a negative status.
 // vw: frames per lane (0: a 16-byte vector, 4 fp32 / 8 int16; else 1, 2, 4 or 8 with the
@@ -223,8 +240,11 @@ int stream_decode(int mode, const DevGraph& dg, const DecodeArgs& a, const Strea
 // The messages eta of the first `frames` frames held in w (a decode without early stop or
 // frame groups: positions are frames) -> out, device float [frames][E] in CSR edge order,
 // in LLR units. Returns the kernels enqueued (1) or a negative status.
+// cmp: w holds compressed messages (cmsg.cuh), rebuilt with the weights w_alpha / w_beta
+// (device, [n_classes]) of the decode's last iteration when the decode was weighted.
 int stream_read_messages(int mode, const DevGraph& g, int32_t M, int64_t E, const StreamWork& w,
-                         int32_t frames, float* out, cudaStream_t st);
+                         int32_t frames, float* out, cudaStream_t st, int cmp = 0,
+                         const float* w_alpha = nullptr, const float* w_beta = nullptr);
 // slots: the graph's eta_slots (message slots per frame).
 size_t stream_bytes(int mode, int32_t N, int64_t slots, int32_t Fp, int32_t L);
 // The workspace of stream_bytes(mode, N, slots, Fp, L) bytes at mem (Fp a multiple of 256).
@@ -280,6 +300,7 @@ struct HandleView {
     int32_t stage_warps = 0, stages = 0;  // staged streaming check pass (stages 0 = off)
     int32_t stage_vw = 0;
     uint32_t wait_limit = 0;
+    int32_t msg_compressed = 1;  // ldpc_set_stream_messages
 };
 int handle_view(::ldpc_t* h, HandleView* v);
 

@@ -129,6 +129,7 @@ extern "C" int ldpc_decode_noalloc(ldpc_t* h, const void* llr, int32_t llr_dtype
     w.stages = v.stages;
     w.stage_vw = v.stage_vw;
     w.wait_limit = v.wait_limit;
+    w.msg_compressed = v.msg_compressed;
     DecodeArgs a;
     a.M = v.M;
     a.N = v.N;

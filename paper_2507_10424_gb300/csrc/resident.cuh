@@ -365,25 +365,6 @@ __device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>:
     sy.row_end();
 }
 
-// Second sweep of a packed row: the row's sign parity is folded into the two candidate
-// magnitudes once (n0, n1: min0 and min1 negated in the lanes whose parity is odd); per
-// edge, |lambda| = min0 exactly where |lambda| - min0 - 1 is negative (|lambda| >= min0),
-// that lane takes n1, the others n0, and lanes where lambda < 0 are negated (Observation 2).
-struct PackedPick {
-    uint32_t n0 = 0, n1 = 0, m0p1 = 0;  // m0p1 = -(min0 + 1) lane by lane
-    __device__ __forceinline__ void set(uint32_t min0, uint32_t min1, uint32_t sx) {
-        const uint32_t pm = p_signmask(sx);
-        n0 = p_cneg(min0, pm);
-        n1 = p_cneg(min1, pm);
-        m0p1 = p_neg(p_add(min0, 0x00010001u));
-    }
-    __device__ __forceinline__ uint32_t operator()(uint32_t lam) const {
-        const uint32_t sm = p_signmask(lam);
-        const uint32_t eq = p_signmask(p_add(p_cneg(lam, sm), m0p1));
-        return p_cneg((n1 & eq) | (n0 & ~eq), sm);
-    }
-};
-
 template <int FT, int DC, typename SY>
 __device__ __forceinline__ void row_fixed_packed(const Idx& ix, Words<FT / 2>* slots, int base,
                                                  SY& sy) {

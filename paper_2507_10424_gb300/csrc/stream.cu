@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "../../include/ldpc.h"
+#include "cmsg.cuh"
 #include "ldpc_internal.h"
 
 namespace ldpc_impl {
@@ -71,11 +72,43 @@ __global__ void k_read_messages(const T* __restrict__ eta, int32_t Fp, const int
     }
 }
 
+// The same from compressed messages (cmsg.cuh): the message of the t-th edge of row i is
+// rebuilt from the row's state, weighted by the class of the edge's bit when w_alpha is set.
+__global__ void k_read_cmessages(CState cs, int32_t Fp, const int32_t* __restrict__ row_ptr,
+                                 const int32_t* __restrict__ col_idx, const uint8_t* __restrict__ col_class,
+                                 int32_t M, int32_t frames, int64_t E, const float* w_alpha,
+                                 const float* w_beta, float* __restrict__ out) {
+    const int64_t total = (int64_t)frames * E;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t f = (int32_t)(k / E);
+        const int32_t e = (int32_t)(k - (int64_t)f * E);
+        int32_t lo = 0, hi = M;
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (row_ptr[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        const int t = e - row_ptr[lo];
+        const size_t o = (size_t)lo * Fp + f;
+        float m = cmsg_mag(cs.m0[o], cs.m1[o], cs.w[o], t);
+        if (w_alpha) {
+            const int c = col_class[col_idx[e]];
+            m = cmsg_weight(m, w_alpha[c], w_beta[c]);
+        }
+        out[k] = cmsg_signed(m, cs.w[o], t);
+    }
+}
+
 int stream_read_messages(int mode, const DevGraph& g, int32_t M, int64_t E, const StreamWork& w,
-                         int32_t frames, float* out, cudaStream_t st) {
+                         int32_t frames, float* out, cudaStream_t st, int cmp, const float* w_alpha,
+                         const float* w_beta) {
     const int64_t total = (int64_t)frames * E;
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 65535);
-    if (mode == kModeFP32)
+    if (cmp)
+        k_read_cmessages<<<grid, 256, 0, st>>>(cstate_at(w.eta, M, w.Fp), w.Fp, g.row_ptr, g.col_idx,
+                                               g.col_class, M, frames, E, w_alpha, w_beta, out);
+    else if (mode == kModeFP32)
         k_read_messages<float><<<grid, 256, 0, st>>>((const float*)w.eta, w.Fp, g.row_ptr, M, g.ell_D,
                                                      frames, E, 1.0f, out);
     else

@@ -17,6 +17,7 @@
 #pragma once
 
 #include "../../include/ldpc.h"
+#include "cmsg.cuh"
 #include "ldpc_internal.h"
 #include "packed16.cuh"
 
@@ -576,24 +577,16 @@ __device__ __forceinline__ uint32_t row_update(Row& row, int d, typename Tr<MODE
 #pragma unroll
             for (int p = 0; p < P; p++) z |= (((zx[p] >> 15) & 1u) | ((zx[p] >> 30) & 2u)) << (2 * p);
         }
-        uint32_t nmin0[P];
+        PackedPick pk[P];
 #pragma unroll
-        for (int p = 0; p < P; p++) nmin0[p] = p_neg(min0[p]);
+        for (int p = 0; p < P; p++) pk[p].set(min0[p], min1[p], sx[p]);
 #pragma unroll
         for (int t = 0; t < D; t++)
             if (t < d) {
                 const VT lv = row.lam(t);
                 VT out;
 #pragma unroll
-                for (int p = 0; p < P; p++) {
-                    const uint32_t l = lv.w[p];
-                    const uint32_t a = p_max(l, p_neg(l));
-                    // lanes where |lambda| != min0 take min0, the others min1
-                    const uint32_t ne = p_spread(p_min(p_add(a, nmin0[p]), 0x00010001u));
-                    const uint32_t m = (min0[p] & ne) | (min1[p] & ~ne);
-                    const uint32_t sb = ((l ^ sx[p]) >> 15) & 0x00010001u;
-                    out.w[p] = p_add(m ^ p_spread(sb), sb);
-                }
+                for (int p = 0; p < P; p++) out.w[p] = pk[p](lv.w[p]);
                 *reinterpret_cast<VT*>(erow + (size_t)t * Fp) = out;
             }
     }
@@ -706,6 +699,86 @@ __global__ void __launch_bounds__(128) k_syn_ell(const int32_t* __restrict__ ell
 // Every wait is bounded: on timeout the kernel records kErrTimeout in *err, waits (again
 // bounded) for its own copies still in flight, and returns.
 // ------------------------------------------------------------------------------------
+// The row update on compressed messages (cmsg.cuh; FP32): the lane's VW frames of a row of
+// d <= D edges, operands in a shared-memory stage (chunk t: s of edge t; chunks D, D + 1,
+// D + 2: the row's old m0, m1, w). The old message of edge t is rebuilt from the old state
+// (weighted with the previous iteration's weights, cls / walpha / wbeta), lambda = s - eta,
+// and the new state (min0, min1, first location of min0, message signs) is written to
+// cs at offset off; returns the syndrome bits of the gathered s when SYN.
+template <bool FIRST, bool SYN, bool PAPER, bool W, int VW, int D>
+__device__ __forceinline__ uint32_t row_update_cmp(const unsigned char* st, int chunk, int lane, int d,
+                                                   const int* cls, const float* walpha,
+                                                   const float* wbeta, const CState& cs, size_t off) {
+    static_assert(D <= 16, "signs and locations of at most 16 edges fit the word");
+    using VF = Vec<float, VW>;
+    using VU = Vec<uint32_t, VW>;
+    auto at = [&](int c) { return st + (size_t)c * chunk + (size_t)lane * sizeof(VF); };
+    VF om0, om1;
+    VU ow;
+    if (!FIRST) {
+        om0 = *reinterpret_cast<const VF*>(at(D));
+        om1 = *reinterpret_cast<const VF*>(at(D + 1));
+        ow = *reinterpret_cast<const VU*>(at(D + 2));
+    }
+    float min0[VW], min1[VW];
+    uint32_t oh[VW], sg[VW], zx[VW];
+#pragma unroll
+    for (int v = 0; v < VW; v++) {
+        min0[v] = big(0.0f);
+        min1[v] = big(0.0f);
+        oh[v] = 0;
+        sg[v] = 0;
+        zx[v] = 0;
+    }
+#pragma unroll
+    for (int t = 0; t < D; t++)
+        if (t < d) {
+            const VF sv = *reinterpret_cast<const VF*>(at(t));
+            float wa = 1.0f, wb = 0.0f;
+            if constexpr (W && !FIRST) {
+                const int c = cls[t];
+                wa = walpha[c];
+                wb = wbeta[c];
+            }
+#pragma unroll
+            for (int v = 0; v < VW; v++) {
+                const float sa = sv.x[v];
+                if (SYN) zx[v] ^= PAPER ? sbits(0.0f - sa) : sbits(sa);
+                float l = sa;
+                if constexpr (!FIRST) {
+                    float m = cmsg_mag(om0.x[v], om1.x[v], ow.x[v], t);
+                    if constexpr (W) m = cmsg_weight(m, wa, wb);
+                    l = sa - cmsg_signed(m, ow.x[v], t);
+                }
+                const float a = fabsf(l);
+                const bool lt = a < min0[v];  // strict: the first location of min0 stays
+                min1[v] = lt ? min0[v] : fminf(min1[v], a);
+                min0[v] = lt ? a : min0[v];
+                oh[v] = lt ? (1u << t) : oh[v];
+                sg[v] |= (sbits(l) >> 31) << t;
+            }
+        }
+    uint32_t z = 0;
+    if (SYN) {
+#pragma unroll
+        for (int v = 0; v < VW; v++) z |= (zx[v] >> 31) << v;
+    }
+    const uint32_t dmask = (1u << d) - 1u;
+    VF n0, n1;
+    VU nw;
+#pragma unroll
+    for (int v = 0; v < VW; v++) {
+        n0.x[v] = min0[v];
+        n1.x[v] = min1[v];
+        // message signs: the row's sign parity XOR each edge's own sign
+        nw.x[v] = oh[v] | ((sg[v] ^ ((__popc(sg[v]) & 1u) ? dmask : 0u)) << 16);
+    }
+    *reinterpret_cast<VF*>(cs.m0 + off) = n0;
+    *reinterpret_cast<VF*>(cs.m1 + off) = n1;
+    *reinterpret_cast<VU*>(cs.w + off) = nw;
+    return z;
+}
+
 constexpr int kErrTimeout = 1;
 constexpr uint32_t kDrainTries = 1u << 16;  // about 1.3 s at most
 
@@ -775,10 +848,12 @@ struct StagedArgs {
 // 32 VW sizeof(T) bytes; then per stage one 32-bit word per lane (degree << 8 | frame
 // mask) and D learned-weight classes; then S mbarriers. With learned weights the CTA's
 // copy of the iteration's alpha and beta tables (256 entries each) follows.
-template <int MODE, int VW, int D>
+template <int MODE, int VW, int D, bool CMP = false>
 struct StagedLayout {
     static constexpr int kChunk = 32 * VW * (int)sizeof(typename Tr<MODE>::T);
-    static constexpr int kStage = 2 * D * kChunk;
+    // per-edge messages: D s chunks and D message chunks; compressed: D s chunks and the
+    // row's three state chunks
+    static constexpr int kStage = (CMP ? D + 3 : 2 * D) * kChunk;
     static constexpr int kMeta = 32 * 4 + D * 4;
     __host__ __device__ static constexpr size_t warp_bytes(int S) {
         return (size_t)S * (kStage + kMeta + 8);
@@ -790,7 +865,11 @@ constexpr int kStagedMaxThreads = 384;
 
 // SYN: test the syndrome of the gathered s (the decision of the previous iteration).
 // SYN_ONLY: the final syndrome pass (with FIRST: s copies only, no message update).
-template <int MODE, bool FIRST, bool SYN, bool W, int VW, int D, bool SYN_ONLY = false>
+// CMP (FP32 only): the messages are compressed (cmsg.cuh): eta points at the row states,
+// each task copies the row's old state (three chunks) instead of its old messages, and
+// writes the new state; the weights given are the previous iteration's (they rebuild the
+// old messages; the new state holds unweighted minima).
+template <int MODE, bool FIRST, bool SYN, bool W, int VW, int D, bool SYN_ONLY = false, bool CMP = false>
 __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const StagedArgs a,
                                                       const typename Tr<MODE>::T* __restrict__ s,
                                                       typename Tr<MODE>::T* __restrict__ eta,
@@ -798,7 +877,7 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
     using T = typename Tr<MODE>::T;
     using VT = typename RowVec<MODE, VW>::VT;
     using VS = Vec<uint8_t, VW>;
-    using LY = StagedLayout<MODE, VW, D>;
+    using LY = StagedLayout<MODE, VW, D, CMP>;
     static_assert(LY::kChunk % 16 == 0, "bulk copies move multiples of 16 bytes");
     extern __shared__ __align__(128) unsigned char smem_st[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -826,7 +905,10 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
     const int first = blockIdx.x * nw + warp, stride = gridDim.x * nw;
     const int di = stride % M, dy = stride / M;
     const int FB = 32 * VW;  // frames per block
-    const uint32_t tx = (FIRST ? 1u : 2u) * (uint32_t)LY::kChunk;
+    static_assert(!CMP || MODE == kModeFP32, "compressed messages are FP32");
+    const uint32_t tx = (FIRST || CMP ? 1u : 2u) * (uint32_t)LY::kChunk;  // per edge
+    const uint32_t tx_row = (CMP && !FIRST) ? 3u * (uint32_t)LY::kChunk : 0u;  // per row
+    const CState cs = CMP ? cstate_at(eta, M, a.Fp) : CState{};
     int ci = first % M, cy = first / M;  // the task being computed
     int ni = ci, ny = cy;                // the next task to issue
     int nx_d = 0, nx_c = 0, nx_cls = 0;  // its row data, loaded one step ahead
@@ -858,16 +940,23 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
         // the generic-proxy reads of this stage (its previous task) precede the copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive_expect_tx(&bar[q], any ? tx * (uint32_t)d : 0u);
+        if (lane == 0) mbar_arrive_expect_tx(&bar[q], any ? tx * (uint32_t)d + tx_row : 0u);
         __syncwarp();
         if (any && lane < d) {
             unsigned char* st = buf + (size_t)q * LY::kStage;
             const size_t fo = (size_t)ny * FB;
             bulk_g2s(st + (size_t)lane * LY::kChunk, s + (size_t)nx_c * a.Fp + fo, LY::kChunk, &bar[q],
                      keep_s);
-            if (!FIRST)
+            if (!FIRST && !CMP)
                 bulk_g2s(st + (size_t)(D + lane) * LY::kChunk, eta + ((size_t)ni * D + lane) * a.Fp + fo,
                          LY::kChunk, &bar[q], drop_eta);
+        }
+        if (CMP && !FIRST && any && lane >= D && lane < D + 3) {  // the row's old state
+            unsigned char* st = buf + (size_t)q * LY::kStage;
+            const int c = lane - D;
+            const float* src = c == 0 ? cs.m0 : c == 1 ? cs.m1 : reinterpret_cast<const float*>(cs.w);
+            bulk_g2s(st + (size_t)lane * LY::kChunk, src + (size_t)ni * a.Fp + (size_t)ny * FB, LY::kChunk,
+                     &bar[q], drop_eta);
         }
         pend |= 1u << q;
         ni += di;
@@ -909,17 +998,30 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
                 }
             zacc |= z & act;
         } else if (act) {
-            const int f0 = cy * FB + lane * VW;
-            SmemRow<VT, D> row{st, LY::kChunk, lane,
-                               reinterpret_cast<const int*>(meta + (size_t)q * LY::kMeta + 128), walpha,
-                               wbeta};
-            T* const erow = eta + (size_t)ci * D * a.Fp + f0;
-            if constexpr (SYN) {
-                const uint32_t z = a.paper ? row_update<MODE, FIRST, true, true, W, VW, D>(row, d, erow, a.Fp, wt)
-                                           : row_update<MODE, FIRST, true, false, W, VW, D>(row, d, erow, a.Fp, wt);
-                zacc |= z & act;
+            if constexpr (CMP) {
+                const int* cls = reinterpret_cast<const int*>(meta + (size_t)q * LY::kMeta + 128);
+                const size_t off = (size_t)ci * a.Fp + (size_t)cy * FB + lane * VW;
+                if constexpr (SYN) {
+                    const uint32_t z =
+                        a.paper ? row_update_cmp<FIRST, true, true, W, VW, D>(st, LY::kChunk, lane, d, cls, walpha, wbeta, cs, off)
+                                : row_update_cmp<FIRST, true, false, W, VW, D>(st, LY::kChunk, lane, d, cls, walpha, wbeta, cs, off);
+                    zacc |= z & act;
+                } else {
+                    row_update_cmp<FIRST, false, false, W, VW, D>(st, LY::kChunk, lane, d, cls, walpha, wbeta, cs, off);
+                }
             } else {
-                row_update<MODE, FIRST, false, false, W, VW, D>(row, d, erow, a.Fp, wt);
+                const int f0 = cy * FB + lane * VW;
+                SmemRow<VT, D> row{st, LY::kChunk, lane,
+                                   reinterpret_cast<const int*>(meta + (size_t)q * LY::kMeta + 128), walpha,
+                                   wbeta};
+                T* const erow = eta + (size_t)ci * D * a.Fp + f0;
+                if constexpr (SYN) {
+                    const uint32_t z = a.paper ? row_update<MODE, FIRST, true, true, W, VW, D>(row, d, erow, a.Fp, wt)
+                                               : row_update<MODE, FIRST, true, false, W, VW, D>(row, d, erow, a.Fp, wt);
+                    zacc |= z & act;
+                } else {
+                    row_update<MODE, FIRST, false, false, W, VW, D>(row, d, erow, a.Fp, wt);
+                }
             }
         }
         __syncwarp();
@@ -941,8 +1043,11 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
 // ------------------------------------------------------------------------------------
 // Variable-node pass. Block = 4 warps = 4 columns; lane = one frame vector.
 // test_prev: the previous decision's syndrome (in unsat) decides whether a frame stops.
+// CMP (FP32): the messages are compressed (cmsg.cuh): col_edge holds padded-row slots
+// i 2^dshift + t, and the message of each edge is rebuilt from row i's state cs, weighted
+// (W) with this iteration's weights of the column's class.
 // ------------------------------------------------------------------------------------
-template <int MODE, int VW = Tr<MODE>::V>
+template <int MODE, int VW = Tr<MODE>::V, bool CMP = false, bool W = false>
 __global__ void __launch_bounds__(128) k_var(const int32_t* __restrict__ col_ptr,
                                              const int32_t* __restrict__ col_edge, int N,
                                              const typename Tr<MODE>::R* __restrict__ r,
@@ -951,7 +1056,8 @@ __global__ void __launch_bounds__(128) k_var(const int32_t* __restrict__ col_ptr
                                              uint8_t* state, int32_t* done_iter,
                                              const int32_t* __restrict__ pos2frame,
                                              const uint8_t* __restrict__ unsat, int test_prev,
-                                             int k, int* n_done, int frames) {
+                                             int k, int* n_done, int frames, CState cs = CState{},
+                                             int dshift = 0, IterWeights wt = IterWeights()) {
     using T = typename Tr<MODE>::T;
     using R = typename Tr<MODE>::R;
     using A = typename Tr<MODE>::A;
@@ -993,11 +1099,39 @@ __global__ void __launch_bounds__(128) k_var(const int32_t* __restrict__ col_ptr
     A acc[V];
 #pragma unroll
     for (int v = 0; v < V; v++) acc[v] = (A)rv.x[v];
-    for (int t = t0; t < t1; t++) {
-        const int e = __ldg(col_edge + t);
-        const VT ev = *reinterpret_cast<const VT*>(eta + (size_t)e * Fp + f0);
+    if constexpr (CMP) {
+        static_assert(MODE == kModeFP32, "compressed messages are FP32");
+        using VF = Vec<float, V>;
+        using VU = Vec<uint32_t, V>;
+        float wa = 1.0f, wb = 0.0f;
+        if constexpr (W) {
+            const int c = __ldg(wt.col_class + j);
+            wa = __ldg(wt.alpha + c);
+            wb = __ldg(wt.beta + c);
+        }
+        const int tmask = (1 << dshift) - 1;
+#pragma unroll 4
+        for (int t = t0; t < t1; t++) {
+            const int slot = __ldg(col_edge + t);
+            const size_t o = (size_t)(slot >> dshift) * Fp + f0;
+            const int tp = slot & tmask;
+            const VF m0 = ld_nc(reinterpret_cast<const VF*>(cs.m0 + o));
+            const VF m1 = ld_nc(reinterpret_cast<const VF*>(cs.m1 + o));
+            const VU w = ld_nc(reinterpret_cast<const VU*>(cs.w + o));
 #pragma unroll
-        for (int v = 0; v < V; v++) acc[v] = acc[v] + (A)ev.x[v];
+            for (int v = 0; v < V; v++) {
+                float m = cmsg_mag(m0.x[v], m1.x[v], w.x[v], tp);
+                if constexpr (W) m = cmsg_weight(m, wa, wb);
+                acc[v] = acc[v] + (A)cmsg_signed(m, w.x[v], tp);
+            }
+        }
+    } else {
+        for (int t = t0; t < t1; t++) {
+            const int e = __ldg(col_edge + t);
+            const VT ev = *reinterpret_cast<const VT*>(eta + (size_t)e * Fp + f0);
+#pragma unroll
+            for (int v = 0; v < V; v++) acc[v] = acc[v] + (A)ev.x[v];
+        }
     }
     T* sp = s + (size_t)j * Fp + f0;
     if (upd == (1u << V) - 1u) {
@@ -1062,19 +1196,21 @@ __global__ void k_finish(const int32_t* done_iter, const int32_t* pos2frame, con
 
 // Launch of the staged check pass; false when the shape does not fit the device or the
 // task count does not fit 32 bits (the caller then runs the unstaged kernel).
-template <int MODE, int V, bool FIRST, bool W, int D, bool SYN_ONLY = false>
+template <int MODE, int V, bool FIRST, bool W, int D, bool SYN_ONLY = false, bool CMP = false>
 bool launch_staged(const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
                    const typename Tr<MODE>::T* s, typename Tr<MODE>::T* eta, uint8_t* un,
                    int test_prev, const IterWeights& wt, cudaStream_t st) {
     if (w.stages <= 0 || w.stage_warps <= 0 || w.num_sms <= 0 || !w.err) return false;
-    using LY = StagedLayout<MODE, V, D>;
+    using LY = StagedLayout<MODE, V, D, CMP>;
     const int threads = 32 * w.stage_warps;
     if (threads > kStagedMaxThreads) return false;
-    const size_t smem = LY::warp_bytes(w.stages) * w.stage_warps + (W ? LY::kWeightBytes : 0);
+    const size_t smem = staged_smem_bytes(MODE, V, D, CMP, w.stage_warps, w.stages, W);
+    static_assert(LY::kStage + LY::kMeta + 8 == (CMP ? D + 3 : 2 * D) * LY::kChunk + 32 * 4 + D * 4 + 8,
+                  "the kernel's layout is the one staged_smem_bytes sizes");
     if (W && a.n_classes > 256) return false;
     auto kern = SYN_ONLY ? k_check_staged<MODE, true, false, false, V, D, true>
-                : test_prev ? k_check_staged<MODE, FIRST, true, W, V, D>
-                            : k_check_staged<MODE, FIRST, false, W, V, D>;
+                : test_prev ? k_check_staged<MODE, FIRST, true, W, V, D, false, CMP>
+                            : k_check_staged<MODE, FIRST, false, W, V, D, false, CMP>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -1110,24 +1246,38 @@ bool launch_staged(const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
 
 // The staged launch with w.stage_vw frames per lane (0: the run's V); any width up to V
 // works on the same frame stride.
-template <int MODE, int V, bool FIRST, bool W, int D>
+template <int MODE, int V, bool FIRST, bool W, int D, bool CMP = false>
 bool staged(const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
             const typename Tr<MODE>::T* s, typename Tr<MODE>::T* eta, uint8_t* un, int test_prev,
             const IterWeights& wt, cudaStream_t st) {
     switch (w.stage_vw) {
-        case 0: return launch_staged<MODE, V, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
-        case 1: return launch_staged<MODE, 1, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
+        case 0: return launch_staged<MODE, V, FIRST, W, D, false, CMP>(g, a, w, s, eta, un, test_prev, wt, st);
+        case 1: return launch_staged<MODE, 1, FIRST, W, D, false, CMP>(g, a, w, s, eta, un, test_prev, wt, st);
         case 2:
-            if constexpr (V >= 2) return launch_staged<MODE, 2, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
+            if constexpr (V >= 2)
+                return launch_staged<MODE, 2, FIRST, W, D, false, CMP>(g, a, w, s, eta, un, test_prev, wt, st);
             break;
         case 4:
-            if constexpr (V >= 4) return launch_staged<MODE, 4, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
+            if constexpr (V >= 4)
+                return launch_staged<MODE, 4, FIRST, W, D, false, CMP>(g, a, w, s, eta, un, test_prev, wt, st);
             break;
         case 8:
-            if constexpr (V >= 8) return launch_staged<MODE, 8, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
+            if constexpr (V >= 8)
+                return launch_staged<MODE, 8, FIRST, W, D, false, CMP>(g, a, w, s, eta, un, test_prev, wt, st);
             break;
     }
-    return launch_staged<MODE, V, FIRST, W, D>(g, a, w, s, eta, un, test_prev, wt, st);
+    return launch_staged<MODE, V, FIRST, W, D, false, CMP>(g, a, w, s, eta, un, test_prev, wt, st);
+}
+
+// One check pass on compressed messages (FP32, padded row layout, staged kernel only);
+// false when the staged kernel cannot run (the caller then keeps per-edge messages; this
+// can only happen on the first iteration, before any state exists).
+template <int V, bool FIRST, bool W>
+bool check_pass_cmp(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, const float* s,
+                    float* state, uint8_t* un, int test_prev, const IterWeights& wt_prev, cudaStream_t st) {
+    if (g.ell_D == 8) return staged<kModeFP32, V, FIRST, W, 8, true>(g, a, w, s, state, un, test_prev, wt_prev, st);
+    if (g.ell_D == 16) return staged<kModeFP32, V, FIRST, W, 16, true>(g, a, w, s, state, un, test_prev, wt_prev, st);
+    return false;
 }
 
 // One check pass of iteration k: with the padded row layout, the staged kernel (when
@@ -1173,7 +1323,7 @@ void check_pass(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, dim
 constexpr int kCompactEvery = 4;  // iterations between compaction checks
 
 template <int MODE>
-int compact(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_t st) {
+int compact(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_t st, bool cmp) {
     using T = typename Tr<MODE>::T;
     using R = typename Tr<MODE>::R;
     const int Fp = w.Fp;
@@ -1182,13 +1332,19 @@ int compact(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStr
     k_cmp_emit<MODE><<<blocks, dim3(32, 8), 0, st>>>(
         (const T*)w.s, Fp, a.N, w.state, w.pos2frame, w.done_iter, w.comp, a.out_bits, a.out_soft,
         a.out_iters, a.out_ok, a.paper_slicer);
-    k_cmp_rows<T><<<blocks, 256, 0, st>>>((T*)w.eta, (long long)g.eta_slots, Fp, w.new_pos, w.comp,
-                                          g.ell_D ? g.ell_deg : nullptr, g.ell_D ? g.ell_D : 1);
+    if (cmp) {  // the rows' compressed messages: m0 and m1 (binary32), then the words
+        const CState cs = cstate_at(w.eta, a.M, Fp);
+        k_cmp_rows<float><<<blocks, 256, 0, st>>>(cs.m0, 2ll * a.M, Fp, w.new_pos, w.comp);
+        k_cmp_rows<uint32_t><<<blocks, 256, 0, st>>>(cs.w, (long long)a.M, Fp, w.new_pos, w.comp);
+    } else {
+        k_cmp_rows<T><<<blocks, 256, 0, st>>>((T*)w.eta, (long long)g.eta_slots, Fp, w.new_pos, w.comp,
+                                              g.ell_D ? g.ell_deg : nullptr, g.ell_D ? g.ell_D : 1);
+    }
     k_cmp_rows<T><<<blocks, 256, 0, st>>>((T*)w.s, (long long)a.N, Fp, w.new_pos, w.comp);
     k_cmp_rows<R><<<blocks, 256, 0, st>>>((R*)w.r, (long long)a.N, Fp, w.new_pos, w.comp);
     k_cmp_rows<int32_t><<<1, 256, 0, st>>>(w.pos2frame, 1, Fp, w.new_pos, w.comp);
     k_cmp_tail<<<1, kCmpThreads, 0, st>>>(w.state, w.pos2frame, w.comp);
-    return 7;
+    return cmp ? 8 : 7;
 }
 
 template <int MODE, int V>
@@ -1212,14 +1368,51 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
     const dim3 gc((a.M + 3) / 4, Fp / (32 * V)), gv((a.N + 3) / 4, Fp / (32 * V));
     // message slot of each edge in column order: padded-row slots or CSR edge ids
     const int32_t* cslot = g.ell_D ? g.ell_cslot : g.col_edge;
-    for (int k = 1; k <= a.L; k++) {
-        const int test_prev = a.early_stop && ((k - 1) % a.check_every == 0);
-        uint8_t* un = w.unsat + (size_t)k * Fp;
+    // compressed messages (cmsg.cuh) where the mode, the layout and the staging allow
+    // (the staged kernel holds at most 256 classes of learned weights)
+    bool cmp = MODE == kModeFP32 && w.msg_compressed && g.ell_D > 0 && w.stages > 0 &&
+               (a.w_rows == 0 || a.n_classes <= 256);
+    const int dshift = g.ell_D == 16 ? 4 : 3;
+    auto weights_of = [&](int k) {  // learned weights of iteration k (none for k < 1)
         IterWeights wt{};
-        if (MODE == kModeFP32 && a.w_rows > 0) {
+        if (MODE == kModeFP32 && a.w_rows > 0 && k >= 1) {
             const int row = (k < a.w_rows ? k : a.w_rows) - 1;
             wt = IterWeights{g.col_class, a.w_alpha + (size_t)row * a.n_classes,
                              a.w_beta + (size_t)row * a.n_classes};
+        }
+        return wt;
+    };
+    for (int k = 1; k <= a.L; k++) {
+        const int test_prev = a.early_stop && ((k - 1) % a.check_every == 0);
+        uint8_t* un = w.unsat + (size_t)k * Fp;
+        const IterWeights wt = weights_of(k);
+        if constexpr (MODE == kModeFP32) {
+            if (cmp) {
+                // the first pass has no old messages to rebuild, so no weights (there are
+                // none for iteration 0); later passes rebuild with the previous iteration's
+                const IterWeights wp = weights_of(k - 1);
+                const bool W = a.w_rows > 0;
+                const bool ok = k == 1 ? check_pass_cmp<V, true, false>(g, a, w, s, (float*)eta, un, test_prev, wp, st)
+                                       : (W ? check_pass_cmp<V, false, true>(g, a, w, s, (float*)eta, un, test_prev, wp, st)
+                                            : check_pass_cmp<V, false, false>(g, a, w, s, (float*)eta, un, test_prev, wp, st));
+                if (ok) {
+                    const CState cs = cstate_at(eta, a.M, Fp);
+                    if (W)
+                        k_var<MODE, V, true, true><<<gv, 128, 0, st>>>(
+                            g.col_ptr, g.ell_cslot, a.N, r, s, eta, Fp, state, w.done_iter, w.pos2frame, un,
+                            test_prev, k, w.n_done, a.frames, cs, dshift, wt);
+                    else
+                        k_var<MODE, V, true, false><<<gv, 128, 0, st>>>(
+                            g.col_ptr, g.ell_cslot, a.N, r, s, eta, Fp, state, w.done_iter, w.pos2frame, un,
+                            test_prev, k, w.n_done, a.frames, cs, dshift, wt);
+                    launches += 2;
+                    if (a.early_stop && k < a.L && k % kCompactEvery == 0 && w.comp)
+                        launches += compact<MODE>(g, a, w, st, true);
+                    continue;
+                }
+                if (k > 1) return LDPC_ERR_CUDA;  // cannot happen: the first launch decided
+                cmp = false;                       // per-edge messages from here on
+            }
         }
         check_pass<MODE, V>(g, a, w, gc, s, eta, un, test_prev, k == 1, wt, st);
         k_var<MODE, V><<<gv, 128, 0, st>>>(g.col_ptr, cslot, a.N, r, s, eta, Fp, state,
@@ -1227,8 +1420,9 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
                                         a.frames);
         launches += 2;
         if (a.early_stop && k < a.L && k % kCompactEvery == 0 && w.comp)
-            launches += compact<MODE>(g, a, w, st);
+            launches += compact<MODE>(g, a, w, st, false);
     }
+    if (w.used_compressed) *w.used_compressed = cmp ? 1 : 0;
     uint8_t* unf = w.unsat + (size_t)(a.L + 1) * Fp;
     if (g.ell_D == 8) {
         if (!launch_staged<MODE, V, true, false, 8, true>(g, a, w, s, eta, unf, 1, IterWeights(), st))

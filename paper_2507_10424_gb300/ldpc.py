@@ -72,6 +72,8 @@ SIGNATURES = {
     "ldpc_set_stream_group": (ctypes.c_int, [P, I32]),
     "ldpc_set_stream_staging": (ctypes.c_int, [P, I32, I32, I32]),
     "ldpc_get_stream_staging": (ctypes.c_int, [P, PI32, PI32, PI32]),
+    "ldpc_set_stream_messages": (ctypes.c_int, [P, I32]),
+    "ldpc_get_stream_messages": (ctypes.c_int, [P, PI32]),
     "ldpc_read_messages": (ctypes.c_int, [P, I32, P]),
     "ldpc_check_device": (ctypes.c_int, [P]),
     "ldpc_set_wait_limit": (ctypes.c_int, [P, I32]),
@@ -194,6 +196,16 @@ def ldpc_get_stream_staging(h):
 
 def ldpc_read_messages(h, frames, out_ptr):
     return load().ldpc_read_messages(h, frames, out_ptr)
+
+
+def ldpc_set_stream_messages(h, compressed):
+    return load().ldpc_set_stream_messages(h, compressed)
+
+
+def ldpc_get_stream_messages(h):
+    c = ctypes.c_int32()
+    _check(load().ldpc_get_stream_messages(h, ctypes.byref(c)), "ldpc_get_stream_messages")
+    return c.value
 
 
 def ldpc_check_device(h):
@@ -394,6 +406,15 @@ class Decoder:
         lane of the staged (bulk-copy) kernel; 0 = automatic, stages -1 = unstaged kernel."""
         _check(load().ldpc_set_stream_staging(self.h, warps_per_cta, stages, frames_per_lane),
                "ldpc_set_stream_staging")
+
+    def set_stream_messages(self, compressed: bool):
+        """Streaming variant, FP32, rows of at most 16 edges: keep each row's messages
+        compressed (two minima, location, signs) or one message per edge slot."""
+        _check(load().ldpc_set_stream_messages(self.h, int(bool(compressed))),
+               "ldpc_set_stream_messages")
+
+    def stream_messages_compressed(self) -> bool:
+        return bool(ldpc_get_stream_messages(self.h))
 
     def stream_staging(self):
         """(warps per CTA, stages, frames per lane) in force; stages 0 when the staged kernel

@@ -574,12 +574,14 @@ def test_full_size_irregular_64800_4096_frames_sampled(torch_cuda, mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("which", ["qc2304 (padded rows)", "paper-shaped (rows of 32: CSR slots)"])
+@pytest.mark.parametrize("which", ["qc2304 (padded rows)", "qc2304 (padded rows, per-edge messages)",
+                                   "paper-shaped (rows of 32: CSR slots)"])
 def test_messages_after_the_last_iteration(torch_cuda, mode, which):
     """The check-to-bit messages eta themselves (eq. eta_update), read back from the
     streaming workspace after k iterations without early stop, against the oracle's trace
     of the same frames: bit-exact in fixed point; in FP32 within 1e-5 relative, and
-    identical (the check update only compares and selects)."""
+    identical (the check update only compares and selects). FP32 codes with short rows keep
+    compressed messages by default (rebuilt for the read-back), or per-edge ones."""
     torch = torch_cuda
     from paper_2507_10424_gb300 import ldpc
     from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
@@ -590,6 +592,9 @@ def test_messages_after_the_last_iteration(torch_cuda, mode, which):
     g = oracle.Graph.from_code(code)
     dec = Decoder.from_code(code, mode=mode)
     dec.set_variant("stream")
+    dec.set_stream_staging(8, 2)  # fits rows of 16 edges with compressed messages
+    dec.set_stream_messages("per-edge" not in which)
+    assert dec.stream_messages_compressed() == (mode == "fp32" and which == "qc2304 (padded rows)")
     x = torch.from_numpy(llr).cuda()
     for k in (1, 3, 7):
         dec.decode(x, k, early_stop=False)
@@ -607,4 +612,54 @@ def test_messages_after_the_last_iteration(torch_cuda, mode, which):
     with pytest.raises(LdpcError) as e:
         dec.read_messages(1)
     assert e.value.status == ldpc.LDPC_ERR_UNSUPPORTED
+    dec.close()
+
+
+@pytest.mark.parametrize("compressed", [True, False])
+@pytest.mark.parametrize("which", ["qc2304", "irregular2000", "learned576"])
+def test_streaming_message_formats(torch_cuda, compressed, which):
+    """FP32 streaming decodes with the rows' messages compressed (two minima, location,
+    signs) or stored per edge slot, with early stop (syndrome every 1 and every 3
+    iterations, frame compaction) and without: identical to the oracle either way; the
+    learned case rebuilds each message with the weights of the iteration that sent it."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder
+    if which == "qc2304":
+        code = inputs.cfg_qc_2304()
+        cw = inputs.Encoder(code).random_codewords(300, 61)
+        llr = inputs.bpsk_awgn_llr(cw, 3.8, code.design_rate, 62)  # frames stop at many iterations
+        L = 20
+    elif which == "irregular2000":
+        code = inputs.irregular_code(2000, 1000, [2, 3, 8], [0.5, 0.375, 0.125], 9)
+        llr = inputs.all_zero_awgn_llr(700, code.N, 1.9, code.design_rate, 63)
+        L = 30
+    else:
+        code = inputs.cfg_regular_576()
+        llr = inputs.all_zero_awgn_llr(500, code.N, 2.0, code.design_rate, 64)
+        L = 15
+    dec = Decoder.from_code(code)
+    dec.set_variant("stream")
+    if which == "qc2304":  # rows of up to 16 edges: 8 warps x 2 stages fit in shared memory
+        dec.set_stream_staging(8, 2)
+    dec.set_stream_messages(compressed)
+    assert dec.stream_messages_compressed() == compressed
+    alpha = beta = None
+    if which == "learned576":
+        alpha = np.linspace(0.7, 0.95, 6, dtype=np.float32)[:, None]
+        beta = np.linspace(0.3, 0.05, 6, dtype=np.float32)[:, None]
+        dec.set_weights(alpha, beta)
+    x = torch.from_numpy(llr).cuda()
+    g = oracle.Graph.from_code(code)
+    for es, ce in ((True, 1), (True, 3), (False, 1)):
+        b, it, ok, sf = dec.decode(x, L, early_stop=es, check_every=ce, want_ok=True, want_soft=True)
+        torch.cuda.synchronize()
+        got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
+        if alpha is None:
+            want = oracle.decode_f32(g, llr, L, es, ce)
+        else:
+            cc, _ = oracle.column_classes(code)
+            want = oracle.decode_weighted_f32(g, llr, L, cc, alpha, beta, early_stop=es, check_every=ce)
+        assert_parity(got, want, "fp32", f"{which} compressed={compressed} es={es} ce={ce}")
+        if es:
+            assert len(np.unique(want[1])) >= 3
     dec.close()
