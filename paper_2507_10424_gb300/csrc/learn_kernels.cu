@@ -19,7 +19,11 @@
 //   (a subgradient through min / argmin): dlambda^t = sign(lambda) * that sum, else 0;
 //   ds^(t-1)_j = sum of dlambda^t over the edges of bit j.
 // Layout: frame-interleaved, element (row/edge/bit x, frame f) at x * Fp + f; a warp
-// covers 32 consecutive frames of one check or bit.
+// covers 32 consecutive frames of one check or bit. The saved state of a check is min0,
+// min1 and one word: for codes whose rows have at most 16 edges the word also holds the
+// row's sign bits (loc | loc2 << 4 | parity << 8 | sign of lambda_k << (16 + k)), so each
+// iteration keeps 12 bytes per check and frame; longer rows keep loc | loc2 << 8 |
+// parity << 16 and one sign byte per edge.
 #include <algorithm>
 
 #include "../../include/ldpc.h"
@@ -32,16 +36,20 @@ using namespace ldpc_impl;
 struct TrainWork {
     int32_t Fp;
     float *r, *s, *eta, *dlam, *ds;
-    uint8_t* sg;     // [T][E][Fp] sign bit of lambda
+    uint8_t* sg;     // [T][E][Fp] sign bit of lambda (rows of more than 16 edges only)
     float* mn0;      // [T][M][Fp]
     float* mn1;      // [T][M][Fp]
-    uint32_t* info;  // [T][M][Fp]: loc | loc2 << 8 | parity << 16
+    uint32_t* info;  // [T][M][Fp]: the check's word (see above)
 };
+
+// Rows of at most 16 edges keep their sign bits in the check's word.
+constexpr int kPackedSignsMaxRow = 16;
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Carve the workspace; returns the bytes needed (and fills w when base != nullptr).
-size_t carve(int32_t M, int32_t N, int64_t E, int32_t F, int32_t T, char* base, TrainWork* w) {
+size_t carve(int32_t M, int32_t N, int64_t E, int32_t F, int32_t T, bool packed, char* base,
+             TrainWork* w) {
     const int32_t Fp = (F + 31) & ~31;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -54,7 +62,7 @@ size_t carve(int32_t M, int32_t N, int64_t E, int32_t F, int32_t T, char* base, 
     char* eta = take((size_t)E * Fp * 4);
     char* dlam = take((size_t)E * Fp * 4);
     char* ds = take((size_t)N * Fp * 4);
-    char* sg = take((size_t)T * E * Fp);
+    char* sg = packed ? nullptr : take((size_t)T * E * Fp);
     char* mn0 = take((size_t)T * M * Fp * 4);
     char* mn1 = take((size_t)T * M * Fp * 4);
     char* info = take((size_t)T * M * Fp * 4);
@@ -117,24 +125,26 @@ struct LwArgs {
 };
 
 // Forward check pass of iteration t with saving; block = 4 checks x 32 frames.
-template <bool FIRST>
+// PK: the row's sign bits go to its word (rows of at most 16 edges).
+template <bool FIRST, bool PK>
 __global__ void __launch_bounds__(128) k_lw_check(LwArgs a, TrainWork w, int t) {
     const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
     const int f = blockIdx.y * 32 + (threadIdx.x & 31);
     if (i >= a.M) return;
     const int Fp = a.Fp;
     const int e0 = __ldg(a.row_ptr + i), d = __ldg(a.row_ptr + i + 1) - e0;
-    uint8_t* sg = w.sg + (size_t)(t - 1) * (size_t)a.E * Fp;
+    uint8_t* sg = PK ? nullptr : w.sg + (size_t)(t - 1) * (size_t)a.E * Fp;
     float min0 = __int_as_float(0x7f800000), min1 = min0;
     int loc = 0, loc2 = 0;
-    uint32_t par = 0;
+    uint32_t par = 0, sgw = 0;
     for (int k = 0; k < d; k++) {
         const int e = e0 + k, c = __ldg(a.col_idx + e);
         const float lam = FIRST ? w.s[(size_t)c * Fp + f] : w.s[(size_t)c * Fp + f] - w.eta[(size_t)e * Fp + f];
         const float m = fabsf(lam);
         const uint32_t neg = lam < 0.0f;
         par ^= neg;
-        sg[(size_t)e * Fp + f] = (uint8_t)neg;
+        if (PK) sgw |= neg << k;
+        else sg[(size_t)e * Fp + f] = (uint8_t)neg;
         if (m < min0) {
             min1 = min0;
             loc2 = loc;
@@ -148,14 +158,16 @@ __global__ void __launch_bounds__(128) k_lw_check(LwArgs a, TrainWork w, int t) 
     const size_t ri = (size_t)(t - 1) * a.M * Fp + (size_t)i * Fp + f;
     w.mn0[ri] = min0;
     w.mn1[ri] = min1;
-    w.info[ri] = (uint32_t)loc | ((uint32_t)loc2 << 8) | (par << 16);
+    w.info[ri] = PK ? (uint32_t)loc | ((uint32_t)loc2 << 4) | (par << 8) | (sgw << 16)
+                    : (uint32_t)loc | ((uint32_t)loc2 << 8) | (par << 16);
     const float* al = a.alpha + (size_t)(t - 1) * a.C;
     const float* be = a.beta + (size_t)(t - 1) * a.C;
     for (int k = 0; k < d; k++) {
         const int e = e0 + k, cls = __ldg(a.col_class + __ldg(a.col_idx + e));
         const float g = __fmaf_rn(__ldg(al + cls), k == loc ? min1 : min0, -__ldg(be + cls));
         const float mag = g > 0.0f ? g : 0.0f;
-        w.eta[(size_t)e * Fp + f] = (par ^ sg[(size_t)e * Fp + f]) ? -mag : mag;
+        const uint32_t neg = PK ? (sgw >> k) & 1u : sg[(size_t)e * Fp + f];
+        w.eta[(size_t)e * Fp + f] = (par ^ neg) ? -mag : mag;
     }
 }
 
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(128) k_lw_var(LwArgs a, TrainWork w) {
 }
 
 // Adjoint of the check pass of iteration t; LAST: t = T (no dlambda^(t+1)).
-template <bool LAST>
+template <bool LAST, bool PK>
 __global__ void __launch_bounds__(128) k_lw_bwd_row(LwArgs a, TrainWork w, int t, int F,
                                                     float* grad_alpha, float* grad_beta) {
     extern __shared__ float gacc[];  // [2][C]
@@ -183,12 +195,15 @@ __global__ void __launch_bounds__(128) k_lw_bwd_row(LwArgs a, TrainWork w, int t
     const int Fp = a.Fp;
     if (i < a.M && f < F) {
         const int e0 = __ldg(a.row_ptr + i), d = __ldg(a.row_ptr + i + 1) - e0;
-        const uint8_t* sg = w.sg + (size_t)(t - 1) * (size_t)a.E * Fp;
+        const uint8_t* sg = PK ? nullptr : w.sg + (size_t)(t - 1) * (size_t)a.E * Fp;
         const size_t ri = (size_t)(t - 1) * a.M * Fp + (size_t)i * Fp + f;
         const float min0 = w.mn0[ri], min1 = w.mn1[ri];
         const uint32_t info = w.info[ri];
-        const int loc = info & 0xff, loc2 = (info >> 8) & 0xff;
-        const uint32_t par = (info >> 16) & 1u;
+        const int loc = PK ? info & 0xf : info & 0xff, loc2 = PK ? (info >> 4) & 0xf : (info >> 8) & 0xff;
+        const uint32_t par = (info >> (PK ? 8 : 16)) & 1u;
+        auto neg_of = [&](int k, int e) -> uint32_t {  // sign bit of lambda of the row's k-th edge
+            return PK ? (info >> (16 + k)) & 1u : sg[(size_t)e * Fp + f];
+        };
         const float* al = a.alpha + (size_t)(t - 1) * a.C;
         const float* be = a.beta + (size_t)(t - 1) * a.C;
         float acc_loc = 0.0f, acc_loc2 = 0.0f;
@@ -201,7 +216,7 @@ __global__ void __launch_bounds__(128) k_lw_bwd_row(LwArgs a, TrainWork w, int t
             const float alpha = __ldg(al + cls);
             const float g = __fmaf_rn(alpha, m, -__ldg(be + cls));
             if (g > 0.0f) {
-                const float dg = (par ^ sg[(size_t)e * Fp + f]) ? -deta : deta;
+                const float dg = (par ^ neg_of(k, e)) ? -deta : deta;
                 atomicAdd(&gacc[cls], dg * m);
                 atomicAdd(&gacc[a.C + cls], -dg);
                 if (k != loc) acc_loc += dg * alpha;
@@ -213,7 +228,7 @@ __global__ void __launch_bounds__(128) k_lw_bwd_row(LwArgs a, TrainWork w, int t
             float v = 0.0f;
             if (k == loc) v = acc_loc;
             else if (k == loc2) v = acc_loc2;
-            if (sg[(size_t)e * Fp + f]) v = -v;  // d|lambda| / dlambda = sign(lambda), sign(0) = +1
+            if (neg_of(k, e)) v = -v;  // d|lambda| / dlambda = sign(lambda), sign(0) = +1
             w.dlam[(size_t)e * Fp + f] = v;
         }
     }
@@ -238,12 +253,14 @@ __global__ void __launch_bounds__(128) k_lw_bwd_col(LwArgs a, TrainWork w, int F
     w.ds[(size_t)j * Fp + f] = acc;
 }
 
+bool packed_signs(const HandleView& v) { return v.dg->max_dc <= kPackedSignsMaxRow; }
+
 int check_common(const HandleView& v, int32_t frames, int32_t iters, const void* alpha,
                  const void* beta, const void* work, uint64_t work_bytes) {
     if (frames <= 0 || iters <= 0 || frames > 65535 * 32) return LDPC_ERR_INVALID_ARG;
     if (!alpha || !beta || !work) return LDPC_ERR_BAD_POINTER;
     if (v.dg->n_classes <= 0 || v.dg->max_dc > 255) return LDPC_ERR_UNSUPPORTED;
-    const size_t need = carve(v.M, v.N, v.E, frames, iters, nullptr, nullptr);
+    const size_t need = carve(v.M, v.N, v.E, frames, iters, packed_signs(v), nullptr, nullptr);
     if (work_bytes < need) return LDPC_ERR_INVALID_ARG;
     return LDPC_OK;
 }
@@ -273,7 +290,7 @@ int ldpc_train_workspace_size(ldpc_t* h, int32_t frames, int32_t iters, uint64_t
     HandleView v;
     if (handle_view(h, &v) != LDPC_OK || !bytes) return LDPC_ERR_BAD_POINTER;
     if (frames <= 0 || iters <= 0) return LDPC_ERR_INVALID_ARG;
-    *bytes = carve(v.M, v.N, v.E, frames, iters, nullptr, nullptr);
+    *bytes = carve(v.M, v.N, v.E, frames, iters, packed_signs(v), nullptr, nullptr);
     return LDPC_OK;
 }
 
@@ -285,7 +302,8 @@ int ldpc_train_forward(ldpc_t* h, const float* llr, int32_t frames, int32_t iter
     int rc = check_common(v, frames, iters, alpha, beta, work, work_bytes);
     if (rc != LDPC_OK) return rc;
     TrainWork w;
-    carve(v.M, v.N, v.E, frames, iters, (char*)work, &w);
+    const bool pk = packed_signs(v);
+    carve(v.M, v.N, v.E, frames, iters, pk, (char*)work, &w);
     const LwArgs a = make_args(v, w.Fp, alpha, beta);
     cudaStream_t st = v.stream;
     k_lw_in<<<dim3((v.N + 31) / 32, w.Fp / 32), dim3(32, 8), 0, st>>>(llr, frames, v.N, w.r, w.s, w.Fp);
@@ -293,8 +311,13 @@ int ldpc_train_forward(ldpc_t* h, const float* llr, int32_t frames, int32_t iter
     const dim3 go((v.N + 31) / 32, (frames + 31) / 32), bo(32, 8);
     int launches = 1;
     for (int t = 1; t <= iters; t++) {
-        if (t == 1) k_lw_check<true><<<gc, 128, 0, st>>>(a, w, t);
-        else k_lw_check<false><<<gc, 128, 0, st>>>(a, w, t);
+        if (pk) {
+            if (t == 1) k_lw_check<true, true><<<gc, 128, 0, st>>>(a, w, t);
+            else k_lw_check<false, true><<<gc, 128, 0, st>>>(a, w, t);
+        } else {
+            if (t == 1) k_lw_check<true, false><<<gc, 128, 0, st>>>(a, w, t);
+            else k_lw_check<false, false><<<gc, 128, 0, st>>>(a, w, t);
+        }
         k_lw_var<<<gv, 128, 0, st>>>(a, w);
         launches += 2;
         if (soft_every || t == iters) {
@@ -316,7 +339,8 @@ int ldpc_train_backward(ldpc_t* h, int32_t frames, int32_t iters, const float* a
     int rc = check_common(v, frames, iters, alpha, beta, work, work_bytes);
     if (rc != LDPC_OK) return rc;
     TrainWork w;
-    carve(v.M, v.N, v.E, frames, iters, (char*)work, &w);
+    const bool pk = packed_signs(v);
+    carve(v.M, v.N, v.E, frames, iters, pk, (char*)work, &w);
     const LwArgs a = make_args(v, w.Fp, alpha, beta);
     cudaStream_t st = v.stream;
     const size_t gbytes = (size_t)iters * a.C * sizeof(float);
@@ -332,8 +356,9 @@ int ldpc_train_backward(ldpc_t* h, int32_t frames, int32_t iters, const float* a
     const size_t sm = 2 * a.C * sizeof(float);
     int launches = 1;
     for (int t = iters; t >= 1; t--) {
-        if (t == iters) k_lw_bwd_row<true><<<gc, 128, sm, st>>>(a, w, t, frames, grad_alpha, grad_beta);
-        else k_lw_bwd_row<false><<<gc, 128, sm, st>>>(a, w, t, frames, grad_alpha, grad_beta);
+        auto row = t == iters ? (pk ? k_lw_bwd_row<true, true> : k_lw_bwd_row<true, false>)
+                              : (pk ? k_lw_bwd_row<false, true> : k_lw_bwd_row<false, false>);
+        row<<<gc, 128, sm, st>>>(a, w, t, frames, grad_alpha, grad_beta);
         launches++;
         if (t > 1) {
             k_lw_bwd_col<<<gv, 128, 0, st>>>(a, w, frames);  // ds^(t-1) through lambda^t

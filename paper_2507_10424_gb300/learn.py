@@ -132,12 +132,27 @@ def train_weights(dec, code, iters=10, steps=300, batch=4096, ebn0=(1.0, 4.0), l
     for step in range(steps):
         llr, bits = src.batch(batch, ebn0)
         soft = WeightedMinSum.apply(dec, llr, alpha, beta, every)
-        target = bits.float().expand_as(soft) if every else bits.float()
-        loss = torch.nn.functional.binary_cross_entropy_with_logits(-soft, target)
+        # binary cross-entropy of the logits z = -s of P(bit = 1): the mean of softplus(z) -
+        # t z, whose gradient w.r.t. s is -(sigmoid(z) - t) / n. Both are formed here one
+        # iteration's posteriors at a time, so that a large batch needs no temporaries the
+        # size of all T x F x N posteriors beyond the gradient itself.
         opt.zero_grad()
-        loss.backward()
+        with torch.no_grad():
+            t = bits.float()
+            n = soft.numel()
+            grad = torch.empty_like(soft)
+            total = 0.0
+            for k in range(soft.shape[0] if every else 1):
+                z = -(soft[k] if every else soft)
+                total += float((torch.nn.functional.softplus(z) - t * z).sum().item())
+                g = grad[k] if every else grad
+                torch.sigmoid(z, out=g)
+                g.sub_(t).mul_(-1.0 / n)
+                del z
+        soft.backward(grad)
+        del grad, soft
         opt.step()
-        losses.append(float(loss.item()))
+        losses.append(total / n)
         if log_every and step % log_every == 0:
             print(f"step {step} loss {losses[-1]:.5f}")
     return alpha.detach().cpu().numpy(), beta.detach().cpu().numpy(), losses

@@ -145,10 +145,22 @@ def test_every_iteration_outputs_and_their_adjoint(torch_cuda):
     np.testing.assert_allclose(tb.grad.cpu().numpy(), rb.grad.numpy(), rtol=1e-3, atol=1e-3)
 
 
-def test_adjoint_matches_autograd_reference(torch_cuda):
+def code_with_a_long_row():
+    """The 40-bit code below plus a check over 20 of its bits: with a row longer than 16
+    edges the training state keeps one sign byte per edge instead of folding the row's
+    sign bits into its word."""
+    base = inputs.irregular_code(40, 20, [2, 3, 4], [0.4, 0.4, 0.2], 21)
+    sets = [list(base.cols[base.rows == i] + 1) for i in range(base.M)]
+    sets.append(list(np.random.default_rng(5).choice(40, 20, replace=False) + 1))
+    return inputs.code_from_index_sets(sets, 40)
+
+
+@pytest.mark.parametrize("long_row", [False, True])
+def test_adjoint_matches_autograd_reference(torch_cuda, long_row):
     torch = torch_cuda
     from paper_2507_10424_gb300.ldpc import Decoder
-    code = inputs.irregular_code(40, 20, [2, 3, 4], [0.4, 0.4, 0.2], 21)
+    code = code_with_a_long_row() if long_row else inputs.irregular_code(40, 20, [2, 3, 4], [0.4, 0.4, 0.2], 21)
+    assert (code.row_weights().max() > 16) == long_row
     cls, degrees = oracle.column_classes(code)
     dec = Decoder.from_code(code)
     T = 5
@@ -220,3 +232,22 @@ def test_a_few_training_steps_lower_the_loss(torch_cuda):
     a, b, losses = train_weights(dec, code, iters=5, steps=40, batch=1024, lr=0.03, seed=3)
     assert a.shape == (5, 1) and np.isfinite(a).all() and np.isfinite(b).all()
     assert np.mean(losses[-5:]) < np.mean(losses[:5])
+
+
+@pytest.mark.parametrize("long_row", [False, True])
+def test_training_workspace_size(torch_cuda, long_row):
+    """Per frame: r, s and the bit-pass gradient (4 N bytes each), messages and their
+    gradient (4 E bytes each), and per iteration 12 M bytes of saved check state; a code
+    with a row longer than 16 edges adds a sign byte per edge and iteration. Each region
+    starts 256-byte aligned, frames are padded to a multiple of 32."""
+    from paper_2507_10424_gb300 import ldpc
+    from paper_2507_10424_gb300.ldpc import Decoder
+    code = code_with_a_long_row() if long_row else inputs.cfg_regular_576()
+    dec = Decoder.from_code(code)
+    F, T = 1000, 10
+    Fp = (F + 31) // 32 * 32
+    al = lambda x: (x + 255) // 256 * 256
+    want = (3 * al(code.N * Fp * 4) + 2 * al(code.E * Fp * 4) + 3 * al(T * code.M * Fp * 4)
+            + (al(T * code.E * Fp) if long_row else 0))
+    assert ldpc.ldpc_train_workspace_size(dec.h, F, T) == want
+    dec.close()
