@@ -385,17 +385,18 @@ def paper_shaped(timed):
 def learned_vs_plain_large(timed):
     """Learned normalised/offset Min-Sum on the irregular N=64800 code, one weight pair per
     column degree (2, 3, 8) and iteration: trained here (20 unrolled iterations, 100 steps of
-    512 all-zero frames at Eb/N0 uniform in [0.8, 1.4] dB; the later iterations reuse the
+    4096 all-zero frames at Eb/N0 uniform in [0.8, 1.4] dB; the later iterations reuse the
     last row), then FER and mean iterations of both decoders (streaming variant, 4096
     frames, early stop) at 1.2 and 1.4 dB for iteration limits 30..50, and decoded Gbit/s of
     both at equal FER at 1.4 dB (plain at 50 iterations, learned at its matching limit)."""
     import torch
     from paper_2507_10424_gb300 import inputs, learn
-    from paper_2507_10424_gb300.ldpc import Decoder
+    from paper_2507_10424_gb300.ldpc import Decoder, ldpc_train_workspace_size
     code = inputs.cfg_irregular_64800()
     dec = Decoder.from_code(code)
+    train_ws = ldpc_train_workspace_size(dec.h, 4096, 20)
     t = time.perf_counter()
-    alpha, beta, losses = learn.train_weights(dec, code, iters=20, steps=100, batch=512,
+    alpha, beta, losses = learn.train_weights(dec, code, iters=20, steps=100, batch=4096,
                                               ebn0=(0.8, 1.4), lr=0.02, seed=1, every=True,
                                               encode=False)
     torch.cuda.synchronize()
@@ -420,7 +421,8 @@ def learned_vs_plain_large(timed):
     cls = dec.classes()
     dec.close()
     return {"code": "irregular N=64800 M=32400, column weights 2/3/8", "classes": cls,
-            "train_steps": 100, "train_s": train_s,
+            "train_steps": 100, "train_batch": 4096, "train_s": train_s,
+            "train_workspace_bytes": train_ws,
             "loss_first_last": [float(np.mean(losses[:5])), float(np.mean(losses[-5:]))],
             "alpha_first_last_iteration": [alpha[0].round(4).tolist(), alpha[-1].round(4).tolist()],
             "beta_first_last_iteration": [beta[0].round(4).tolist(), beta[-1].round(4).tolist()],
@@ -480,11 +482,18 @@ def mixed_codes(timed):
     codes, frames = inputs.cfg_mixed_codes()
     L = 25
     decs = [Decoder.from_code(c) for c in codes]
-    batch = Batch(decs)
     xs = []
     for k, (c, F) in enumerate(zip(codes, frames)):
-        x = torch.from_numpy(inputs.all_zero_awgn_llr(F, c.N, 2.0, c.design_rate, 300 + k)).cuda()
-        xs.append(x)
+        xs.append(torch.from_numpy(inputs.all_zero_awgn_llr(F, c.N, 2.0, c.design_rate, 300 + k)).cuda())
+    # every code tuned on its own frames first: the per-code calls use the tuned shapes, and
+    # the batch's large codes run the streaming kernels with their handle's tuned staging
+    for d, x, F in zip(decs, xs, frames):
+        try:  # resident tile shape, or streaming check-pass staging (rows of at most 16 edges)
+            d.autotune(F, L, llr=x, early_stop=True)
+        except Exception:
+            pass
+    batch = Batch(decs)
+    for k, x in enumerate(xs):
         batch.set_io(k, x)
     threads, _ = batch.autotune(L)
     batch.prepare(L)
@@ -498,10 +507,6 @@ def mixed_codes(timed):
     bits_total = sum(c.N * F for c, F in zip(codes, frames))
     outs = []
     for d, c, F, x in zip(decs, codes, frames, xs):
-        try:  # resident tile shape, or streaming check-pass staging (rows of at most 16 edges)
-            d.autotune(F, L, llr=x, early_stop=True)
-        except Exception:
-            pass
         outs.append((torch.empty((F, c.N), dtype=torch.uint8, device="cuda"),
                      torch.empty(F, dtype=torch.int32, device="cuda"), None, None))
 
