@@ -518,11 +518,13 @@ def mixed_codes(timed):
     same = all(bool((batch._keep[k][1] == outs[k][0]).all()) for k in range(len(codes)))
     info = batch.info()
     cap = batch.tile_frames()
+    split = batch.sm_split()
     batch.close()
     return {"codes": [{"N": c.N, "M": c.M, "E": c.E, "frames": F} for c, F in zip(codes, frames)],
             "max_iter": L, "ebn0_db": 2.0, "frames_total": int(sum(frames)),
             "one_launch_graph": {"ms": ms_graph, "Gbit/s": bits_total / (ms_graph * 1e-3) / 1e9,
                                  "threads": threads, "frames_per_tile_at_most": cap,
+                                 "sm_split": split,
                                  "codes_in_shared_memory": info["codes_in_shared_memory"]},
             "per_code_calls": {"ms": ms_seq, "Gbit/s": bits_total / (ms_seq * 1e-3) / 1e9,
                                "launches": sum(d.last_kernel_count() for d in decs)},

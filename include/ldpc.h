@@ -263,6 +263,17 @@ int ldpc_batch_launch(ldpc_batch_t *b);
  * for other values. */
 int ldpc_batch_set_large_codes(ldpc_batch_t *b, int32_t streaming);
 
+/* ldpc_batch_set_sm_split: with large codes decoded by the streaming kernels beside the
+ * persistent launch, run the persistent kernel on at most `sms` SMs (its CTAs) and size
+ * the streaming kernels' persistent check passes to the other SMs, so that the resident
+ * tiles (bound by shared memory and instruction issue) and the streaming passes (bound by
+ * DRAM bandwidth) run side by side on disjoint SMs instead of taking turns on all of them.
+ * 0 (default): no split. Results do not depend on it. Takes effect at the next
+ * ldpc_batch_prepare; ldpc_batch_autotune tries several splits. LDPC_ERR_INVALID_ARG for
+ * sms < 0 or sms >= the device's SM count. ldpc_batch_get_sm_split reads it back. */
+int ldpc_batch_set_sm_split(ldpc_batch_t *b, int32_t sms);
+int ldpc_batch_get_sm_split(const ldpc_batch_t *b, int32_t *sms);
+
 /* ldpc_batch_decode: ldpc_batch_prepare then ldpc_batch_launch. */
 int ldpc_batch_decode(ldpc_batch_t *b, int32_t max_iter, int32_t early_stop);
 
@@ -278,7 +289,8 @@ int ldpc_batch_replay(ldpc_batch_t *b);
  * takes effect at the next ldpc_batch_prepare. ldpc_batch_get_tile_frames reads it back.
  * ldpc_batch_autotune: times the decode prepared for max_iter / early_stop on the buffers
  * set with ldpc_batch_set_io, for every cap on the frames per tile x CTA size, keeps the
- * fastest pair and leaves the batch prepared with it; best_threads and best_ms
+ * fastest pair, then (with streamed large codes) times SM splits (ldpc_batch_set_sm_split)
+ * and leaves the batch prepared with the fastest; best_threads and best_ms
  * (nullable) receive the CTA size and the time of one decode; on an error the cap and CTA
  * size the batch had stay in force (prepare it again before launching). With early stop a
  * tile runs until its last frame stops, so narrower tiles can win. */

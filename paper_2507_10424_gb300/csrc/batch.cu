@@ -116,6 +116,9 @@ struct ldpc_batch {
     int32_t last_launches = 0, captured_launches = 0;
     // codes too large for shared memory: streaming kernels (1) or the persistent launch (0)
     int large_stream = 1;
+    // SMs of the persistent kernel while streamed codes run beside it (0: all of them);
+    // the streaming kernels' persistent passes then size their grids to the other SMs
+    int32_t sm_split = 0;
     struct Streamed {
         int32_t code;
         DecodeArgs a;
@@ -182,7 +185,9 @@ static int batch_enqueue(ldpc_batch_t* b) {
     }
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), b->stream) != cudaSuccess) return LDPC_ERR_CUDA;
     if (b->n_tiles > 0) {
-        const int grid = std::min(b->grid, b->n_tiles);
+        int grid = std::min(b->grid, b->n_tiles);
+        if (side && b->sm_split > 0)  // leave the other SMs to the streaming kernels
+            grid = std::min(grid, b->sm_split * std::max(1, b->grid / std::max(1, b->num_sms)));
         multi_kernel(b)<<<grid, b->threads, b->smem, b->stream>>>(b->d_desc, b->d_tiles, b->n_tiles,
                                                                   b->d_counter, b->d_scratch,
                                                                   b->slot_bytes);
@@ -354,7 +359,7 @@ int ldpc_batch_prepare(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
             x.code = c;
             x.w = stream_carve(kModeFP32, x.mem, v.N, v.dg->eta_slots, Fp, max_iter);
             x.w.err = v.err;  // the code handle's device error word (ldpc_check_device)
-            x.w.num_sms = v.num_sms;
+            x.w.num_sms = b->sm_split > 0 ? std::max(1, v.num_sms - b->sm_split) : v.num_sms;
             x.w.stage_warps = v.stage_warps;
             x.w.stages = v.stages;
             x.w.stage_vw = v.stage_vw;
@@ -421,6 +426,19 @@ int ldpc_batch_set_large_codes(ldpc_batch_t* b, int32_t streaming) {
     if (streaming != 0 && streaming != 1) return LDPC_ERR_INVALID_ARG;
     b->large_stream = streaming;
     return LDPC_OK;  // takes effect at the next ldpc_batch_prepare
+}
+
+int ldpc_batch_set_sm_split(ldpc_batch_t* b, int32_t sms) {
+    if (!b) return LDPC_ERR_BAD_POINTER;
+    if (sms < 0 || sms >= b->num_sms) return LDPC_ERR_INVALID_ARG;
+    b->sm_split = sms;
+    return LDPC_OK;  // takes effect at the next ldpc_batch_prepare
+}
+
+int ldpc_batch_get_sm_split(const ldpc_batch_t* b, int32_t* sms) {
+    if (!b || !sms) return LDPC_ERR_BAD_POINTER;
+    *sms = b->sm_split;
+    return LDPC_OK;
 }
 
 int ldpc_batch_decode(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
@@ -555,9 +573,38 @@ int ldpc_batch_autotune(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop, i
             }
         }
     }
+    // with codes streamed beside the persistent kernel: the SMs it keeps (the resident
+    // tiles are bound on chip, the streaming passes by DRAM, so disjoint SM sets can run
+    // both near their own limits)
+    const int32_t keep_split = b->sm_split;
+    int32_t best_split = keep_split;
+    if (rc == LDPC_OK && best >= 0.0f && ldpc_batch_set_tile_frames(b, best_cap) == LDPC_OK &&
+        ldpc_batch_set_threads(b, best_t) == LDPC_OK) {
+        for (int q : {0, 8, 6, 5, 4, 3}) {  // 0: no split; else num_sms / q SMs
+            const int32_t split = q ? std::max(1, b->num_sms / q) : 0;
+            b->sm_split = split;
+            if (ldpc_batch_prepare(b, max_iter, early_stop) != LDPC_OK) continue;
+            if (b->streamed.empty() && split) break;  // nothing runs beside the kernel
+            float ms = 0.0f;
+            bool bad = batch_enqueue(b) < 0 || cudaEventRecord(e0, b->stream) != cudaSuccess;
+            for (int r = 0; r < 2 && !bad; r++) bad = batch_enqueue(b) < 0;
+            bad = bad || cudaEventRecord(e1, b->stream) != cudaSuccess ||
+                  cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess;
+            if (bad) {
+                cudaGetLastError();
+                continue;
+            }
+            if (ms < best) {
+                best = ms;
+                best_split = split;
+            }
+        }
+    }
+    b->sm_split = best_split;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != LDPC_OK || best < 0.0f) {  // leave the shape the caller had
+        b->sm_split = keep_split;
         ldpc_batch_set_tile_frames(b, keep_cap);
         ldpc_batch_set_threads(b, keep_t);
         return rc != LDPC_OK ? rc : LDPC_ERR_UNSUPPORTED;

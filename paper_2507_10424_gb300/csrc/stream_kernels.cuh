@@ -721,7 +721,7 @@ __device__ __forceinline__ uint32_t row_update_cmp(const unsigned char* st, int 
         ow = *reinterpret_cast<const VU*>(at(D + 2));
     }
     float min0[VW], min1[VW];
-    uint32_t oh[VW], sg[VW], zx[VW];
+    uint32_t oh[VW], sg[VW], zx[VW];  // sg: lambda's sign bits, the first edge's highest
 #pragma unroll
     for (int v = 0; v < VW; v++) {
         min0[v] = big(0.0f);
@@ -755,7 +755,7 @@ __device__ __forceinline__ uint32_t row_update_cmp(const unsigned char* st, int 
                 min1[v] = lt ? min0[v] : fminf(min1[v], a);
                 min0[v] = lt ? a : min0[v];
                 oh[v] = lt ? (1u << t) : oh[v];
-                sg[v] |= (sbits(l) >> 31) << t;
+                sg[v] = __funnelshift_l(sbits(l), sg[v], 1);  // (sg << 1) | sign of l
             }
         }
     uint32_t z = 0;
@@ -763,15 +763,17 @@ __device__ __forceinline__ uint32_t row_update_cmp(const unsigned char* st, int 
 #pragma unroll
         for (int v = 0; v < VW; v++) z |= (zx[v] >> 31) << v;
     }
-    const uint32_t dmask = (1u << d) - 1u;
+    const uint32_t dmask = (1u << d) - 1u;  // d <= 16
     VF n0, n1;
     VU nw;
 #pragma unroll
     for (int v = 0; v < VW; v++) {
         n0.x[v] = min0[v];
         n1.x[v] = min1[v];
-        // message signs: the row's sign parity XOR each edge's own sign
-        nw.x[v] = oh[v] | ((sg[v] ^ ((__popc(sg[v]) & 1u) ? dmask : 0u)) << 16);
+        // message signs: the row's sign parity XOR each edge's own sign; edge t's sign sits
+        // at bit d - 1 - t of sg, at bit 16 + t of the word (bit reversal, shift)
+        const uint32_t sgt = __brev(sg[v]) >> (16 - d);
+        nw.x[v] = oh[v] | ((sgt ^ ((__popc(sg[v]) & 1u) ? dmask << 16 : 0u)));
     }
     *reinterpret_cast<VF*>(cs.m0 + off) = n0;
     *reinterpret_cast<VF*>(cs.m1 + off) = n1;

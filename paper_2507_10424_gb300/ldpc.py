@@ -65,6 +65,8 @@ SIGNATURES = {
     "ldpc_batch_autotune": (ctypes.c_int, [P, I32, I32, PI32, ctypes.POINTER(ctypes.c_float)]),
     "ldpc_batch_info": (ctypes.c_int, [P, PI32, PI32, PI32, PI32]),
     "ldpc_batch_set_large_codes": (ctypes.c_int, [P, I32]),
+    "ldpc_batch_set_sm_split": (ctypes.c_int, [P, I32]),
+    "ldpc_batch_get_sm_split": (ctypes.c_int, [P, PI32]),
     "ldpc_batch_destroy": (None, [P]),
     "ldpc_set_stream": (ctypes.c_int, [P, P]),
     "ldpc_set_mode": (ctypes.c_int, [P, I32]),
@@ -617,6 +619,16 @@ class Batch:
         """Codes too large for shared memory: streaming kernels (True) or the persistent
         launch from global scratch (False); takes effect at the next prepare."""
         _check(load().ldpc_batch_set_large_codes(self.b, int(streaming)), "ldpc_batch_set_large_codes")
+
+    def set_sm_split(self, sms: int):
+        """Run the persistent kernel on at most `sms` SMs and the streamed large codes on the
+        others (0: no split); takes effect at the next prepare."""
+        _check(load().ldpc_batch_set_sm_split(self.b, sms), "ldpc_batch_set_sm_split")
+
+    def sm_split(self) -> int:
+        v = ctypes.c_int32()
+        _check(load().ldpc_batch_get_sm_split(self.b, ctypes.byref(v)), "ldpc_batch_get_sm_split")
+        return v.value
 
     def capture(self):
         _check(load().ldpc_batch_capture(self.b), "ldpc_batch_capture")

@@ -133,3 +133,39 @@ def test_batch_frames_per_tile_caps_and_both_kernel_forms(torch_cuda, cap):
             if frames[k]:
                 check_code(c, ins[k], outs[k], L, f"cap {cap} early_stop={es} code {k}", es)
     batch.close()
+
+
+@pytest.mark.parametrize("sms", [19, 76])
+def test_batch_sm_split_keeps_results(torch_cuda, sms):
+    """The persistent kernel on a subset of the SMs and the streamed large code's passes on
+    the others, launched directly and from a graph: the same results as the oracle."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300 import ldpc
+    from paper_2507_10424_gb300.ldpc import Batch, Decoder, LdpcError
+    codes, frames = mixed_small()
+    frames = [131, 70, 40, 37]
+    decs = [Decoder.from_code(c) for c in codes]
+    batch = Batch(decs)
+    with pytest.raises(LdpcError):
+        batch.set_sm_split(-1)
+    batch.set_sm_split(sms)
+    assert batch.sm_split() == sms
+    L = 20
+    ins, outs = [], []
+    for k, (c, F) in enumerate(zip(codes, frames)):
+        llr = inputs.all_zero_awgn_llr(F, c.N, 2.2, c.design_rate, 150 + k)
+        x = torch.from_numpy(llr).cuda()
+        ins.append(llr)
+        outs.append(batch.set_io(k, x, want_ok=True, want_soft=True))
+    batch.decode(L)
+    batch.stream.synchronize()
+    for k, c in enumerate(codes):
+        check_code(c, ins[k], outs[k], L, f"split {sms} code {k}")
+    batch.capture()
+    batch.replay()
+    batch.stream.synchronize()
+    for k, c in enumerate(codes):
+        check_code(c, ins[k], outs[k], L, f"split {sms} replay code {k}")
+    threads, ms = batch.autotune(L)
+    assert ms > 0 and 0 <= batch.sm_split() < 152
+    batch.close()
