@@ -337,30 +337,29 @@ __device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>:
             for (int f = 0; f < FT; f++) out.x[f] = (T)signed_pick((float)lv[t].x[f], (float)min0[f], p0[f], p1[f]);
             slots[base + 32 * t] = out;
         }
-        sy.row_end();
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int t = 0; t < DC; t++) {
-        const int slot = base + 32 * t;
-        float wa = 1.0f, wb = 0.0f;
-        if constexpr (W) {
-            const int c = ix.wcls[slot];
-            wa = ix.walpha[c];
-            wb = ix.wbeta[c];
-        }
-        VT out;
-#pragma unroll
-        for (int f = 0; f < FT; f++) {
-            const A lam = (A)lv[t].x[f];
-            A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
-            if constexpr (W) {  // max(fma(alpha, m, -beta), 0)
-                const float x = __fmaf_rn(wa, (float)m, -wb);
-                m = (A)(x > 0.0f ? x : 0.0f);
+        for (int t = 0; t < DC; t++) {
+            const int slot = base + 32 * t;
+            float wa = 1.0f, wb = 0.0f;
+            if constexpr (W) {
+                const int c = ix.wcls[slot];
+                wa = ix.walpha[c];
+                wb = ix.wbeta[c];
             }
-            out.x[f] = (T)with_sign(m, bits_of(lam) ^ sx[f]);
+            VT out;
+#pragma unroll
+            for (int f = 0; f < FT; f++) {
+                const A lam = (A)lv[t].x[f];
+                A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
+                if constexpr (W) {  // max(fma(alpha, m, -beta), 0)
+                    const float x = __fmaf_rn(wa, (float)m, -wb);
+                    m = (A)(x > 0.0f ? x : 0.0f);
+                }
+                out.x[f] = (T)with_sign(m, bits_of(lam) ^ sx[f]);
+            }
+            slots[slot] = out;
         }
-        slots[slot] = out;
     }
     sy.row_end();
 }
@@ -486,31 +485,30 @@ __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>:
                 for (int f = 0; f < FT; f++) out.x[f] = (T)signed_pick((float)lv.x[f], (float)min0[f], p0[f], p1[f]);
                 slots[slot] = out;
             }
-            sy.row_end();
-            continue;
-        }
+        } else {
 #pragma unroll UNR
-        for (int t = 0; t < d; t++) {
-            const int slot = base + 32 * t;
-            const VT lv = slots[slot];
-            float wa = 1.0f, wb = 0.0f;
-            if constexpr (W) {
-                const int c = ix.wcls[slot];
-                wa = ix.walpha[c];
-                wb = ix.wbeta[c];
-            }
-            VT out;
-#pragma unroll
-            for (int f = 0; f < FT; f++) {
-                const A lam = (A)lv.x[f];
-                A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
-                if constexpr (W) {  // max(fma(alpha, m, -beta), 0)
-                    const float x = __fmaf_rn(wa, (float)m, -wb);
-                    m = (A)(x > 0.0f ? x : 0.0f);
+            for (int t = 0; t < d; t++) {
+                const int slot = base + 32 * t;
+                const VT lv = slots[slot];
+                float wa = 1.0f, wb = 0.0f;
+                if constexpr (W) {
+                    const int c = ix.wcls[slot];
+                    wa = ix.walpha[c];
+                    wb = ix.wbeta[c];
                 }
-                out.x[f] = (T)with_sign(m, bits_of(lam) ^ sx[f]);
+                VT out;
+#pragma unroll
+                for (int f = 0; f < FT; f++) {
+                    const A lam = (A)lv.x[f];
+                    A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
+                    if constexpr (W) {  // max(fma(alpha, m, -beta), 0)
+                        const float x = __fmaf_rn(wa, (float)m, -wb);
+                        m = (A)(x > 0.0f ? x : 0.0f);
+                    }
+                    out.x[f] = (T)with_sign(m, bits_of(lam) ^ sx[f]);
+                }
+                slots[slot] = out;
             }
-            slots[slot] = out;
         }
         sy.row_end();
     }
@@ -992,7 +990,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
     }
     const float* walpha0 = ix.walpha;
     const float* wbeta0 = ix.wbeta;
-    const int N = a.N, n_rtasks = a.n_rsl * 32;
+    const int n_rtasks = a.n_rsl * 32;
 
     for (;;) {
         if (threadIdx.x == 0) {

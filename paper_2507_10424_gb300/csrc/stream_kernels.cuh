@@ -500,8 +500,8 @@ __device__ __forceinline__ uint32_t row_update(Row& row, int d, typename Tr<MODE
             zx[v] = 0;
         }
 #pragma unroll
-        for (int t = 0; t < D; t++)
-            if (t < d) {
+        for (int t = 0; t < D; t++) {
+            if (t >= d) break;  // d is the same for the whole warp: a branch, no idle slots
                 const VT sv = row.s(t);
                 VT ev;
                 if (!FIRST) ev = row.e(t);
@@ -524,8 +524,8 @@ __device__ __forceinline__ uint32_t row_update(Row& row, int d, typename Tr<MODE
             for (int v = 0; v < VW; v++) z |= (zx[v] >> 31) << v;
         }
 #pragma unroll
-        for (int t = 0; t < D; t++)
-            if (t < d) {
+        for (int t = 0; t < D; t++) {
+            if (t >= d) break;  // d is the same for the whole warp: a branch, no idle slots
                 float wa = 1.0f, wb = 0.0f;
                 if constexpr (W) row.weights(t, wt, wa, wb);
                 const VT lv = row.lam(t);
@@ -553,8 +553,8 @@ __device__ __forceinline__ uint32_t row_update(Row& row, int d, typename Tr<MODE
             zx[p] = 0;
         }
 #pragma unroll
-        for (int t = 0; t < D; t++)
-            if (t < d) {
+        for (int t = 0; t < D; t++) {
+            if (t >= d) break;  // d is the same for the whole warp: a branch, no idle slots
                 const VT sv = row.s(t);
                 VT ev;
                 if (!FIRST) ev = row.e(t);
@@ -581,8 +581,8 @@ __device__ __forceinline__ uint32_t row_update(Row& row, int d, typename Tr<MODE
 #pragma unroll
         for (int p = 0; p < P; p++) pk[p].set(min0[p], min1[p], sx[p]);
 #pragma unroll
-        for (int t = 0; t < D; t++)
-            if (t < d) {
+        for (int t = 0; t < D; t++) {
+            if (t >= d) break;  // d is the same for the whole warp: a branch, no idle slots
                 const VT lv = row.lam(t);
                 VT out;
 #pragma unroll
@@ -731,8 +731,8 @@ __device__ __forceinline__ uint32_t row_update_cmp(const unsigned char* st, int 
         zx[v] = 0;
     }
 #pragma unroll
-    for (int t = 0; t < D; t++)
-        if (t < d) {
+    for (int t = 0; t < D; t++) {
+        if (t >= d) break;  // d is the same for the whole warp: a branch, no idle slots
             const VF sv = *reinterpret_cast<const VF*>(at(t));
             float wa = 1.0f, wb = 0.0f;
             if constexpr (W && !FIRST) {
