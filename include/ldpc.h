@@ -229,9 +229,9 @@ int ldpc_train_backward(ldpc_t *h, int32_t frames, int32_t iters, const float *a
  * device, all with or all without LDPC_FLAG_PAPER_SLICER, each small enough for the
  * resident variant's sliced layout). Its kernel takes (code, frame) tiles from one work
  * counter, largest codes first; a code whose frame fits in shared memory keeps its
- * messages there. A larger code is by default decoded by the streaming kernels on a
- * second stream forked from (and joined back to) the batch's stream, alongside the
- * persistent kernel; ldpc_batch_set_large_codes(b, 0) puts it in the persistent launch
+ * messages there. A larger code is by default decoded by the streaming kernels on one of
+ * two streams forked from (and joined back to) the batch's stream (the large codes
+ * alternate between them), alongside the persistent kernel; ldpc_batch_set_large_codes(b, 0) puts it in the persistent launch
  * instead, with a per-CTA slot of the batch's global scratch. Either way the launch is
  * one recordable unit. Results equal ldpc_decode_ex with check_every = 1 on each code.
  *

@@ -4,9 +4,9 @@
 // frame) from a single atomic work counter, largest codes first, and run every flooding
 // iteration of the tile with the resident variant's tile body (decode_tile). A code whose
 // frame fits the launch's shared memory keeps eta, s and r there. A code too large for
-// that is, by default, decoded by the streaming kernels on a second stream forked from
+// that is, by default, decoded by the streaming kernels on one of two streams forked from
 // the batch's stream (so they can fill the SMs that the persistent kernel's last tiles
-// leave idle); optionally it joins the persistent launch instead, with eta, s and r in
+// leave idle, and the launch gaps of each other's passes); optionally it joins the persistent launch instead, with eta, s and r in
 // the CTA's own slot of a global scratch buffer. The index arrays of every code are read
 // from global memory. FP32 mode.
 //
@@ -127,8 +127,10 @@ struct ldpc_batch {
         size_t bytes = 0;
     };
     std::vector<Streamed> streamed;
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    // the streamed codes alternate between two side streams (their passes fill each
+    // other's launch gaps and tails)
+    cudaStream_t side = nullptr, side2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
 };
 
 static void batch_free(ldpc_batch_t* b) {
@@ -136,8 +138,10 @@ static void batch_free(ldpc_batch_t* b) {
     for (auto& x : b->streamed)
         if (x.mem) cudaFree(x.mem);
     if (b->side) cudaStreamDestroy(b->side);
+    if (b->side2) cudaStreamDestroy(b->side2);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->join) cudaEventDestroy(b->join);
+    if (b->join2) cudaEventDestroy(b->join2);
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_counter) cudaFree(b->d_counter);
@@ -166,19 +170,22 @@ static int batch_occupancy(ldpc_batch_t* b, int threads, int* grid) {
     return LDPC_OK;
 }
 
-// Enqueue the launch (capturable): the streaming decodes of the large codes on the side
-// stream between a fork and a join event, the work counter reset and the persistent kernel
-// on the batch's stream. Returns the number of kernels enqueued, or a negative status.
+// Enqueue the launch (capturable): the streaming decodes of the large codes on the two
+// side streams between a fork and join events, the work counter reset and the persistent
+// kernel on the batch's stream. Returns the number of kernels enqueued, or a negative status.
 static int batch_enqueue(ldpc_batch_t* b) {
     int launches = 0;
     const bool side = !b->streamed.empty();
+    const bool two = b->streamed.size() > 1;
     if (side) {
         if (cudaEventRecord(b->fork, b->stream) != cudaSuccess ||
-            cudaStreamWaitEvent(b->side, b->fork, 0) != cudaSuccess)
+            cudaStreamWaitEvent(b->side, b->fork, 0) != cudaSuccess ||
+            (two && cudaStreamWaitEvent(b->side2, b->fork, 0) != cudaSuccess))
             return LDPC_ERR_CUDA;
-        for (auto& x : b->streamed) {
+        for (size_t k = 0; k < b->streamed.size(); k++) {
+            const auto& x = b->streamed[k];
             if (x.a.frames == 0) continue;
-            const int n = stream_decode(kModeFP32, *b->views[x.code].dg, x.a, x.w, b->side);
+            const int n = stream_decode(kModeFP32, *b->views[x.code].dg, x.a, x.w, (k & 1) ? b->side2 : b->side);
             if (n < 0) return n;
             launches += n;
         }
@@ -195,6 +202,9 @@ static int batch_enqueue(ldpc_batch_t* b) {
     }
     if (side && (cudaEventRecord(b->join, b->side) != cudaSuccess ||
                  cudaStreamWaitEvent(b->stream, b->join, 0) != cudaSuccess))
+        return LDPC_ERR_CUDA;
+    if (two && (cudaEventRecord(b->join2, b->side2) != cudaSuccess ||
+                cudaStreamWaitEvent(b->stream, b->join2, 0) != cudaSuccess))
         return LDPC_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? launches : LDPC_ERR_CUDA;
 }
@@ -248,8 +258,10 @@ ldpc_batch_t* ldpc_batch_create(int32_t n_codes, ldpc_t* const* codes) {
     }
     b->slot_bytes = (slot + 255) & ~(size_t)255;
     cudaError_t e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join2, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_desc, sizeof(CodeDesc) * n_codes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int32_t));
     if (e == cudaSuccess && batch_occupancy(b, b->threads, &b->grid) != LDPC_OK) e = cudaErrorInvalidConfiguration;
@@ -345,6 +357,7 @@ int ldpc_batch_prepare(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
             if (need > x.bytes) {
                 if (x.mem) {
                     cudaStreamSynchronize(b->side);
+                    cudaStreamSynchronize(b->side2);
                     cudaFree(x.mem);
                 }
                 x.mem = nullptr;
@@ -389,6 +402,7 @@ int ldpc_batch_prepare(ldpc_batch_t* b, int32_t max_iter, int32_t early_stop) {
     for (auto& old : b->streamed)
         if (old.mem) {
             cudaStreamSynchronize(b->side);
+            cudaStreamSynchronize(b->side2);
             cudaFree(old.mem);
         }
     b->streamed = keep;
