@@ -6,7 +6,8 @@ cannot let a decode call cudaMalloc. This entry point takes its scratch from a s
 device array inside the library instead. The test calls it through the C ABI twice in a
 row, on two different batches, and checks each result against ldpc_decode_ex (the
 regular entry point) on the same batch: bits, iteration counts and status identical,
-posteriors within 1e-5 relative (exact in fixed point). The same comparison covers learned
+posteriors within 1e-5 relative (exact in fixed point); the first test also compares
+with the oracle directly. The same comparison covers learned
 weights set on the handle and an irregular code on the padded row layout (more message
 slots than edges). Requests are accepted up to the size the header's formula gives and
 refused beyond it. This file is collected last on purpose.
@@ -16,6 +17,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2507_10424_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -62,6 +64,14 @@ def test_noalloc_matches_regular_entry_point_twice(mode):
         else:
             np.testing.assert_allclose(got[3], want[3], rtol=RTOL, atol=0)
         assert want[1].max() > 1
+        g = oracle.Graph.from_code(code)  # and the oracle itself, directly
+        if mode == "fixed":
+            ob, oi, ook, os_ = oracle.decode_fixed(g, oracle.quantize(llr), 20, es)
+            os_ = os_.astype(np.float32) * 0.25
+        else:
+            ob, oi, ook, os_ = oracle.decode_f32(g, llr, 20, es)
+        assert (got[0] == ob).all() and (got[1] == oi).all() and (got[2] == ook).all()
+        assert (got[3] == os_).all()
     dec.close()
 
 
