@@ -245,36 +245,47 @@ __global__ void __launch_bounds__(kCmpThreads) k_cmp_tail(uint8_t* state, int32_
     }
 }
 
-// llr [frames][N] (frame-major) -> r, s [N][Fp] (frame-interleaved); 32 x 32 tiles.
+// llr [frames][N] (frame-major) -> r, s [N][Fp] (frame-interleaved). A block of 8 warps
+// moves a tile of 32 frames x 128 bits: each warp reads frame rows (four coalesced 128-byte
+// loads per row, sixteen per thread in flight), then writes bit rows of 32 frames; the
+// shared tile is padded so that neither phase has bank conflicts.
+constexpr int kLoadTJ = 128, kLoadTF = 32;
 template <int MODE>
-__global__ void k_load(const void* llr, int llr_i8, int frames, int N, typename Tr<MODE>::R* r,
-                       typename Tr<MODE>::T* s, int Fp) {
+__global__ void __launch_bounds__(256) k_load(const void* llr, int llr_i8, int frames, int N,
+                                              typename Tr<MODE>::R* r, typename Tr<MODE>::T* s, int Fp) {
     using T = typename Tr<MODE>::T;
     using R = typename Tr<MODE>::R;
-    __shared__ float tile[32][33];
-    const int j0 = blockIdx.x * 32, f0 = blockIdx.y * 32;
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        int f = f0 + y, j = j0 + threadIdx.x;
-        float v = 0.0f;
-        if (f < frames && j < N) {
-            size_t idx = (size_t)f * N + j;
-            v = llr_i8 ? (float)((const int8_t*)llr)[idx] : ((const float*)llr)[idx];
+    __shared__ float tile[kLoadTF][kLoadTJ + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j0 = blockIdx.x * kLoadTJ, f0 = blockIdx.y * kLoadTF;
+#pragma unroll
+    for (int y = warp; y < kLoadTF; y += 8) {
+        const int f = f0 + y;
+#pragma unroll
+        for (int q = 0; q < kLoadTJ / 32; q++) {
+            const int j = j0 + q * 32 + lane;
+            float v = 0.0f;
+            if (f < frames && j < N) {
+                const size_t idx = (size_t)f * N + j;
+                v = llr_i8 ? (float)((const int8_t*)llr)[idx] : ((const float*)llr)[idx];
+            }
+            tile[y][q * 32 + lane] = v;
         }
-        tile[y][threadIdx.x] = v;
     }
     __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        int j = j0 + y, f = f0 + threadIdx.x;
+#pragma unroll 4
+    for (int c = warp; c < kLoadTJ; c += 8) {
+        const int j = j0 + c, f = f0 + lane;
         if (j < N && f < Fp) {
-            float v = tile[threadIdx.x][y];
-            size_t idx = (size_t)j * Fp + f;
+            const float v = tile[lane][c];
+            const size_t idx = (size_t)j * Fp + f;
             if (MODE == kModeFP32) {  // "+ 0.0f" turns -0.0 into +0.0, no other value
                 r[idx] = (R)(v + 0.0f);
                 s[idx] = (T)(v + 0.0f);
             } else {
-                int8_t q = llr_i8 ? (int8_t)v : quantize(v);
-                r[idx] = (R)q;
-                s[idx] = (T)q;
+                const int8_t q8 = llr_i8 ? (int8_t)v : quantize(v);
+                r[idx] = (R)q8;
+                s[idx] = (T)q8;
             }
         }
     }
@@ -1155,34 +1166,44 @@ __global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col
     }
 }
 
-// s [N][Fp] (by position) -> bits (and soft) [frames][N] (by frame); 32 x 32 tiles.
+// s [N][Fp] (by position) -> bits (and soft) [frames][N] (by frame). A block of 8 warps
+// moves a tile of 128 bits x 32 positions: each warp reads bit rows (32 positions, one
+// coalesced load), then writes frame rows of 128 decisions (four 32-byte stores per row).
+constexpr int kStoreTJ = 128, kStoreTF = 32;
 template <int MODE>
-__global__ void k_store(const typename Tr<MODE>::T* s, int Fp, int N, const int32_t* pos2frame,
-                        const int32_t* comp, uint8_t* bits, float* soft, int paper) {
+__global__ void __launch_bounds__(256) k_store(const typename Tr<MODE>::T* s, int Fp, int N,
+                                               const int32_t* pos2frame, const int32_t* comp,
+                                               uint8_t* bits, float* soft, int paper) {
     using A = typename Tr<MODE>::A;
-    __shared__ float tile[32][33];
-    __shared__ int32_t fr[32];
+    __shared__ float tile[kStoreTJ][kStoreTF + 1];
+    __shared__ int32_t fr[kStoreTF];
     const int cur = comp[1];
-    const int j0 = blockIdx.x * 32, p0 = blockIdx.y * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j0 = blockIdx.x * kStoreTJ, p0 = blockIdx.y * kStoreTF;
     if (p0 >= cur) return;
-    if (threadIdx.y == 0) {
-        const int p = p0 + threadIdx.x;
-        fr[threadIdx.x] = p < cur ? pos2frame[p] : -1;
+    if (warp == 0) {
+        const int p = p0 + lane;
+        fr[lane] = p < cur ? pos2frame[p] : -1;
     }
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        int j = j0 + y, p = p0 + threadIdx.x;
-        float v = 0.0f;
-        if (j < N && p < cur) v = (float)s[(size_t)j * Fp + p];
-        tile[y][threadIdx.x] = v;
+#pragma unroll 4
+    for (int c = warp; c < kStoreTJ; c += 8) {
+        const int j = j0 + c, p = p0 + lane;
+        tile[c][lane] = (j < N && p < cur) ? (float)s[(size_t)j * Fp + p] : 0.0f;
     }
     __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int f = fr[y], j = j0 + threadIdx.x;
-        if (f >= 0 && j < N) {
-            float v = tile[threadIdx.x][y];  // exact for fp32 and int16 values
-            size_t idx = (size_t)f * N + j;
-            bits[idx] = (uint8_t)slice((A)v, paper);
-            if (soft) soft[idx] = (MODE == kModeFP32) ? v : v * 0.25f;
+#pragma unroll
+    for (int y = warp; y < kStoreTF; y += 8) {
+        const int f = fr[y];
+        if (f < 0) continue;
+#pragma unroll
+        for (int q = 0; q < kStoreTJ / 32; q++) {
+            const int j = j0 + q * 32 + lane;
+            if (j < N) {
+                const float v = tile[q * 32 + lane][y];  // exact for fp32 and int16 values
+                const size_t idx = (size_t)f * N + j;
+                bits[idx] = (uint8_t)slice((A)v, paper);
+                if (soft) soft[idx] = (MODE == kModeFP32) ? v : v * 0.25f;
+            }
         }
     }
 }
@@ -1368,8 +1389,8 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
     k_init_state<<<(Fp + 255) / 256, 256, 0, st>>>(state, w.done_iter, w.pos2frame, w.comp, Fp,
                                                     a.frames);
     launches++;
-    k_load<MODE><<<dim3((a.N + 31) / 32, Fp / 32), dim3(32, 8), 0, st>>>(a.llr, a.llr_is_i8, a.frames,
-                                                                        a.N, r, s, Fp);
+    k_load<MODE><<<dim3((a.N + kLoadTJ - 1) / kLoadTJ, Fp / kLoadTF), 256, 0, st>>>(a.llr, a.llr_is_i8,
+                                                                                      a.frames, a.N, r, s, Fp);
     launches++;
     const dim3 gc((a.M + 3) / 4, Fp / (32 * V)), gv((a.N + 3) / 4, Fp / (32 * V));
     // message slot of each edge in column order: padded-row slots or CSR edge ids
@@ -1440,7 +1461,7 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
         k_check<MODE, false, true, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp, state,
                                                                  unf, 1, w.n_done, a.frames, a.paper_slicer);
     // (frames that stopped early are skipped there: their status is known)
-    k_store<MODE><<<dim3((a.N + 31) / 32, Fp / 32), dim3(32, 8), 0, st>>>(
+    k_store<MODE><<<dim3((a.N + kStoreTJ - 1) / kStoreTJ, Fp / kStoreTF), 256, 0, st>>>(
         s, Fp, a.N, w.pos2frame, w.comp, a.out_bits, a.out_soft, a.paper_slicer);
     k_finish<<<(Fp + 255) / 256, 256, 0, st>>>(w.done_iter, w.pos2frame, w.comp, unf, Fp, a.L,
                                                a.out_iters, a.out_ok);
