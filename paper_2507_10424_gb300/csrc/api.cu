@@ -158,8 +158,8 @@ static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L, int32_t gran
         }
         const size_t tb = 4, rb = 4;  // sized for fp32; the fixed mode uses less
         const size_t eta = (size_t)h->dg.eta_slots * Fp * tb, sb = (size_t)h->N * Fp * tb,
-                     rr = (size_t)h->N * Fp * rb;
-        const size_t total = eta + sb + rr + (size_t)Fp * 12 + (size_t)Fp + 1024;
+                     rr = (size_t)h->N * Fp * rb, hd = (size_t)h->N * (Fp / 4);
+        const size_t total = eta + sb + rr + hd + (size_t)Fp * 12 + (size_t)Fp + 1280;
         cudaError_t e = cudaMalloc(&h->sw_big, total);
         if (e != cudaSuccess) {
             h->sw_big = nullptr;
@@ -173,6 +173,8 @@ static int ensure_stream_work(ldpc_t* h, int32_t frames, int32_t L, int32_t gran
         p += (sb + 255) & ~(size_t)255;
         h->sw.r = p;
         p += (rr + 255) & ~(size_t)255;
+        h->sw.hd = (uint8_t*)p;
+        p += (hd + 255) & ~(size_t)255;
         h->sw.done_iter = (int32_t*)p;
         p += (size_t)Fp * 4;
         h->sw.pos2frame = (int32_t*)p;

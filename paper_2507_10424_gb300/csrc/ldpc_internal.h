@@ -203,6 +203,9 @@ struct StreamWork {
     int32_t* comp = nullptr;       // [4]
     uint8_t* unsat = nullptr;      // [(L+2)][Fp]
     int32_t* n_done = nullptr;     // [1]
+    // decisions of the last bit pass, one byte per lane of 4 or 8 frames: [N][Fp / 4] bytes
+    // (nullable: the final syndrome and the output bits are then taken from s)
+    uint8_t* hd = nullptr;
     // staged check pass (padded row layout only): warps per CTA and shared-memory stages
     // per warp, 0 stages = the register kernel; err: device error word (kernels set it,
     // the host reads and clears it); wait_limit: tries of each bounded wait

@@ -14,11 +14,12 @@ int stream_decode_fixed(const DevGraph& g, const DecodeArgs& a, const StreamWork
 
 size_t stream_bytes(int mode, int32_t N, int64_t slots, int32_t Fp, int32_t L) {
     size_t tb = mode == kModeFP32 ? 4 : 2, rb = mode == kModeFP32 ? 4 : 1;
-    return (size_t)slots * Fp * tb + (size_t)N * Fp * (tb + rb) + (size_t)Fp * 13 + (size_t)(L + 2) * Fp + 256;
+    return (size_t)slots * Fp * tb + (size_t)N * Fp * (tb + rb) + (size_t)N * (Fp / 4) + (size_t)Fp * 13 +
+           (size_t)(L + 2) * Fp + 256;
 }
 
 StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t slots, int32_t Fp, int32_t L) {
-    // Fp is a multiple of 256, so every region below starts 256-byte aligned
+    // Fp is a multiple of 256, so every region below starts 64-byte aligned (256-byte up to hd)
     const size_t tb = mode == kModeFP32 ? 4 : 2, rb = mode == kModeFP32 ? 4 : 1;
     char* p = (char*)mem;
     StreamWork w;
@@ -29,6 +30,8 @@ StreamWork stream_carve(int mode, void* mem, int32_t N, int64_t slots, int32_t F
     p += (size_t)N * Fp * tb;
     w.r = p;
     p += (size_t)N * Fp * rb;
+    w.hd = (uint8_t*)p;
+    p += (size_t)N * (Fp / 4);
     w.done_iter = (int32_t*)p;
     p += (size_t)Fp * 4;
     w.pos2frame = (int32_t*)p;

@@ -1059,12 +1059,16 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
 // CMP (FP32): the messages are compressed (cmsg.cuh): col_edge holds padded-row slots
 // i 2^dshift + t, and the message of each edge is rebuilt from row i's state cs, weighted
 // (W) with this iteration's weights of the column's class.
+// HD (the last iteration, 4 or 8 frames per lane): each lane also writes the decisions of
+// its frames as one byte, bit v = frame f0 + v, to hd[j][Fp / VW] (byte f0 / VW), for the
+// final syndrome and the output bits (k_syn_hd, k_store_hd). Only lanes that update
+// their frames write: the other bytes belong to frames whose status is already known.
 // ------------------------------------------------------------------------------------
 // The pass is bound by the latency of its gathers (index, then message or row state), not
 // by bandwidth: it runs at 16 blocks of 128 threads per SM (all 64 warps, at most 32
 // registers), which measured faster than fewer, larger-register warps (N=64800 FP32 with
 // compressed messages: 102 -> 96.5 ms per 4096-frame, 50-iteration decode).
-template <int MODE, int VW = Tr<MODE>::V, bool CMP = false, bool W = false>
+template <int MODE, int VW = Tr<MODE>::V, bool CMP = false, bool W = false, bool HD = false>
 __global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col_ptr,
                                              const int32_t* __restrict__ col_edge, int N,
                                              const typename Tr<MODE>::R* __restrict__ r,
@@ -1074,7 +1078,8 @@ __global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col
                                              const int32_t* __restrict__ pos2frame,
                                              const uint8_t* __restrict__ unsat, int test_prev,
                                              int k, int* n_done, int frames, CState cs = CState{},
-                                             int dshift = 0, IterWeights wt = IterWeights()) {
+                                             int dshift = 0, IterWeights wt = IterWeights(),
+                                             uint8_t* hd = nullptr, int paper = 0) {
     using T = typename Tr<MODE>::T;
     using R = typename Tr<MODE>::R;
     using A = typename Tr<MODE>::A;
@@ -1150,6 +1155,13 @@ __global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col
             for (int v = 0; v < V; v++) acc[v] = acc[v] + (A)ev.x[v];
         }
     }
+    if constexpr (HD) {
+        static_assert(V == 4 || V == 8, "one byte of decisions per lane");
+        uint32_t b = 0;
+#pragma unroll
+        for (int v = 0; v < V; v++) b |= slice(acc[v], paper) << v;  // the sign survives sat16
+        hd[(size_t)j * (Fp / V) + f0 / V] = (uint8_t)b;
+    }
     T* sp = s + (size_t)j * Fp + f0;
     if (upd == (1u << V) - 1u) {
         VT out;
@@ -1204,6 +1216,110 @@ __global__ void __launch_bounds__(256) k_store(const typename Tr<MODE>::T* s, in
                 bits[idx] = (uint8_t)slice((A)v, paper);
                 if (soft) soft[idx] = (MODE == kModeFP32) ? v : v * 0.25f;
             }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Decisions of the last bit pass, packed (HD variant of k_var): hd[j][Fp / VW] bytes, bit v
+// of byte g = the decision at position g VW + v. A 32-bit word u of a row of hd holds
+// positions 4 u VW + q, q = k VW + v at bit 8 k + v (the upper nibbles stay 0 when VW = 4).
+// ------------------------------------------------------------------------------------
+// Final syndrome (eq. 1-2) from the packed decisions: a thread XORs the words of a row's
+// bits, for kSynRows rows in a row, and flags the positions of every failing check once.
+// A warp reads 32 consecutive words of one row of hd: 128 bytes, mostly from L2 (the
+// decisions of 4096 frames of N=64800 bits take 33 MB).
+constexpr int kSynRows = 8;
+template <int VW, int D>
+__global__ void __launch_bounds__(256) k_syn_hd(const int32_t* __restrict__ ell_col,
+                                                const uint8_t* __restrict__ ell_deg, int M,
+                                                const uint8_t* __restrict__ hd, int Fp,
+                                                uint8_t* __restrict__ unsat) {
+    const int nw = Fp / (4 * VW);  // words per row of hd
+    const int wpr = (nw + 31) / 32;  // warps per run of rows
+    const int gw = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int run = gw / wpr, u = (gw - run * wpr) * 32 + (threadIdx.x & 31);
+    const int i0 = run * kSynRows;
+    if (i0 >= M || u >= nw) return;
+    const uint32_t* hw = reinterpret_cast<const uint32_t*>(hd) + u;
+    const int i1 = min(M, i0 + kSynRows);
+    uint32_t fail = 0;
+    for (int i = i0; i < i1; i++) {
+        const int d = __ldg(ell_deg + i);
+        int c[D];
+#pragma unroll
+        for (int q = 0; q < D / 4; q++) {
+            const int4 v = __ldg(reinterpret_cast<const int4*>(ell_col + (size_t)i * D) + q);
+            c[4 * q] = v.x;
+            c[4 * q + 1] = v.y;
+            c[4 * q + 2] = v.z;
+            c[4 * q + 3] = v.w;
+        }
+        uint32_t z = 0;
+#pragma unroll
+        for (int t = 0; t < D; t++) {
+            if (t >= d) break;
+            z ^= __ldg(hw + (size_t)c[t] * nw);
+        }
+        fail |= z;
+    }
+    while (fail) {  // read before writing, as flag_unsat does
+        const int b = __ffs(fail) - 1;
+        fail &= fail - 1;
+        const int p = 4 * u * VW + (b >> 3) * VW + (b & 7);
+        if (!((volatile const uint8_t*)unsat)[p]) unsat[p] = 1;
+    }
+}
+
+// Output bits from the packed decisions (no soft output, and every position in use was
+// updated by the last bit pass: no early stop). A warp takes 32 bits j (lane = bit) and
+// four words of hd: each lane loads 16 bytes of its bit's row, and one ballot per position
+// gives the decisions of the 32 bits at that position (a 32 x 32 bit transpose); the lane
+// of that position then writes them as 32 bytes of its frame's row of `bits`.
+template <int VW>
+__global__ void __launch_bounds__(256) k_store_hd(const uint8_t* __restrict__ hd, int Fp, int N,
+                                                  const int32_t* __restrict__ pos2frame,
+                                                  const int32_t* __restrict__ comp, uint8_t* __restrict__ bits) {
+    constexpr int PW = 4 * VW;    // positions per word
+    constexpr int WPB = 32 / PW;  // words per 32 positions
+    const int nw = Fp / PW;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int nq = nw / 4;  // groups of 4 words
+    const int jt = gw / nq, u0 = (gw - jt * nq) * 4;
+    const int j0 = jt * 32;
+    if (j0 >= N) return;  // warp-uniform
+    const int cur = comp[1];
+    if (u0 * PW >= cur) return;  // warp-uniform: no position in use
+    const int j = j0 + lane;
+    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+    if (j < N) w4 = __ldg(reinterpret_cast<const uint4*>(hd + (size_t)j * (Fp / VW)) + u0 / 4);
+    const uint32_t words[4] = {w4.x, w4.y, w4.z, w4.w};
+    const bool vec = (N & 15) == 0 && j0 + 32 <= N && ((uintptr_t)bits & 15) == 0;
+#pragma unroll
+    for (int bt = 0; bt < 4 / WPB; bt++) {  // 32 positions at a time
+        uint32_t mine = 0;
+#pragma unroll
+        for (int x = 0; x < WPB; x++) {
+#pragma unroll
+            for (int q = 0; q < PW; q++) {
+                const uint32_t m = __ballot_sync(0xffffffffu, (words[bt * WPB + x] >> ((q / VW) * 8 + q % VW)) & 1u);
+                if (lane == x * PW + q) mine = m;
+            }
+        }
+        const int p = (u0 + bt * WPB) * PW + lane;
+        if (p >= cur) continue;
+        const int f = pos2frame[p];
+        if (f < 0) continue;
+        uint8_t* dst = bits + (size_t)f * N + j0;
+        if (vec) {  // 16-byte aligned: bits, N and j0 are
+            uint32_t o[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) o[k] = (((mine >> (4 * k)) & 15u) * 0x00204081u) & 0x01010101u;
+            reinterpret_cast<uint4*>(dst)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+            reinterpret_cast<uint4*>(dst)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        } else {
+            for (int k = 0; k < 32 && j0 + k < N; k++) dst[k] = (uint8_t)((mine >> k) & 1u);
         }
     }
 }
@@ -1374,6 +1490,30 @@ int compact(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStr
     return cmp ? 8 : 7;
 }
 
+// One bit pass of iteration k; hd: the HD variant (the last iteration, decisions packed).
+template <int MODE, int V, bool CMP, bool W>
+void var_pass(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, dim3 gv, const int32_t* cslot,
+              uint8_t* un, int test_prev, int k, bool hd, const CState& cs, int dshift,
+              const IterWeights& wt, cudaStream_t st) {
+    using T = typename Tr<MODE>::T;
+    using R = typename Tr<MODE>::R;
+    const R* r = (const R*)w.r;
+    T* s = (T*)w.s;
+    const T* eta = (const T*)w.eta;
+    if constexpr (V == 4 || V == 8) {
+        if (hd) {
+            k_var<MODE, V, CMP, W, true><<<gv, 128, 0, st>>>(g.col_ptr, cslot, a.N, r, s, eta, w.Fp, w.state,
+                                                             w.done_iter, w.pos2frame, un, test_prev, k,
+                                                             w.n_done, a.frames, cs, dshift, wt, w.hd,
+                                                             a.paper_slicer);
+            return;
+        }
+    }
+    k_var<MODE, V, CMP, W><<<gv, 128, 0, st>>>(g.col_ptr, cslot, a.N, r, s, eta, w.Fp, w.state, w.done_iter,
+                                               w.pos2frame, un, test_prev, k, w.n_done, a.frames, cs, dshift,
+                                               wt);
+}
+
 template <int MODE, int V>
 int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_t st) {
     using T = typename Tr<MODE>::T;
@@ -1400,6 +1540,11 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
     bool cmp = MODE == kModeFP32 && w.msg_compressed && g.ell_D > 0 && w.stages > 0 &&
                (a.w_rows == 0 || a.n_classes <= 256);
     const int dshift = g.ell_D == 16 ? 4 : 3;
+    // decisions of the last bit pass packed into w.hd (4 or 8 frames per lane): for the final
+    // syndrome on the padded row layout, and for the output bits when no frame stops early
+    // and no soft output is asked for (every position in use is then updated by that pass)
+    const bool hd_store = !a.early_stop && !a.out_soft;
+    const bool hd = (V == 4 || V == 8) && w.hd && a.L >= 1 && (g.ell_D > 0 || hd_store);
     auto weights_of = [&](int k) {  // learned weights of iteration k (none for k < 1)
         IterWeights wt{};
         if (MODE == kModeFP32 && a.w_rows > 0 && k >= 1) {
@@ -1425,13 +1570,11 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
                 if (ok) {
                     const CState cs = cstate_at(eta, a.M, Fp);
                     if (W)
-                        k_var<MODE, V, true, true><<<gv, 128, 0, st>>>(
-                            g.col_ptr, g.ell_cslot, a.N, r, s, eta, Fp, state, w.done_iter, w.pos2frame, un,
-                            test_prev, k, w.n_done, a.frames, cs, dshift, wt);
+                        var_pass<MODE, V, true, true>(g, a, w, gv, g.ell_cslot, un, test_prev, k, hd && k == a.L,
+                                                      cs, dshift, wt, st);
                     else
-                        k_var<MODE, V, true, false><<<gv, 128, 0, st>>>(
-                            g.col_ptr, g.ell_cslot, a.N, r, s, eta, Fp, state, w.done_iter, w.pos2frame, un,
-                            test_prev, k, w.n_done, a.frames, cs, dshift, wt);
+                        var_pass<MODE, V, true, false>(g, a, w, gv, g.ell_cslot, un, test_prev, k, hd && k == a.L,
+                                                       cs, dshift, wt, st);
                     launches += 2;
                     if (a.early_stop && k < a.L && k % kCompactEvery == 0 && w.comp)
                         launches += compact<MODE>(g, a, w, st, true);
@@ -1442,27 +1585,53 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
             }
         }
         check_pass<MODE, V>(g, a, w, gc, s, eta, un, test_prev, k == 1, wt, st);
-        k_var<MODE, V><<<gv, 128, 0, st>>>(g.col_ptr, cslot, a.N, r, s, eta, Fp, state,
-                                        w.done_iter, w.pos2frame, un, test_prev, k, w.n_done,
-                                        a.frames);
+        var_pass<MODE, V, false, false>(g, a, w, gv, cslot, un, test_prev, k, hd && k == a.L, CState{}, 0,
+                                        IterWeights(), st);
         launches += 2;
         if (a.early_stop && k < a.L && k % kCompactEvery == 0 && w.comp)
             launches += compact<MODE>(g, a, w, st, false);
     }
     if (w.used_compressed) *w.used_compressed = cmp ? 1 : 0;
     uint8_t* unf = w.unsat + (size_t)(a.L + 1) * Fp;
-    if (g.ell_D == 8) {
-        if (!launch_staged<MODE, V, true, false, 8, true>(g, a, w, s, eta, unf, 1, IterWeights(), st))
-            k_syn_ell<MODE, V, 8><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, Fp, state, unf, a.paper_slicer);
-    } else if (g.ell_D == 16) {
-        if (!launch_staged<MODE, V, true, false, 16, true>(g, a, w, s, eta, unf, 1, IterWeights(), st))
-            k_syn_ell<MODE, V, 16><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, Fp, state, unf, a.paper_slicer);
-    } else
-        k_check<MODE, false, true, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp, state,
-                                                                 unf, 1, w.n_done, a.frames, a.paper_slicer);
+    bool syn_done = false;
+    if constexpr (V == 4 || V == 8) {
+        if (hd && (g.ell_D == 8 || g.ell_D == 16)) {
+            const int64_t warps = (int64_t)((a.M + kSynRows - 1) / kSynRows) * ((Fp / (4 * V) + 31) / 32);
+            const unsigned blocks = (unsigned)((warps + 7) / 8);
+            if (g.ell_D == 8)
+                k_syn_hd<V, 8><<<blocks, 256, 0, st>>>(g.ell_col, g.ell_deg, a.M, w.hd, Fp, unf);
+            else
+                k_syn_hd<V, 16><<<blocks, 256, 0, st>>>(g.ell_col, g.ell_deg, a.M, w.hd, Fp, unf);
+            syn_done = true;
+        }
+    }
+    if (!syn_done) {
+        if (g.ell_D == 8) {
+            if (!launch_staged<MODE, V, true, false, 8, true>(g, a, w, s, eta, unf, 1, IterWeights(), st))
+                k_syn_ell<MODE, V, 8><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, Fp, state, unf,
+                                                          a.paper_slicer);
+        } else if (g.ell_D == 16) {
+            if (!launch_staged<MODE, V, true, false, 16, true>(g, a, w, s, eta, unf, 1, IterWeights(), st))
+                k_syn_ell<MODE, V, 16><<<gc, 128, 0, st>>>(g.ell_col, g.ell_deg, a.M, s, Fp, state, unf,
+                                                           a.paper_slicer);
+        } else
+            k_check<MODE, false, true, false, V><<<gc, 128, 0, st>>>(g.row_ptr, g.col_idx, a.M, s, eta, Fp,
+                                                                     state, unf, 1, w.n_done, a.frames,
+                                                                     a.paper_slicer);
+    }
     // (frames that stopped early are skipped there: their status is known)
-    k_store<MODE><<<dim3((a.N + kStoreTJ - 1) / kStoreTJ, Fp / kStoreTF), 256, 0, st>>>(
-        s, Fp, a.N, w.pos2frame, w.comp, a.out_bits, a.out_soft, a.paper_slicer);
+    bool stored = false;
+    if constexpr (V == 4 || V == 8) {
+        if (hd && hd_store) {
+            const int64_t warps = (int64_t)((a.N + 31) / 32) * (Fp / (16 * V));
+            k_store_hd<V><<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(w.hd, Fp, a.N, w.pos2frame, w.comp,
+                                                                     a.out_bits);
+            stored = true;
+        }
+    }
+    if (!stored)
+        k_store<MODE><<<dim3((a.N + kStoreTJ - 1) / kStoreTJ, Fp / kStoreTF), 256, 0, st>>>(
+            s, Fp, a.N, w.pos2frame, w.comp, a.out_bits, a.out_soft, a.paper_slicer);
     k_finish<<<(Fp + 255) / 256, 256, 0, st>>>(w.done_iter, w.pos2frame, w.comp, unf, Fp, a.L,
                                                a.out_iters, a.out_ok);
     launches += 3;
