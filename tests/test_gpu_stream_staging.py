@@ -141,3 +141,44 @@ def test_frame_compaction_keeps_every_output(torch_cuda, mode, shape):
     assert len(np.unique(want[1])) > 8  # stops spread over many iterations
     got = staged_decode(torch_cuda, code, llr, 30, mode, shape)
     assert_parity(got, want, mode, f"compaction {shape}")
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fixed"])
+def test_bits_only_outputs_match_oracle(torch_cuda, mode):
+    """Decodes that ask for no posteriors take their final syndrome, and (without early
+    stop) their output bits, from the decisions the last bit pass packs one byte per lane.
+    Checked against the oracle on codes with 8- and 16-slot padded rows, rows longer than
+    16 edges (CSR), a length that is not a multiple of 16, ragged frame counts, both
+    slicers, lanes of every width, and an output buffer that starts at an odd address."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder
+    cs = dict(codes())
+    cs["irregular1000"] = inputs.irregular_code(1000, 500, [2, 3, 8], [0.5, 0.375, 0.125], 12)
+    cs["paper_shaped"] = inputs.cfg_paper_shaped()
+    for name, code in cs.items():
+        F = 300 if code.N < 4000 else 40
+        llr = inputs.all_zero_awgn_llr(F, code.N, 2.0, code.design_rate, 43)
+        x = torch.from_numpy(llr).cuda()
+        for paper in (False, True):
+            for early_stop in (False, True):
+                want = oracle_decode(code, llr, 9, mode, early_stop=early_stop, paper_slicer=paper)
+                for shape in [(0, 0, 0), (0, -1, 0), (12, 2, 4), (12, 2, 2)]:
+                    dec = Decoder.from_code(code, mode=mode, paper_slicer=paper)
+                    dec.set_variant("stream")
+                    dec.set_stream_staging(*shape)
+                    raw = torch.full((F * code.N + 1,), 7, dtype=torch.uint8, device="cuda")
+                    bits = raw[1:].view(F, code.N)  # odd address: no 16-byte stores
+                    iters = torch.empty(F, dtype=torch.int32, device="cuda")
+                    ok = torch.empty(F, dtype=torch.uint8, device="cuda")
+                    dec.decode(x, 9, early_stop=early_stop, out=(bits, iters, ok, None))
+                    dec.check_device()
+                    what = f"{name} {mode} paper={paper} early_stop={early_stop} {shape}"
+                    assert raw[0].item() == 7, what
+                    np.testing.assert_array_equal(bits.cpu().numpy(), want[0], err_msg=what)
+                    np.testing.assert_array_equal(iters.cpu().numpy(), want[1], err_msg=what)
+                    np.testing.assert_array_equal(ok.cpu().numpy(), want[2], err_msg=what)
+                    # the same decode into an aligned buffer
+                    b2, it2, ok2, _ = dec.decode(x, 9, early_stop=early_stop, want_ok=True)
+                    np.testing.assert_array_equal(b2.cpu().numpy(), want[0], err_msg=what)
+                    np.testing.assert_array_equal(ok2.cpu().numpy(), want[2], err_msg=what)
+                    dec.close()
