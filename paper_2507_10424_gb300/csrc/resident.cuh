@@ -237,19 +237,42 @@ __host__ __device__ constexpr int col_body_max() {
 // The row pass reads its slots contiguously: no gather of s and no index read per edge.
 // ---------------------------------------------------------------------------------------
 
+// Decision byte of a posterior vector (standard slicer): bit f = [s_f < 0], the sign bit
+// (s never holds -0.0, and the fixed-point sums are saturated integers).
+template <typename T, int FT>
+__device__ __forceinline__ uint32_t dec_byte(const VecR<T, FT>& v) {
+    uint32_t b = 0;
+#pragma unroll
+    for (int f = 0; f < FT; f++) b |= (bits_of((typename std::conditional<sizeof(T) == 4, float, int32_t>::type)v.x[f]) >> 31) << f;
+    return b;
+}
+// The same for packed pairs: frame 2p in bit 15 of word p, frame 2p + 1 in bit 31.
+template <int P>
+__device__ __forceinline__ uint32_t dec_byte_packed(const Words<P>& w) {
+    uint32_t b = 0;
+#pragma unroll
+    for (int p = 0; p < P; p++) b |= (((w.w[p] >> 15) & 1u) << (2 * p)) | ((w.w[p] >> 31) << (2 * p + 1));
+    return b;
+}
+
 // The syndrome of s gathered by the row pass itself (early-stop kernels, on the iterations
 // that test it): per row, bit 31 of zx[f] is the XOR of frame f's decisions over the row's
 // bits (read from s through the slot's column position); the failing frames of the
 // thread's rows collect in z, and a warp-wide OR reaches the CTA's word once per pass.
 // With ON false every member is empty and the row pass is the plain one.
-template <int MODE, int FT, bool PAPER, bool ON>
+// DEC: the decisions come from the slots' decision bytes instead (bit f = frame f's
+// decision on the slot's bit, written by the column pass): one contiguous byte per edge
+// instead of a position index and a gathered posterior vector.
+template <int MODE, int FT, bool PAPER, bool ON, bool DEC = false>
 struct RowSyn {
     const VecR<typename RT<MODE>::T, FT>* s;
     uint32_t* unsat_w;
+    const uint8_t* dec;
     uint32_t zx[FT];
     uint32_t z;
-    __device__ __forceinline__ RowSyn(const VecR<typename RT<MODE>::T, FT>* s_, uint32_t* u)
-        : s(s_), unsat_w(u), z(0) {}
+    __device__ __forceinline__ RowSyn(const VecR<typename RT<MODE>::T, FT>* s_, uint32_t* u,
+                                      const uint8_t* d = nullptr)
+        : s(s_), unsat_w(u), dec(d), z(0) {}
     __device__ __forceinline__ void row_begin() {
         if constexpr (ON) {
 #pragma unroll
@@ -257,7 +280,9 @@ struct RowSyn {
         }
     }
     __device__ __forceinline__ void add(const Idx& ix, int slot) {
-        if constexpr (ON) {
+        if constexpr (ON && DEC) {
+            zx[0] ^= dec[slot];
+        } else if constexpr (ON) {
             using A = typename RT<MODE>::A;
             const auto sv = s[ix.r_slot_pos[slot]];
 #pragma unroll
@@ -265,7 +290,9 @@ struct RowSyn {
         }
     }
     __device__ __forceinline__ void row_end() {
-        if constexpr (ON) {
+        if constexpr (ON && DEC) {
+            z |= zx[0];
+        } else if constexpr (ON) {
 #pragma unroll
             for (int f = 0; f < FT; f++) z |= (zx[f] >> 31) << f;
         }
@@ -588,9 +615,10 @@ __device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT
 
 // Syndrome of the current s for every row: bit f of the row's result is set when frame f
 // fails the check; the CTA's word collects them.
-template <int MODE, int FT, bool PAPER>
+template <int MODE, int FT, bool PAPER, bool DEC = false>
 __device__ __forceinline__ void syn_pass(const Idx& ix, const VecR<typename RT<MODE>::T, FT>* s,
-                                         int n_rtasks, uint32_t* unsat_w) {
+                                         int n_rtasks, uint32_t* unsat_w,
+                                         const uint8_t* dec = nullptr) {
     using T = typename RT<MODE>::T;
     using A = typename RT<MODE>::A;
     using VT = VecR<T, FT>;
@@ -601,26 +629,33 @@ __device__ __forceinline__ void syn_pass(const Idx& ix, const VecR<typename RT<M
         const int d = ix.r_deg[task];
         if (d == 0) continue;
         const int base = ix.r_base[task >> 5] + (task & 31);
-        uint32_t zx[FT];
-#pragma unroll
-        for (int f = 0; f < FT; f++) zx[f] = 0;
-#pragma unroll 4
-        for (int t = 0; t < d; t++) {
-            const VT sv = s[ix.r_slot_pos[base + 32 * t]];
-#pragma unroll
-            for (int f = 0; f < FT; f++) zx[f] ^= dec_bits<PAPER>((A)sv.x[f]);
-        }
         uint32_t z = 0;
+        if constexpr (DEC) {  // the slots' decision bytes (written by the last column pass)
+#pragma unroll 4
+            for (int t = 0; t < d; t++) z ^= dec[base + 32 * t];
+        } else {
+            uint32_t zx[FT];
 #pragma unroll
-        for (int f = 0; f < FT; f++) z |= (zx[f] >> 31) << f;
+            for (int f = 0; f < FT; f++) zx[f] = 0;
+#pragma unroll 4
+            for (int t = 0; t < d; t++) {
+                const VT sv = s[ix.r_slot_pos[base + 32 * t]];
+#pragma unroll
+                for (int f = 0; f < FT; f++) zx[f] ^= dec_bits<PAPER>((A)sv.x[f]);
+            }
+#pragma unroll
+            for (int f = 0; f < FT; f++) z |= (zx[f] >> 31) << f;
+        }
         if (z) atomicOr(unsat_w, z);
     }
 }
 
-// First lambda of every edge: the channel value of its bit.
-template <int MODE, int FT>
+// First lambda of every edge: the channel value of its bit (DEC: and the decision byte of
+// the channel values, for the syndrome before the first iteration).
+template <int MODE, int FT, bool DEC = false>
 __device__ __forceinline__ void init_pass(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
-                                          const VecR<typename RT<MODE>::T, FT>* r, int N) {
+                                          const VecR<typename RT<MODE>::T, FT>* r, int N,
+                                          uint8_t* dec = nullptr) {
     const int nth = blockDim.x;
     for (int k = 0;; k++) {
         const int p = snake(k, nth);
@@ -628,17 +663,23 @@ __device__ __forceinline__ void init_pass(const Idx& ix, VecR<typename RT<MODE>:
         const int d = ix.c_deg[p];
         const int base = ix.c_base[p >> 5] + (p & 31);
         const auto rv = r[p];
-        for (int t = 0; t < d; t++) slots[ix.c_slot[base + 32 * t]] = rv;
+        const uint32_t db = DEC ? dec_byte(rv) : 0u;
+        for (int t = 0; t < d; t++) {
+            const int slot = ix.c_slot[base + 32 * t];
+            slots[slot] = rv;
+            if constexpr (DEC) dec[slot] = (uint8_t)db;
+        }
     }
 }
 
 // One column of exactly DC edges, per frame: s = r + sum of eta (ascending rows), then
 // lambda = s - eta into each of its slots. Fully unrolled: slots and messages stay in
 // registers between the two loops, and no predicated-off iteration is issued.
-template <int MODE, int FT, int DC>
+template <int MODE, int FT, int DC, bool DEC = false>
 __device__ __forceinline__ void col_fixed(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
                                           VecR<typename RT<MODE>::T, FT>* s,
-                                          const VecR<typename RT<MODE>::T, FT>& rv, int p, int base) {
+                                          const VecR<typename RT<MODE>::T, FT>& rv, int p, int base,
+                                          uint8_t* dec = nullptr) {
     using T = typename RT<MODE>::T;
     using A = typename RT<MODE>::A;
     using VT = VecR<T, FT>;
@@ -665,14 +706,21 @@ __device__ __forceinline__ void col_fixed(const Idx& ix, VecR<typename RT<MODE>:
         for (int f = 0; f < FT; f++) lv.x[f] = (T)lam_sat((A)out.x[f], (A)ev[t].x[f]);
         slots[sl[t]] = lv;
     }
+    if constexpr (DEC) {
+        if (dec) {
+            const uint8_t db = (uint8_t)dec_byte(out);
+#pragma unroll
+            for (int t = 0; t < DC; t++) dec[sl[t]] = db;
+        }
+    }
 }
 
 // A column of any degree: the second loop reads its slots and messages again.
-template <int MODE, int FT>
+template <int MODE, int FT, bool DEC = false>
 __device__ __forceinline__ void col_any(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
                                         VecR<typename RT<MODE>::T, FT>* s,
                                         const VecR<typename RT<MODE>::T, FT>& rv, int p, int base,
-                                        int d) {
+                                        int d, uint8_t* dec = nullptr) {
     using T = typename RT<MODE>::T;
     using A = typename RT<MODE>::A;
     using VT = VecR<T, FT>;
@@ -688,6 +736,7 @@ __device__ __forceinline__ void col_any(const Idx& ix, VecR<typename RT<MODE>::T
 #pragma unroll
     for (int f = 0; f < FT; f++) out.x[f] = (T)rsat_out(acc[f]);
     s[p] = out;
+    const uint32_t db = DEC ? dec_byte(out) : 0u;
     for (int t = 0; t < d; t++) {
         const int slot = ix.c_slot[base + 32 * t];
         const VT ev = slots[slot];
@@ -695,6 +744,9 @@ __device__ __forceinline__ void col_any(const Idx& ix, VecR<typename RT<MODE>::T
 #pragma unroll
         for (int f = 0; f < FT; f++) lv.x[f] = (T)lam_sat((A)out.x[f], (A)ev.x[f]);
         slots[slot] = lv;
+        if constexpr (DEC) {
+            if (dec) dec[slot] = (uint8_t)db;
+        }
     }
 }
 
@@ -718,9 +770,10 @@ struct PackedLam {
     }
 };
 
-template <int FT, int DC>
+template <int FT, int DC, bool DEC = false>
 __device__ __forceinline__ void col_fixed_packed(const Idx& ix, Words<FT / 2>* slots, Words<FT / 2>* s,
-                                                 const Words<FT / 2>& rv, int p0, int base) {
+                                                 const Words<FT / 2>& rv, int p0, int base,
+                                                 uint8_t* dec = nullptr) {
     constexpr int P = FT / 2;
     using WT = Words<P>;
     int32_t lo[P], hi[P];
@@ -755,11 +808,19 @@ __device__ __forceinline__ void col_fixed_packed(const Idx& ix, Words<FT / 2>* s
         for (int p = 0; p < P; p++) lv.w[p] = lam[p](ev[t].w[p]);
         slots[sl[t]] = lv;
     }
+    if constexpr (DEC) {
+        if (dec) {
+            const uint8_t db = (uint8_t)dec_byte_packed(out);
+#pragma unroll
+            for (int t = 0; t < DC; t++) dec[sl[t]] = db;
+        }
+    }
 }
 
-template <int FT>
+template <int FT, bool DEC = false>
 __device__ __forceinline__ void col_any_packed(const Idx& ix, Words<FT / 2>* slots, Words<FT / 2>* s,
-                                               const Words<FT / 2>& rv, int p0, int base, int d) {
+                                               const Words<FT / 2>& rv, int p0, int base, int d,
+                                               uint8_t* dec = nullptr) {
     constexpr int P = FT / 2;
     using WT = Words<P>;
     int32_t lo[P], hi[P];
@@ -783,6 +844,7 @@ __device__ __forceinline__ void col_any_packed(const Idx& ix, Words<FT / 2>* slo
     PackedLam lam[P];
 #pragma unroll
     for (int p = 0; p < P; p++) lam[p].set(out.w[p]);
+    const uint32_t db = DEC ? dec_byte_packed(out) : 0u;
     for (int t = 0; t < d; t++) {
         const int slot = ix.c_slot[base + 32 * t];
         const WT ev = slots[slot];
@@ -790,16 +852,21 @@ __device__ __forceinline__ void col_any_packed(const Idx& ix, Words<FT / 2>* slo
 #pragma unroll
         for (int p = 0; p < P; p++) lv.w[p] = lam[p](ev.w[p]);
         slots[slot] = lv;
+        if constexpr (DEC) {
+            if (dec) dec[slot] = (uint8_t)db;
+        }
     }
 }
 
 // Column pass over every column position of the tile; columns up to col_body_max edges take
 // the fully unrolled body of their degree (the degree-sorted slices keep a warp's columns
 // on the same case).
-template <int MODE, int FT, bool UNROLL = true>
+// DEC: also the decision byte of each column into its slots of `dec` (when not null).
+template <int MODE, int FT, bool UNROLL = true, bool DEC = false>
 __device__ __forceinline__ void cols_pass(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots_v,
                                           VecR<typename RT<MODE>::T, FT>* s_v,
-                                          const VecR<typename RT<MODE>::T, FT>* r_v, int N) {
+                                          const VecR<typename RT<MODE>::T, FT>* r_v, int N,
+                                          uint8_t* dec = nullptr) {
     constexpr bool kPacked = MODE == kModeFixed && FT % 2 == 0;
     const int nth = blockDim.x;
     for (int k = 0;; k++) {
@@ -813,15 +880,15 @@ __device__ __forceinline__ void cols_pass(const Idx& ix, VecR<typename RT<MODE>:
             WT* s = reinterpret_cast<WT*>(s_v);
             const WT rv = reinterpret_cast<const WT*>(r_v)[p];
             if (!UNROLL || !by_degree<col_body_max<MODE, FT>()>(d, [&](auto dc) {
-                    col_fixed_packed<FT, decltype(dc)::value>(ix, slots, s, rv, p, base);
+                    col_fixed_packed<FT, decltype(dc)::value, DEC>(ix, slots, s, rv, p, base, dec);
                 }))
-                col_any_packed<FT>(ix, slots, s, rv, p, base, d);
+                col_any_packed<FT, DEC>(ix, slots, s, rv, p, base, d, dec);
         } else {
             const auto rv = r_v[p];
             if (!UNROLL || !by_degree<col_body_max<MODE, FT>()>(d, [&](auto dc) {
-                    col_fixed<MODE, FT, decltype(dc)::value>(ix, slots_v, s_v, rv, p, base);
+                    col_fixed<MODE, FT, decltype(dc)::value, DEC>(ix, slots_v, s_v, rv, p, base, dec);
                 }))
-                col_any<MODE, FT>(ix, slots_v, s_v, rv, p, base, d);
+                col_any<MODE, FT, DEC>(ix, slots_v, s_v, rv, p, base, d, dec);
         }
     }
 }
@@ -869,11 +936,16 @@ __device__ __forceinline__ void copy_to_smem(T* dst, const T* src, int n) {
 // costs no pass of its own; the frames that are codewords are written out between the
 // two passes. Without ES the syndrome is a pass of its own before the row pass (one
 // barrier more per tested iteration).
-template <int MODE, int FT, bool PAPER, bool W, typename VT, bool UNROLL = true, bool ES = false>
+// DEC (early-stop kernels with the index arrays in shared memory): every syndrome reads
+// the slots' decision bytes `dec` [E_pad], which the init pass and the column passes before
+// a tested iteration write, instead of gathering s through the slots' column positions.
+template <int MODE, int FT, bool PAPER, bool W, typename VT, bool UNROLL = true, bool ES = false,
+          bool DEC = false>
 __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, VT* s, VT* r,
                                             uint32_t* unsat_w, int fbase, int nf,
                                             const float* walpha0, const float* wbeta0,
-                                            int n_rtasks) {
+                                            int n_rtasks, uint8_t* dec = nullptr) {
+    static_assert(!DEC || (ES && !PAPER), "decision bytes are the standard slicer's");
     using T = typename RT<MODE>::T;
     constexpr bool kPacked = MODE == kModeFixed && FT % 2 == 0;
     const int N = a.N;
@@ -888,7 +960,7 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
     }
     uint32_t active = (1u << nf) - 1u;
     __syncthreads();
-    init_pass<MODE, FT>(ix, eta, r, N);  // the edge slots hold lambda from here on
+    init_pass<MODE, FT, DEC>(ix, eta, r, N, dec);  // the edge slots hold lambda from here on
     __syncthreads();
 
     for (int k = 0;; k++) {
@@ -896,7 +968,7 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
         const bool last = (k == a.L);
         const bool syn = last || (a.early_stop && (k % a.check_every == 0));
         if (syn && (!ES || last)) {  // the decisions of the current s: stop the codewords
-            syn_pass<MODE, FT, PAPER>(ix, s, n_rtasks, &unsat_w[par]);
+            syn_pass<MODE, FT, PAPER, DEC>(ix, s, n_rtasks, &unsat_w[par], dec);
             __syncthreads();
             const uint32_t conv = active & ~unsat_w[par];
             if (last) {
@@ -917,10 +989,10 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
         if (ES && syn) {
             if constexpr (kPacked)
                 rows_pass_packed<FT, UNROLL>(ix, eta, n_rtasks,
-                                             RowSyn<MODE, FT, PAPER, true>(s, &unsat_w[par]));
+                                             RowSyn<MODE, FT, PAPER, true, DEC>(s, &unsat_w[par], dec));
             else
                 rows_pass<MODE, FT, W, UNROLL && !W>(ix, eta, n_rtasks,
-                                               RowSyn<MODE, FT, PAPER, true>(s, &unsat_w[par]));
+                                               RowSyn<MODE, FT, PAPER, true, DEC>(s, &unsat_w[par], dec));
             __syncthreads();
             const uint32_t conv = active & ~unsat_w[par];
             if (conv) {  // s still holds the decisions of iteration k
@@ -938,7 +1010,13 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
                                                RowSyn<MODE, FT, PAPER, false>(s, nullptr));
             __syncthreads();  // (also orders emit's reads of s before the column pass rewrites s)
         }
-        cols_pass<MODE, FT, UNROLL>(ix, eta, s, r, N);
+        if constexpr (DEC) {  // decision bytes only before an iteration that tests the syndrome
+            const int k1 = k + 1;
+            const bool tested = k1 == a.L || (a.early_stop && k1 % a.check_every == 0);
+            cols_pass<MODE, FT, UNROLL, true>(ix, eta, s, r, N, tested ? dec : nullptr);
+        } else {
+            cols_pass<MODE, FT, UNROLL>(ix, eta, s, r, N);
+        }
         if (threadIdx.x == 0) unsat_w[par ^ 1] = 0;
         __syncthreads();
     }
@@ -954,6 +1032,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
     const int w_entries = W ? a.w_rows * a.n_classes : 0;
     const ResLayout lay = res_layout((int)sizeof(T), FT, a.E_pad, a.Ec_pad, a.n_rsl, a.n_csl, a.N,
                                      IDX_SMEM, w_entries);
+    // early stop with the index arrays in shared memory: the slots' decision bytes take the
+    // place of the slot position array (E_pad bytes of its 2 E_pad). Taken where the gather
+    // of s it replaces is dear: fixed point (the gather's per-frame sign extraction costs
+    // ALU, the bound there, and registers) and FP32 tiles of 4 frames (16-byte vectors
+    // gathered). FP32 tiles of 2 frames keep the gather: measured on the QC N=2304 batch
+    // with early stop, decision bytes took 10.26 -> 10.91 ms (fixed point 9.09 -> 8.08 ms,
+    // FP32 4-frame tiles on N=576 0.0759 -> 0.0704 ms).
+    constexpr bool kDec = ES && IDX_SMEM && !PAPER && (MODE == kModeFixed || FT >= 4);
+    uint8_t* dec = nullptr;
     VT* eta = reinterpret_cast<VT*>(smem_raw + lay.eta);
     VT* s = reinterpret_cast<VT*>(smem_raw + lay.s);
     VT* r = reinterpret_cast<VT*>(smem_raw + lay.r);
@@ -966,14 +1053,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
         uint8_t* cdeg = smem_raw + lay.cdeg;
         int32_t* rbase = reinterpret_cast<int32_t*>(smem_raw + lay.rbase);
         int32_t* cbase = reinterpret_cast<int32_t*>(smem_raw + lay.cbase);
-        copy_to_smem(rpos, a.r_slot_pos, a.E_pad);
+        if (!kDec) copy_to_smem(rpos, a.r_slot_pos, a.E_pad);  // (kDec: the decision bytes' region)
         copy_to_smem(cslot, a.c_slot, a.Ec_pad);
         copy_to_smem(cpos, a.col_pos, a.N);
         copy_to_smem(rdeg, a.r_deg, a.n_rsl * 32);
         copy_to_smem(cdeg, a.c_deg, a.n_csl * 32);
         copy_to_smem(rbase, a.r_base, a.n_rsl + 1);
         copy_to_smem(cbase, a.c_base, a.n_csl + 1);
-        ix = Idx{rbase, rdeg, rpos, cbase, cdeg, cslot, cpos, nullptr, nullptr, nullptr};
+        ix = Idx{rbase, rdeg, kDec ? a.r_slot_pos : rpos, cbase, cdeg, cslot, cpos, nullptr, nullptr, nullptr};
+        dec = reinterpret_cast<uint8_t*>(rpos);
         if (W) {
             uint8_t* wcls = smem_raw + lay.wcls;
             float* wtab = reinterpret_cast<float*>(smem_raw + lay.wtab);
@@ -1002,9 +1090,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_resident(const ResArgs a) {
         const int tile = tile_sh;
         if (tile >= a.n_tiles) break;
         const int fbase = tile * FT;
-        decode_tile<MODE, FT, PAPER, W, VT, true, ES>(a, ix, eta, s, r, unsat_w, fbase,
-                                                      min(FT, a.frames - fbase), walpha0, wbeta0,
-                                                      n_rtasks);
+        decode_tile<MODE, FT, PAPER, W, VT, true, ES, kDec>(a, ix, eta, s, r, unsat_w, fbase,
+                                                            min(FT, a.frames - fbase), walpha0, wbeta0,
+                                                            n_rtasks, dec);
         __syncthreads();
     }
 }
