@@ -1226,49 +1226,66 @@ __global__ void __launch_bounds__(256) k_store(const typename Tr<MODE>::T* s, in
 // positions 4 u VW + q, q = k VW + v at bit 8 k + v (the upper nibbles stay 0 when VW = 4).
 // ------------------------------------------------------------------------------------
 // Final syndrome (eq. 1-2) from the packed decisions: a thread XORs the words of a row's
-// bits, for kSynRows rows in a row, and flags the positions of every failing check once.
-// A warp reads 32 consecutive words of one row of hd: 128 bytes, mostly from L2 (the
-// decisions of 4096 frames of N=64800 bits take 33 MB).
+// bits for kSynRows rows in a row. The 8 warps of a block take 8 runs of rows over the same
+// 32 words of hd (blockIdx.y), OR their failure words in shared memory, and one warp sets
+// the failing positions in the bit array ubits (bit p of word p / 32 = position p fails;
+// cleared beforehand), reading each word first so that the atomic is skipped once its bits
+// are set: every block reports to the same few words. A warp reads 32 consecutive words of
+// one row of hd: 128 bytes, mostly from L2 (the decisions of 4096 frames of N=64800 bits
+// take 33 MB).
 constexpr int kSynRows = 8;
 template <int VW, int D>
 __global__ void __launch_bounds__(256) k_syn_hd(const int32_t* __restrict__ ell_col,
                                                 const uint8_t* __restrict__ ell_deg, int M,
                                                 const uint8_t* __restrict__ hd, int Fp,
-                                                uint8_t* __restrict__ unsat) {
+                                                uint32_t* __restrict__ ubits) {
+    __shared__ uint32_t red[8][32];
     const int nw = Fp / (4 * VW);  // words per row of hd
-    const int wpr = (nw + 31) / 32;  // warps per run of rows
-    const int gw = blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int run = gw / wpr, u = (gw - run * wpr) * 32 + (threadIdx.x & 31);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int run = blockIdx.x * 8 + warp, u = blockIdx.y * 32 + lane;
     const int i0 = run * kSynRows;
-    if (i0 >= M || u >= nw) return;
-    const uint32_t* hw = reinterpret_cast<const uint32_t*>(hd) + u;
-    const int i1 = min(M, i0 + kSynRows);
     uint32_t fail = 0;
-    for (int i = i0; i < i1; i++) {
-        const int d = __ldg(ell_deg + i);
-        int c[D];
+    if (i0 < M && u < nw) {
+        const uint32_t* hw = reinterpret_cast<const uint32_t*>(hd) + u;
+        const int i1 = min(M, i0 + kSynRows);
+        for (int i = i0; i < i1; i++) {
+            const int d = __ldg(ell_deg + i);
+            int c[D];
 #pragma unroll
-        for (int q = 0; q < D / 4; q++) {
-            const int4 v = __ldg(reinterpret_cast<const int4*>(ell_col + (size_t)i * D) + q);
-            c[4 * q] = v.x;
-            c[4 * q + 1] = v.y;
-            c[4 * q + 2] = v.z;
-            c[4 * q + 3] = v.w;
-        }
-        uint32_t z = 0;
+            for (int q = 0; q < D / 4; q++) {
+                const int4 v = __ldg(reinterpret_cast<const int4*>(ell_col + (size_t)i * D) + q);
+                c[4 * q] = v.x;
+                c[4 * q + 1] = v.y;
+                c[4 * q + 2] = v.z;
+                c[4 * q + 3] = v.w;
+            }
+            uint32_t z = 0;
 #pragma unroll
-        for (int t = 0; t < D; t++) {
-            if (t >= d) break;
-            z ^= __ldg(hw + (size_t)c[t] * nw);
+            for (int t = 0; t < D; t++) {
+                if (t >= d) break;
+                z ^= __ldg(hw + (size_t)c[t] * nw);
+            }
+            fail |= z;
         }
-        fail |= z;
     }
-    while (fail) {  // read before writing, as flag_unsat does
-        const int b = __ffs(fail) - 1;
-        fail &= fail - 1;
-        const int p = 4 * u * VW + (b >> 3) * VW + (b & 7);
-        if (!((volatile const uint8_t*)unsat)[p]) unsat[p] = 1;
+    red[warp][lane] = fail;
+    __syncthreads();
+    if (warp != 0 || u >= nw) return;
+    uint32_t f = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) f |= red[k][lane];
+    // word u covers positions 4 u VW + 8 k + v (bit 8 k + v, v < VW): to position bits
+    uint32_t bits = f;
+    int word = u, shift = 0;
+    if constexpr (VW == 4) {
+        bits = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) bits |= ((f >> (8 * k)) & 15u) << (4 * k);
+        word = u >> 1;
+        shift = 16 * (u & 1);
     }
+    bits <<= shift;
+    if (bits && (((volatile const uint32_t*)ubits)[word] & bits) != bits) atomicOr(ubits + word, bits);
 }
 
 // Output bits from the packed decisions (no soft output, and every position in use was
@@ -1325,16 +1342,18 @@ __global__ void __launch_bounds__(256) k_store_hd(const uint8_t* __restrict__ hd
 }
 
 // Status of the frames in the final layout (positions in use).
+// ubits (nullable): the final syndrome as a bit array (k_syn_hd) instead of unsat_final.
 __global__ void k_finish(const int32_t* done_iter, const int32_t* pos2frame, const int32_t* comp,
                          const uint8_t* unsat_final, int Fp, int L, int32_t* out_iters,
-                         uint8_t* out_ok) {
+                         uint8_t* out_ok, const uint32_t* ubits = nullptr) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= Fp || p >= comp[1]) return;
     const int f = pos2frame[p];
     if (f < 0) return;
     const int d = done_iter[f];
     out_iters[f] = d >= 0 ? d : L;
-    if (out_ok) out_ok[f] = d >= 0 ? 1 : (unsat_final[p] == 0);
+    const int fails = ubits ? (int)((ubits[p >> 5] >> (p & 31)) & 1u) : (unsat_final[p] != 0);
+    if (out_ok) out_ok[f] = d >= 0 ? 1 : !fails;
 }
 
 // Launch of the staged check pass; false when the shape does not fit the device or the
@@ -1594,14 +1613,16 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
     if (w.used_compressed) *w.used_compressed = cmp ? 1 : 0;
     uint8_t* unf = w.unsat + (size_t)(a.L + 1) * Fp;
     bool syn_done = false;
+    uint32_t* ubits = nullptr;  // the final syndrome as bits, in the (cleared) unf region
     if constexpr (V == 4 || V == 8) {
         if (hd && (g.ell_D == 8 || g.ell_D == 16)) {
-            const int64_t warps = (int64_t)((a.M + kSynRows - 1) / kSynRows) * ((Fp / (4 * V) + 31) / 32);
-            const unsigned blocks = (unsigned)((warps + 7) / 8);
+            const int runs = (a.M + kSynRows - 1) / kSynRows;
+            const dim3 gs((unsigned)((runs + 7) / 8), (unsigned)((Fp / (4 * V) + 31) / 32));
+            ubits = reinterpret_cast<uint32_t*>(unf);  // Fp / 8 of its Fp bytes, 256-byte aligned
             if (g.ell_D == 8)
-                k_syn_hd<V, 8><<<blocks, 256, 0, st>>>(g.ell_col, g.ell_deg, a.M, w.hd, Fp, unf);
+                k_syn_hd<V, 8><<<gs, 256, 0, st>>>(g.ell_col, g.ell_deg, a.M, w.hd, Fp, ubits);
             else
-                k_syn_hd<V, 16><<<blocks, 256, 0, st>>>(g.ell_col, g.ell_deg, a.M, w.hd, Fp, unf);
+                k_syn_hd<V, 16><<<gs, 256, 0, st>>>(g.ell_col, g.ell_deg, a.M, w.hd, Fp, ubits);
             syn_done = true;
         }
     }
@@ -1633,7 +1654,7 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
         k_store<MODE><<<dim3((a.N + kStoreTJ - 1) / kStoreTJ, Fp / kStoreTF), 256, 0, st>>>(
             s, Fp, a.N, w.pos2frame, w.comp, a.out_bits, a.out_soft, a.paper_slicer);
     k_finish<<<(Fp + 255) / 256, 256, 0, st>>>(w.done_iter, w.pos2frame, w.comp, unf, Fp, a.L,
-                                               a.out_iters, a.out_ok);
+                                               a.out_iters, a.out_ok, ubits);
     launches += 3;
     if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
     return launches;
