@@ -29,6 +29,19 @@ __device__ __forceinline__ uint32_t p_add(uint32_t a, uint32_t b) {  // lane-wis
 __device__ __forceinline__ uint32_t p_neg(uint32_t a) { return p_add(~a, 0x00010001u); }
 __device__ __forceinline__ int32_t p_lo(uint32_t w) { return (int32_t)(int16_t)(w & 0xffffu); }
 __device__ __forceinline__ int32_t p_hi(uint32_t w) { return (int32_t)w >> 16; }
+// acc + the low (p_acc_lo) or high (p_acc_hi) lane of w, or minus it (p_sub_lo, p_sub_hi):
+// one two-way 16 x 8-bit dot product (dp2a) with the byte weights (1, 0), (0, 1), (-1, 0)
+// or (0, -1); it extracts, sign-extends and adds in one instruction. Exact in int32.
+template <int B>
+__device__ __forceinline__ int32_t p_dot(int32_t acc, uint32_t w) {
+    int32_t d;
+    asm("dp2a.lo.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(w), "r"(B), "r"(acc));
+    return d;
+}
+__device__ __forceinline__ int32_t p_acc_lo(int32_t acc, uint32_t w) { return p_dot<0x0001>(acc, w); }
+__device__ __forceinline__ int32_t p_acc_hi(int32_t acc, uint32_t w) { return p_dot<0x0100>(acc, w); }
+__device__ __forceinline__ int32_t p_sub_lo(int32_t acc, uint32_t w) { return p_dot<0x00ff>(acc, w); }
+__device__ __forceinline__ int32_t p_sub_hi(int32_t acc, uint32_t w) { return p_dot<0xff00>(acc, w); }
 // Both lanes saturated to [-32767, 32767] and packed (lo in the low half).
 __device__ __forceinline__ uint32_t p_pack_sat(int32_t lo, int32_t hi) {
     uint32_t d;

@@ -790,8 +790,8 @@ __device__ __forceinline__ void col_fixed_packed(const Idx& ix, Words<FT / 2>* s
         ev[t] = slots[sl[t]];
 #pragma unroll
         for (int p = 0; p < P; p++) {
-            lo[p] += p_lo(ev[t].w[p]);
-            hi[p] += p_hi(ev[t].w[p]);
+            lo[p] = p_acc_lo(lo[p], ev[t].w[p]);
+            hi[p] = p_acc_hi(hi[p], ev[t].w[p]);
         }
     }
     WT out;
@@ -833,8 +833,8 @@ __device__ __forceinline__ void col_any_packed(const Idx& ix, Words<FT / 2>* slo
         const WT ev = slots[ix.c_slot[base + 32 * t]];
 #pragma unroll
         for (int p = 0; p < P; p++) {
-            lo[p] += p_lo(ev.w[p]);
-            hi[p] += p_hi(ev.w[p]);
+            lo[p] = p_acc_lo(lo[p], ev.w[p]);
+            hi[p] = p_acc_hi(hi[p], ev.w[p]);
         }
     }
     WT out;

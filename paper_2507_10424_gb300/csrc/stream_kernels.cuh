@@ -575,7 +575,7 @@ __device__ __forceinline__ uint32_t row_update(Row& row, int d, typename Tr<MODE
                     const uint32_t sw = sv.w[p];
                     if (SYN) zx[p] ^= PAPER ? p_neg(sw) : sw;
                     const uint32_t l =
-                        FIRST ? sw : p_pack_sat(p_lo(sw) - p_lo(ev.w[p]), p_hi(sw) - p_hi(ev.w[p]));
+                        FIRST ? sw : p_pack_sat(p_sub_lo(p_acc_lo(0, sw), ev.w[p]), p_sub_hi(p_acc_hi(0, sw), ev.w[p]));
                     const uint32_t m = p_max(l, p_neg(l));
                     min1[p] = p_min(min1[p], p_max(min0[p], m));
                     min0[p] = p_min(min0[p], m);
