@@ -74,6 +74,14 @@ struct PackedPick {
         n1 = p_cneg(min1, pm);
         m0p1 = p_neg(p_add(min0, 0x00010001u));
     }
+    // The same, picking the negated messages (-eta): the candidates negated once per row,
+    // since the conditional negation of -x is minus that of x.
+    __device__ __forceinline__ void set_neg(uint32_t min0, uint32_t min1, uint32_t sx) {
+        const uint32_t pm = ~p_signmask(sx);
+        n0 = p_cneg(min0, pm);
+        n1 = p_cneg(min1, pm);
+        m0p1 = p_neg(p_add(min0, 0x00010001u));
+    }
     __device__ __forceinline__ uint32_t operator()(uint32_t lam) const {
         const uint32_t sm = p_signmask(lam);
         const uint32_t eq = p_signmask(p_add(p_cneg(lam, sm), m0p1));

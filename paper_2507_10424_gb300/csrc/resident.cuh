@@ -418,9 +418,9 @@ __device__ __forceinline__ void row_fixed_packed(const Idx& ix, Words<FT / 2>* s
             sx[p] ^= lam;
         }
     }
-    PackedPick pk[P];
+    PackedPick pk[P];  // the slots take -eta (the column pass's sums and lambda use it so)
 #pragma unroll
-    for (int p = 0; p < P; p++) pk[p].set(min0[p], min1[p], sx[p]);
+    for (int p = 0; p < P; p++) pk[p].set_neg(min0[p], min1[p], sx[p]);
 #pragma unroll
     for (int t = 0; t < DC; t++) {
         WT out;
@@ -546,14 +546,14 @@ __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>:
 // Fixed point with an even number of interleaved frames: the int16 values of two frames
 // share a 32-bit word (frame 2p in the low half, 2p + 1 in the high half) and the passes
 // work on the pair at once with the packed 16-bit min / max / add instructions. Every
-// step is exact, so the results are those of the per-frame code:
-//   lambda = sat(s - eta): two 32-bit differences, saturated and packed by one
-//            conversion (to [-32768, 32767]), then max with -32767 (symmetric limit);
+// step is exact, so the results are those of the per-frame code. The row pass reads
+// lambda = sat(s - eta) from the slots (formed by the column pass, PackedLam) and writes
+// the negated new messages -eta back:
 //   |lambda| = max(lambda, -lambda), -x = ~x + 1 lane by lane;
 //   min0, min1, the XOR of the words (the sign bits of both lanes), as before;
-//   sweep 2: magnitude min1 where |lambda| = min0 (|lambda| - min0 >= 0, so
-//            min(|lambda| - min0, 1) is 0 there and 1 elsewhere), conditional negation
-//            by (m ^ mask) + (mask & 1) with the lane mask of the new sign.
+//   sweep 2: magnitude min1 where |lambda| = min0 (|lambda| - min0 - 1 < 0), the row's
+//            sign parity and the negation folded into the two candidates once per row,
+//            and lambda's own sign applied by (m ^ mask) + (mask & 1) (PackedPick).
 // ---------------------------------------------------------------------------------------
 template <int FT, bool UNROLL = true, typename SY>
 __device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT>* slots_v,
@@ -596,9 +596,9 @@ __device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT
                 sx[p] ^= lam;
             }
         }
-        PackedPick pk[P];
+        PackedPick pk[P];  // the slots take -eta
 #pragma unroll
-        for (int p = 0; p < P; p++) pk[p].set(min0[p], min1[p], sx[p]);
+        for (int p = 0; p < P; p++) pk[p].set_neg(min0[p], min1[p], sx[p]);
 #pragma unroll UNR
         for (int t = 0; t < d; t++) {
             const int slot = base + 32 * t;
@@ -750,23 +750,25 @@ __device__ __forceinline__ void col_any(const Idx& ix, VecR<typename RT<MODE>::T
     }
 }
 
-// Packed fixed point: 32-bit sums, saturated and packed at the end, then lambda =
-// sat(s - eta) lane by lane without leaving the packed form. With s, eta in [-32767, 32767],
-// clamping eta to [max(s, 0) - 32767, min(s, 0) + 32767] (both bounds representable) makes
-// s - eta' equal to sat(s - eta) exactly: eta is raised only when s >= 0 and
-// s - eta > 32767, lowered only when s <= 0 and s - eta < -32767, and otherwise the
-// difference is already within the limits. s - eta' = (s + 1) + ~eta' is formed with
-// wrapping adds, exact because the result is in range. Per column: the bounds and s + 1;
-// per edge: max, min, not, add.
+// Packed fixed point: the slots hold the negated messages ne = -eta between the row and
+// the column pass (the row pass negates its two candidate magnitudes once per row). The
+// column pass sums s = r - sum(ne) in 32 bits (one dp2a per lane and edge), saturates and
+// packs, then forms lambda = sat(s - eta) = sat(s + ne) lane by lane without leaving the
+// packed form. With s, ne in [-32767, 32767], clamping ne to
+// [-32767 - min(s, 0), 32767 - max(s, 0)] (both bounds representable) makes s + ne' equal to
+// sat(s + ne) exactly: ne is raised only when s < 0 and s + ne < -32767, lowered only when
+// s > 0 and s + ne > 32767, and otherwise the sum is already within the limits; the wrapping
+// packed add is exact because the result is in range. Per column: the two bounds; per edge:
+// max, min, add.
 struct PackedLam {
-    uint32_t lo = 0, hi = 0, s1 = 0;
-    __device__ __forceinline__ void set(uint32_t sw) {
-        lo = p_add(p_max(sw, 0u), 0x80018001u);  // max(s, 0) - 32767
-        hi = p_add(p_min(sw, 0u), 0x7fff7fffu);  // min(s, 0) + 32767
-        s1 = p_add(sw, 0x00010001u);
+    uint32_t lo = 0, hi = 0, sw = 0;
+    __device__ __forceinline__ void set(uint32_t s) {
+        sw = s;
+        lo = p_add(~p_min(s, 0u), 0x80028002u);  // -32767 - min(s, 0) = ~min(s, 0) - 32766
+        hi = p_add(~p_max(s, 0u), 0x80008000u);  // 32767 - max(s, 0) = ~max(s, 0) + 32768 (mod 2^16)
     }
-    __device__ __forceinline__ uint32_t operator()(uint32_t ew) const {
-        return p_add(s1, ~p_min(p_max(ew, lo), hi));
+    __device__ __forceinline__ uint32_t operator()(uint32_t ne) const {
+        return p_add(sw, p_min(p_max(ne, lo), hi));
     }
 };
 
@@ -790,8 +792,8 @@ __device__ __forceinline__ void col_fixed_packed(const Idx& ix, Words<FT / 2>* s
         ev[t] = slots[sl[t]];
 #pragma unroll
         for (int p = 0; p < P; p++) {
-            lo[p] = p_acc_lo(lo[p], ev[t].w[p]);
-            hi[p] = p_acc_hi(hi[p], ev[t].w[p]);
+            lo[p] = p_sub_lo(lo[p], ev[t].w[p]);  // the slots hold -eta
+            hi[p] = p_sub_hi(hi[p], ev[t].w[p]);
         }
     }
     WT out;
@@ -833,8 +835,8 @@ __device__ __forceinline__ void col_any_packed(const Idx& ix, Words<FT / 2>* slo
         const WT ev = slots[ix.c_slot[base + 32 * t]];
 #pragma unroll
         for (int p = 0; p < P; p++) {
-            lo[p] = p_acc_lo(lo[p], ev.w[p]);
-            hi[p] = p_acc_hi(hi[p], ev.w[p]);
+            lo[p] = p_sub_lo(lo[p], ev.w[p]);  // the slots hold -eta
+            hi[p] = p_sub_hi(hi[p], ev.w[p]);
         }
     }
     WT out;

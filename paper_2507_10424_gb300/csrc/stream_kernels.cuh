@@ -1147,6 +1147,18 @@ __global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col
                 acc[v] = acc[v] + (A)cmsg_signed(m, w.x[v], tp);
             }
         }
+    } else if constexpr (MODE == kModeFixed && V % 2 == 0) {
+        // int16 pairs: each lane of a word added by one two-way dot product (dp2a)
+        using VW32 = Words<V / 2>;
+        for (int t = t0; t < t1; t++) {
+            const int e = __ldg(col_edge + t);
+            const VW32 ev = *reinterpret_cast<const VW32*>(eta + (size_t)e * Fp + f0);
+#pragma unroll
+            for (int p = 0; p < V / 2; p++) {
+                acc[2 * p] = p_acc_lo(acc[2 * p], ev.w[p]);
+                acc[2 * p + 1] = p_acc_hi(acc[2 * p + 1], ev.w[p]);
+            }
+        }
     } else {
         for (int t = t0; t < t1; t++) {
             const int e = __ldg(col_edge + t);
@@ -1164,13 +1176,20 @@ __global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col
     }
     T* sp = s + (size_t)j * Fp + f0;
     if (upd == (1u << V) - 1u) {
-        VT out;
+        if constexpr (MODE == kModeFixed && V % 2 == 0) {  // saturated and packed in pairs
+            Words<V / 2> out;
 #pragma unroll
-        for (int v = 0; v < V; v++) {
-            if (MODE == kModeFP32) out.x[v] = (T)acc[v];
-            else out.x[v] = (T)sat16((int32_t)acc[v]);
+            for (int p = 0; p < V / 2; p++) out.w[p] = p_pack_sat((int32_t)acc[2 * p], (int32_t)acc[2 * p + 1]);
+            *reinterpret_cast<Words<V / 2>*>(sp) = out;
+        } else {
+            VT out;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                if (MODE == kModeFP32) out.x[v] = (T)acc[v];
+                else out.x[v] = (T)sat16((int32_t)acc[v]);
+            }
+            *reinterpret_cast<VT*>(sp) = out;
         }
-        *reinterpret_cast<VT*>(sp) = out;
     } else {
 #pragma unroll
         for (int v = 0; v < V; v++)
