@@ -622,30 +622,6 @@ int ldpc_decode_host(ldpc_t* h, const void* llr_host, int32_t llr_dtype, int32_t
         } else {  // too few frames for a ramp: even chunks
             for (; left > 0; left -= std::min(chunk, left)) sizes.push_back(std::min(chunk, left));
         }
-        // Resident decodes without early stop run in waves of equal tiles (CTAs resident on
-        // the SMs x frames per tile): every chunk but the last is rounded to whole waves, so
-        // that only the last one ends on a partial wave (each partial wave leaves SMs idle).
-        const ResidentPlan& rp = h->plan[h->mode];
-        if (!early_stop && resolved_variant(h) == LDPC_VARIANT_RESIDENT && rp.ok && sizes.size() > 1) {
-            int per_sm = 0, smem_sm = 0;
-            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
-            per_sm = std::min(2048 / std::max(1, rp.threads), (int)(smem_sm / (rp.smem + 1024)));
-            const int64_t wave = (int64_t)std::max(1, per_sm) * h->num_sms * rp.FT;
-            std::vector<int32_t> rounded;
-            int64_t used = 0;
-            for (size_t i = 0; wave <= chunk && i + 1 < sizes.size(); i++) {
-                int64_t c = (sizes[i] + wave / 2) / wave * wave;  // nearest whole number of waves
-                if (c > chunk) c -= wave;                         // within the staging buffers
-                c = std::max<int64_t>(c, wave);
-                rounded.push_back((int32_t)c);
-                used += c;
-            }
-            // the last chunk keeps the remainder (kept only when it fits the buffers too)
-            if (rounded.size() + 1 == sizes.size() && used < frames && frames - used <= chunk) {
-                rounded.push_back((int32_t)(frames - used));
-                sizes = rounded;
-            }
-        }
     }
     const size_t per_frame = (size_t)N * in_b + (size_t)N + 4 + 1 + (soft_host ? (size_t)N * 4 : 0);
     const size_t need = ((size_t)chunk * per_frame + 4096);
