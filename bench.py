@@ -797,7 +797,10 @@ def main():
         del xd
         result["e2e"]["link"] = {"h2d_ms": h2d_ms, "h2d_GBs": xh.numel() * 4 / h2d_ms / 1e6,
                                  "d2h_ms": d2h_ms, "d2h_GBs": bh.numel() / d2h_ms / 1e6}
-    if not args.quick and args.workload == "qc2304":
+    # The extra measurements are single-GPU records: they run at N=1 only (under torchrun the
+    # rank-0-only parts would otherwise enter the timer's collectives alone, and every GPU
+    # would be held while one of them works).
+    if not args.quick and args.workload == "qc2304" and world == 1:
         # the other arithmetic mode and the other kernel variant, same workload
         others = {}
         for m2, v2 in (("fixed" if mode == "fp32" else "fp32", "auto"), (mode, "stream")):
