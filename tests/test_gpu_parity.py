@@ -319,6 +319,45 @@ def test_every_resident_launch_shape(torch_cuda, mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
+def test_every_resident_launch_shape_small_code(torch_cuda, mode):
+    """The same on the (3,6)-regular N=576 code, whose tiles of 4 FP32 frames fit shared
+    memory: the early-stop kernels that read per-slot decision bytes (fixed point, and FP32
+    tiles of 4 frames) in every frames-per-tile and CTA size, with the syndrome tested every
+    iteration and every third (the column pass writes the bytes only before a tested
+    iteration)."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
+    code = inputs.cfg_regular_576()
+    F = 203
+    snr = np.random.default_rng(8).permutation(np.linspace(1.5, 6.0, F))
+    llr = np.concatenate([inputs.all_zero_awgn_llr(1, code.N, float(snr[k]), code.design_rate, 700 + k)
+                          for k in range(F)])
+    llr[[5, 150]] = 3.0  # codewords at the input
+    x = torch.from_numpy(llr).cuda()
+    tried = 0
+    for ce in (1, 3):
+        want = oracle_decode(code, llr, 14, mode, early_stop=True, check_every=ce)
+        assert len(np.unique(want[1])) >= 5
+        for ft in (1, 2, 4):
+            for th in (0, 96, 288, 512):
+                for ip in (1, 2):
+                    dec = Decoder.from_code(code, mode=mode)
+                    dec.set_variant("resident")
+                    try:
+                        dec.set_tuning(ft, th, ip)
+                    except LdpcError:
+                        continue
+                    b, it, ok, sf = dec.decode(x, 14, early_stop=True, check_every=ce, want_ok=True,
+                                               want_soft=True)
+                    torch.cuda.synchronize()
+                    got = (b.cpu().numpy(), it.cpu().numpy(), ok.cpu().numpy(), sf.cpu().numpy())
+                    assert_parity(got, want, mode, f"FT={ft} threads={th} index={ip} check_every={ce}")
+                    tried += 1
+                    dec.close()
+    assert tried >= 30
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_autotune_keeps_results(torch_cuda, mode):
     torch = torch_cuda
     from paper_2507_10424_gb300.ldpc import Decoder
