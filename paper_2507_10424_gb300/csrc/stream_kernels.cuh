@@ -1132,7 +1132,9 @@ __global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col
             wb = __ldg(wt.beta + c);
         }
         const int tmask = (1 << dshift) - 1;
-#pragma unroll 4
+        // Not unrolled: at the 32-register bound each further edge in flight (three 16-byte
+        // row-state loads) spilled, and the spills cost 4 % of the whole decode.
+#pragma unroll 1
         for (int t = t0; t < t1; t++) {
             const int slot = __ldg(col_edge + t);
             const size_t o = (size_t)(slot >> dshift) * Fp + f0;
