@@ -308,9 +308,10 @@ struct RowSyn {
 
 // One row of exactly DC edges, per frame: the row's lambdas are read once into registers
 // (fully unrolled), then the new messages are written.
+// W: the learned decoder with a single weight class (alpha = wa, beta = wb for every edge).
 template <int MODE, int FT, bool W, int DC, typename SY>
 __device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
-                                          int base, SY& sy) {
+                                          int base, SY& sy, float wa = 1.0f, float wb = 0.0f) {
     using T = typename RT<MODE>::T;
     using A = typename RT<MODE>::A;
     using VT = VecR<T, FT>;
@@ -350,12 +351,20 @@ __device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>:
             sx[f] ^= bits_of(lam);
         }
     }
-    if constexpr (MODE == kModeFP32 && !W) {
+    if constexpr (MODE == kModeFP32) {
+        // the two candidate magnitudes, weighted once per row when W: max(fma(alpha, m,
+        // -beta), 0) of min0 and of min1 is what each edge would get from its own pick
         float p0[FT], p1[FT];
 #pragma unroll
         for (int f = 0; f < FT; f++) {
-            p0[f] = with_sign((float)min0[f], sx[f]);
-            p1[f] = with_sign((float)min1[f], sx[f]);
+            float c0 = (float)min0[f], c1 = (float)min1[f];
+            if constexpr (W) {
+                const float x0 = __fmaf_rn(wa, c0, -wb), x1 = __fmaf_rn(wa, c1, -wb);
+                c0 = x0 > 0.0f ? x0 : 0.0f;
+                c1 = x1 > 0.0f ? x1 : 0.0f;
+            }
+            p0[f] = with_sign(c0, sx[f]);
+            p1[f] = with_sign(c1, sx[f]);
         }
 #pragma unroll
         for (int t = 0; t < DC; t++) {
@@ -365,24 +374,15 @@ __device__ __forceinline__ void row_fixed(const Idx& ix, VecR<typename RT<MODE>:
             slots[base + 32 * t] = out;
         }
     } else {
+        static_assert(!W, "learned weights are FP32");
 #pragma unroll
         for (int t = 0; t < DC; t++) {
             const int slot = base + 32 * t;
-            float wa = 1.0f, wb = 0.0f;
-            if constexpr (W) {
-                const int c = ix.wcls[slot];
-                wa = ix.walpha[c];
-                wb = ix.wbeta[c];
-            }
             VT out;
 #pragma unroll
             for (int f = 0; f < FT; f++) {
                 const A lam = (A)lv[t].x[f];
-                A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
-                if constexpr (W) {  // max(fma(alpha, m, -beta), 0)
-                    const float x = __fmaf_rn(wa, (float)m, -wb);
-                    m = (A)(x > 0.0f ? x : 0.0f);
-                }
+                const A m = (rabs(lam) == min0[f]) ? min1[f] : min0[f];
                 out.x[f] = (T)with_sign(m, bits_of(lam) ^ sx[f]);
             }
             slots[slot] = out;
@@ -454,14 +454,24 @@ __device__ __forceinline__ bool by_degree(int d, Body&& body) {
 
 // Row pass, per frame. Rows too long for an unrolled body read lambda twice (two sweeps);
 // every row's slots end up holding the new messages. sy: the syndrome gather riding along.
+// W1 (with W): the code has a single weight class, so the weights apply to the row's two
+// candidate magnitudes once and the rows take the unrolled bodies; with several classes the
+// weights are looked up per edge in the loop form.
 template <int MODE, int FT, bool W, bool UNROLL = true, typename SY>
 __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>::T, FT>* slots,
-                                          int n_rtasks, SY&& sy) {
+                                          int n_rtasks, SY&& sy, bool w1 = false) {
     using T = typename RT<MODE>::T;
     using A = typename RT<MODE>::A;
     using VT = VecR<T, FT>;
     constexpr int UNR = FT >= 4 ? 2 : 4;
     const int nth = blockDim.x;
+    float wa1 = 1.0f, wb1 = 0.0f;
+    if constexpr (W) {
+        if (w1) {
+            wa1 = ix.walpha[0];
+            wb1 = ix.wbeta[0];
+        }
+    }
     for (int k = 0;; k++) {
         const int task = snake(k, nth);  // strictly increasing in k
         if (task >= n_rtasks) break;
@@ -469,8 +479,8 @@ __device__ __forceinline__ void rows_pass(const Idx& ix, VecR<typename RT<MODE>:
         if (d == 0) continue;
         const int base = ix.r_base[task >> 5] + (task & 31);
         if constexpr (UNROLL) {
-            if (by_degree<row_body_max<MODE, FT>()>(d, [&](auto dc) {
-                    row_fixed<MODE, FT, W, decltype(dc)::value>(ix, slots, base, sy);
+            if ((!W || w1) && by_degree<row_body_max<MODE, FT>()>(d, [&](auto dc) {
+                    row_fixed<MODE, FT, W, decltype(dc)::value>(ix, slots, base, sy, wa1, wb1);
                 }))
                 continue;
         }
@@ -930,9 +940,11 @@ __device__ __forceinline__ void copy_to_smem(T* dst, const T* src, int n) {
 // eta, s and r at the given addresses (shared memory, or a CTA's slot of global scratch),
 // ending with the decisions of every frame written out. unsat_w: two words reset to 0.
 // UNROLL: the fully unrolled row and column bodies (false in kernels that inline several
-// tile shapes and would exceed their register budget). Weighted rows always take the loop
-// form: unrolled, their per-edge class and weight loads raised the early-stop kernels to
-// the 64-register bound, which costs small tiles resident CTAs per SM.
+// tile shapes and would exceed their register budget). Weighted rows take the unrolled
+// bodies only when the code has one weight class (the weights then act on the row's two
+// candidate magnitudes); with several classes they take the loop form: unrolled, their
+// per-edge class and weight loads raised the early-stop kernels to the 64-register bound,
+// which costs small tiles resident CTAs per SM.
 // ES (early-stop kernels): the row pass of iteration k + 1 also gathers the syndrome of s
 // after iteration k, which s still holds until the column pass, so a tested iteration
 // costs no pass of its own; the frames that are codewords are written out between the
@@ -993,8 +1005,9 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
                 rows_pass_packed<FT, UNROLL>(ix, eta, n_rtasks,
                                              RowSyn<MODE, FT, PAPER, true, DEC>(s, &unsat_w[par], dec));
             else
-                rows_pass<MODE, FT, W, UNROLL && !W>(ix, eta, n_rtasks,
-                                               RowSyn<MODE, FT, PAPER, true, DEC>(s, &unsat_w[par], dec));
+                rows_pass<MODE, FT, W, UNROLL>(ix, eta, n_rtasks,
+                                               RowSyn<MODE, FT, PAPER, true, DEC>(s, &unsat_w[par], dec),
+                                               W && a.n_classes == 1);
             __syncthreads();
             const uint32_t conv = active & ~unsat_w[par];
             if (conv) {  // s still holds the decisions of iteration k
@@ -1008,8 +1021,9 @@ __device__ __forceinline__ void decode_tile(const ResArgs& a, Idx ix, VT* eta, V
                 rows_pass_packed<FT, UNROLL>(ix, eta, n_rtasks,
                                              RowSyn<MODE, FT, PAPER, false>(s, nullptr));
             else
-                rows_pass<MODE, FT, W, UNROLL && !W>(ix, eta, n_rtasks,
-                                               RowSyn<MODE, FT, PAPER, false>(s, nullptr));
+                rows_pass<MODE, FT, W, UNROLL>(ix, eta, n_rtasks,
+                                               RowSyn<MODE, FT, PAPER, false>(s, nullptr),
+                                               W && a.n_classes == 1);
             __syncthreads();  // (also orders emit's reads of s before the column pass rewrites s)
         }
         if constexpr (DEC) {  // decision bytes only before an iteration that tests the syndrome

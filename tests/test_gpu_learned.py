@@ -59,6 +59,43 @@ def test_weighted_decode_matches_oracle(torch_cuda, variant, early_stop):
         dec.close()
 
 
+@pytest.mark.parametrize("shape", ["2,768,1", "4,768,1", "1,256,1", "1,1024,2", "2,384,2"])
+@pytest.mark.parametrize("early_stop", [True, False])
+def test_one_class_weights_over_resident_shapes(torch_cuda, shape, early_stop):
+    """A regular code has one weight class, so the resident rows apply the weights to their
+    two candidate magnitudes once (the unrolled row bodies) instead of per edge. Every
+    launch shape, with and without early stop (tested every iteration and every third),
+    must equal the oracle's weighted decode bit for bit, posteriors included."""
+    torch = torch_cuda
+    from paper_2507_10424_gb300.ldpc import Decoder, LdpcError
+    code = inputs.cfg_regular_576()
+    cls, degrees = oracle.column_classes(code)
+    assert len(degrees) == 1
+    a, b = random_weights(7, 1, 13)
+    llr = inputs.all_zero_awgn_llr(259, code.N, 2.5, code.design_rate, 17)
+    g = oracle.Graph.from_code(code)
+    dec = Decoder.from_code(code)
+    dec.set_weights(a, b)
+    dec.set_variant("resident")
+    ft, th, ip = (int(v) for v in shape.split(","))
+    try:
+        dec.set_tuning(ft, th, ip)
+    except LdpcError:
+        pytest.skip(f"{shape} does not fit this code")
+    x = torch.from_numpy(llr).cuda()
+    for check_every in ((1, 3) if early_stop else (1,)):
+        bits, it, ok, soft = dec.decode(x, 12, early_stop=early_stop, check_every=check_every,
+                                        want_ok=True, want_soft=True)
+        torch.cuda.synchronize()
+        wb, wi, wok, ws = oracle.decode_weighted_f32(g, llr, 12, cls, a, b, early_stop=early_stop,
+                                                     check_every=check_every)
+        assert (it.cpu().numpy() == wi).all() and (ok.cpu().numpy() == wok).all()
+        assert (bits.cpu().numpy() == wb).all()
+        assert (soft.cpu().numpy() == ws).all(), (shape, early_stop, check_every)
+    assert wi.max() > 1
+    dec.close()
+
+
 @pytest.mark.parametrize("variant", ["stream", "resident", "cluster"])
 def test_unit_weights_equal_plain_on_gpu(torch_cuda, variant):
     torch = torch_cuda
