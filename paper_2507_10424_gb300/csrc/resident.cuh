@@ -205,15 +205,19 @@ __device__ __forceinline__ int snake(int k, int nth) {
 // Largest row / column degree whose fully unrolled body keeps its operands in registers:
 // about 32 (FP32 rows), 24 (fixed-point rows: the packed sweeps need more temporaries) or
 // 30 (columns: slot ids too) registers of operands, at FT x sizeof(T) / 4 registers per
-// edge vector. (Within the 64 registers of a 1024-thread CTA, without spills.)
+// edge vector. (Within the 64 registers of a 1024-thread CTA.) Fixed-point rows that also
+// gather the syndrome (SYN) take 32 registers of operands: measured on the QC N=2304 batch
+// with early stop, 4-frame tiles, rows of 13-16 edges unrolled instead of read twice by the
+// loop form: 7.82 -> 7.53 ms, although the kernel then spills a few words; without the
+// syndrome the same bodies were slower (6.59 -> 6.68 ms).
 template <int MODE, int FT>
 __host__ __device__ constexpr int vec_regs() {
     return (FT * (MODE == kModeFP32 ? 4 : 2) + 3) / 4;
 }
-template <int MODE, int FT>
+template <int MODE, int FT, bool SYN = true>
 __host__ __device__ constexpr int row_body_max() {
-    return (MODE == kModeFP32 ? 32 : 24) / vec_regs<MODE, FT>() < 16
-               ? (MODE == kModeFP32 ? 32 : 24) / vec_regs<MODE, FT>()
+    return (MODE == kModeFP32 || SYN ? 32 : 24) / vec_regs<MODE, FT>() < 16
+               ? (MODE == kModeFP32 || SYN ? 32 : 24) / vec_regs<MODE, FT>()
                : 16;
 }
 template <int MODE, int FT>
@@ -265,6 +269,7 @@ __device__ __forceinline__ uint32_t dec_byte_packed(const Words<P>& w) {
 // instead of a position index and a gathered posterior vector.
 template <int MODE, int FT, bool PAPER, bool ON, bool DEC = false>
 struct RowSyn {
+    static constexpr bool kOn = ON;
     const VecR<typename RT<MODE>::T, FT>* s;
     uint32_t* unsat_w;
     const uint8_t* dec;
@@ -580,7 +585,7 @@ __device__ __forceinline__ void rows_pass_packed(const Idx& ix, VecR<int16_t, FT
         if (d == 0) continue;
         const int base = ix.r_base[task >> 5] + (task & 31);
         if constexpr (UNROLL) {
-            if (by_degree<row_body_max<kModeFixed, FT>()>(d, [&](auto dc) {
+            if (by_degree<row_body_max<kModeFixed, FT, std::decay_t<SY>::kOn>()>(d, [&](auto dc) {
                     row_fixed_packed<FT, decltype(dc)::value>(ix, slots, base, sy);
                 }))
                 continue;
