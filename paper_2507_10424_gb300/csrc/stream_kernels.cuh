@@ -855,6 +855,7 @@ struct StagedArgs {
     const uint8_t* state;
     uint8_t* unsat;
     int32_t* err;
+    const int32_t* comp;  // [1]: positions in use (frame blocks behind them get no task)
 };
 
 // Shared memory of one warp: S stages of [D s chunks][D message chunks], each chunk
@@ -894,7 +895,9 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
     static_assert(LY::kChunk % 16 == 0, "bulk copies move multiples of 16 bytes");
     extern __shared__ __align__(128) unsigned char smem_st[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int S = a.stages, M = a.M, NB = a.n_fblocks;
+    const int S = a.stages, M = a.M;
+    // the frame blocks in use: after a frame compaction the running frames sit at the front
+    const int NB = min(a.n_fblocks, (__ldcg(a.comp + 1) + 32 * VW - 1) / (32 * VW));
     unsigned char* const buf = smem_st + (size_t)warp * S * LY::kStage;
     unsigned char* const meta = smem_st + (size_t)nw * S * LY::kStage + (size_t)warp * S * LY::kMeta;
     uint64_t* const bar = reinterpret_cast<uint64_t*>(smem_st + (size_t)nw * S * (LY::kStage + LY::kMeta)) +
@@ -1068,18 +1071,18 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_check_staged(const Staged
 // by bandwidth: it runs at 16 blocks of 128 threads per SM (all 64 warps, at most 32
 // registers), which measured faster than fewer, larger-register warps (N=64800 FP32 with
 // compressed messages: 102 -> 96.5 ms per 4096-frame, 50-iteration decode).
-template <int MODE, int VW = Tr<MODE>::V, bool CMP = false, bool W = false, bool HD = false>
-__global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col_ptr,
-                                             const int32_t* __restrict__ col_edge, int N,
-                                             const typename Tr<MODE>::R* __restrict__ r,
-                                             typename Tr<MODE>::T* s,
-                                             const typename Tr<MODE>::T* __restrict__ eta, int Fp,
-                                             uint8_t* state, int32_t* done_iter,
-                                             const int32_t* __restrict__ pos2frame,
-                                             const uint8_t* __restrict__ unsat, int test_prev,
-                                             int k, int* n_done, int frames, CState cs = CState{},
-                                             int dshift = 0, IterWeights wt = IterWeights(),
-                                             uint8_t* hd = nullptr, int paper = 0) {
+// One task: column j for the V frames at positions f0 .. f0 + V - 1.
+template <int MODE, int VW, bool CMP, bool W, bool HD>
+__device__ __forceinline__ void var_task(int j, int f0, const int32_t* __restrict__ col_ptr,
+                                         const int32_t* __restrict__ col_edge,
+                                         const typename Tr<MODE>::R* __restrict__ r,
+                                         typename Tr<MODE>::T* s,
+                                         const typename Tr<MODE>::T* __restrict__ eta, int Fp,
+                                         uint8_t* state, int32_t* done_iter,
+                                         const int32_t* __restrict__ pos2frame,
+                                         const uint8_t* __restrict__ unsat, int test_prev, int k,
+                                         int* n_done, const CState& cs, int dshift,
+                                         const IterWeights& wt, uint8_t* hd, int paper) {
     using T = typename Tr<MODE>::T;
     using R = typename Tr<MODE>::R;
     using A = typename Tr<MODE>::A;
@@ -1087,11 +1090,6 @@ __global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col
     using VT = Vec<T, V>;
     using VR = Vec<R, V>;
     using VS = Vec<uint8_t, V>;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int j = blockIdx.x * 4 + warp;
-    const int f0 = (blockIdx.y * 32 + lane) * V;
-    if (j >= N) return;
-    if (*(volatile const int*)n_done >= frames) return;
     const VS st = *reinterpret_cast<const VS*>(state + f0);
     uint32_t act = 0;
 #pragma unroll
@@ -1196,6 +1194,59 @@ __global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col
 #pragma unroll
         for (int v = 0; v < V; v++)
             if ((upd >> v) & 1) sp[v] = (MODE == kModeFP32) ? (T)acc[v] : (T)sat16((int32_t)acc[v]);
+    }
+}
+
+// The bit pass over the positions in use (comp[1]: after a frame compaction the running
+// frames sit at the front): tasks t = y G + c, column group c (4 columns, one per warp) of
+// frame block y (32 lanes x V frames).
+// Per-edge messages: a grid of at most as many CTAs as fit the GPU at once takes the tasks
+// in steps of the grid size, so frame blocks behind the positions in use get no CTA at all.
+// Compressed messages (CMP): one CTA per task (grid G x frame blocks), which the hardware
+// starts in task order; the gathered row states of a frame block are then reused in L2 by
+// the CTAs running together (CTAs that loop over strided tasks drift apart and measured
+// 20 % slower on the N=64800 code), and a CTA behind the positions in use returns at once.
+template <int MODE, int VW = Tr<MODE>::V, bool CMP = false, bool W = false, bool HD = false>
+__global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col_ptr,
+                                             const int32_t* __restrict__ col_edge, int N,
+                                             const typename Tr<MODE>::R* __restrict__ r,
+                                             typename Tr<MODE>::T* s,
+                                             const typename Tr<MODE>::T* __restrict__ eta, int Fp,
+                                             uint8_t* state, int32_t* done_iter,
+                                             const int32_t* __restrict__ pos2frame,
+                                             const uint8_t* __restrict__ unsat, int test_prev,
+                                             int k, int* n_done, int frames, const int32_t* comp,
+                                             CState cs = CState{}, int dshift = 0,
+                                             IterWeights wt = IterWeights(), uint8_t* hd = nullptr,
+                                             int paper = 0) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int FB = 32 * VW;
+    if constexpr (CMP) {
+        const int j = blockIdx.x * 4 + warp, y = blockIdx.y;
+        if (j >= N || y * FB >= __ldcg(comp + 1)) return;
+        if (*(volatile const int*)n_done >= frames) return;
+        var_task<MODE, VW, CMP, W, HD>(j, (y * 32 + lane) * VW, col_ptr, col_edge, r, s, eta, Fp, state,
+                                       done_iter, pos2frame, unsat, test_prev, k, n_done, cs, dshift, wt,
+                                       hd, paper);
+        return;
+    }
+    if (*(volatile const int*)n_done >= frames) return;
+    const int nb = min(Fp / FB, (__ldcg(comp + 1) + FB - 1) / FB);
+    const int G = (N + 3) / 4;
+    const int step_y = (int)(gridDim.x / G), step_c = (int)(gridDim.x % G);
+    int y = (int)(blockIdx.x / G), c = (int)(blockIdx.x % G);
+    for (; y < nb;) {
+        const int j = c * 4 + warp;
+        if (j < N)
+            var_task<MODE, VW, CMP, W, HD>(j, (y * 32 + lane) * VW, col_ptr, col_edge, r, s, eta, Fp, state,
+                                           done_iter, pos2frame, unsat, test_prev, k, n_done, cs, dshift,
+                                           wt, hd, paper);
+        y += step_y;
+        c += step_c;
+        if (c >= G) {
+            c -= G;
+            y++;
+        }
     }
 }
 
@@ -1423,6 +1474,7 @@ bool launch_staged(const DevGraph& g, const DecodeArgs& a, const StreamWork& w,
     sa.state = w.state;
     sa.unsat = un;
     sa.err = w.err;
+    sa.comp = w.comp;
     kern<<<(int)ctas, threads, smem, st>>>(sa, s, eta, wt);
     return true;
 }
@@ -1544,14 +1596,14 @@ void var_pass(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, dim3 
         if (hd) {
             k_var<MODE, V, CMP, W, true><<<gv, 128, 0, st>>>(g.col_ptr, cslot, a.N, r, s, eta, w.Fp, w.state,
                                                              w.done_iter, w.pos2frame, un, test_prev, k,
-                                                             w.n_done, a.frames, cs, dshift, wt, w.hd,
-                                                             a.paper_slicer);
+                                                             w.n_done, a.frames, w.comp, cs, dshift, wt,
+                                                             w.hd, a.paper_slicer);
             return;
         }
     }
     k_var<MODE, V, CMP, W><<<gv, 128, 0, st>>>(g.col_ptr, cslot, a.N, r, s, eta, w.Fp, w.state, w.done_iter,
-                                               w.pos2frame, un, test_prev, k, w.n_done, a.frames, cs, dshift,
-                                               wt);
+                                               w.pos2frame, un, test_prev, k, w.n_done, a.frames, w.comp, cs,
+                                               dshift, wt);
 }
 
 template <int MODE, int V>
@@ -1572,7 +1624,13 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
     k_load<MODE><<<dim3((a.N + kLoadTJ - 1) / kLoadTJ, Fp / kLoadTF), 256, 0, st>>>(a.llr, a.llr_is_i8,
                                                                                       a.frames, a.N, r, s, Fp);
     launches++;
-    const dim3 gc((a.M + 3) / 4, Fp / (32 * V)), gv((a.N + 3) / 4, Fp / (32 * V));
+    const dim3 gc((a.M + 3) / 4, Fp / (32 * V));
+    // the bit pass (k_var): with per-edge messages at most as many CTAs as are resident (16
+    // per SM) loop over the tasks of the frame blocks in use; with compressed messages one
+    // CTA per task (column group x frame block)
+    const long long var_tasks = (long long)((a.N + 3) / 4) * (Fp / (32 * V));
+    const dim3 gv((unsigned)std::max(1ll, std::min(var_tasks, 16ll * (w.num_sms > 0 ? w.num_sms : 148))));
+    const dim3 gv_cmp((a.N + 3) / 4, Fp / (32 * V));
     // message slot of each edge in column order: padded-row slots or CSR edge ids
     const int32_t* cslot = g.ell_D ? g.ell_cslot : g.col_edge;
     // compressed messages (cmsg.cuh) where the mode, the layout and the staging allow
@@ -1610,10 +1668,10 @@ int run(const DevGraph& g, const DecodeArgs& a, const StreamWork& w, cudaStream_
                 if (ok) {
                     const CState cs = cstate_at(eta, a.M, Fp);
                     if (W)
-                        var_pass<MODE, V, true, true>(g, a, w, gv, g.ell_cslot, un, test_prev, k, hd && k == a.L,
+                        var_pass<MODE, V, true, true>(g, a, w, gv_cmp, g.ell_cslot, un, test_prev, k, hd && k == a.L,
                                                       cs, dshift, wt, st);
                     else
-                        var_pass<MODE, V, true, false>(g, a, w, gv, g.ell_cslot, un, test_prev, k, hd && k == a.L,
+                        var_pass<MODE, V, true, false>(g, a, w, gv_cmp, g.ell_cslot, un, test_prev, k, hd && k == a.L,
                                                        cs, dshift, wt, st);
                     launches += 2;
                     if (a.early_stop && k < a.L && k % kCompactEvery == 0 && w.comp)
