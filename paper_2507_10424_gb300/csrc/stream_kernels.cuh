@@ -1223,8 +1223,8 @@ __global__ void __launch_bounds__(128, 16) k_var(const int32_t* __restrict__ col
     constexpr int FB = 32 * VW;
     if constexpr (CMP) {
         const int j = blockIdx.x * 4 + warp, y = blockIdx.y;
-        if (j >= N || y * FB >= __ldcg(comp + 1)) return;
-        if (*(volatile const int*)n_done >= frames) return;
+        const int cur = __ldcg(comp + 1), done = *(volatile const int*)n_done;  // one round trip
+        if (j >= N || y * FB >= cur || done >= frames) return;
         var_task<MODE, VW, CMP, W, HD>(j, (y * 32 + lane) * VW, col_ptr, col_edge, r, s, eta, Fp, state,
                                        done_iter, pos2frame, unsat, test_prev, k, n_done, cs, dshift, wt,
                                        hd, paper);
