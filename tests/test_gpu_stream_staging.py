@@ -144,6 +144,28 @@ def test_frame_compaction_keeps_every_output(torch_cuda, mode, shape):
 
 
 @pytest.mark.parametrize("mode", ["fp32", "fixed"])
+@pytest.mark.parametrize("shape", [(0, -1, 0), (8, 2, 0), (12, 2, 1)])
+def test_passes_bounded_by_positions_in_use(torch_cuda, mode, shape):
+    """Most frames stop at the pre-check and the rest never stop: after the first compaction
+    the running frames fill only the first frame blocks, and the check and bit passes skip
+    every block behind them. A frame count that is not a multiple of the block size, the
+    stopped frames scattered (not a prefix); outputs of every frame equal the oracle's,
+    with early stop and, for the same frames, without (no compaction)."""
+    code = inputs.cfg_regular_576()
+    F = 2077
+    rng = np.random.default_rng(31)
+    llr = inputs.all_zero_awgn_llr(F, code.N, 0.5, code.design_rate, 32)
+    stop = rng.permutation(F)[: F - 300]  # 1777 frames are codewords at the pre-check
+    llr[stop] = np.abs(llr[stop]) + 1.0
+    for es in (True, False):
+        want = oracle_decode(code, llr, 17, mode, early_stop=es)
+        if es:
+            assert (want[1][stop] == 0).all() and (want[1] > 12).sum() > 200
+        got = staged_decode(torch_cuda, code, llr, 17, mode, shape, early_stop=es)
+        assert_parity(got, want, mode, f"bounded passes {shape} early_stop={es}")
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fixed"])
 def test_bits_only_outputs_match_oracle(torch_cuda, mode):
     """Decodes that ask for no posteriors take their final syndrome, and (without early
     stop) their output bits, from the decisions the last bit pass packs one byte per lane.
