@@ -13,7 +13,9 @@
 //            syndrome of the previous iteration's decision (eq. 1-2).
 //   k_var:   for every bit j and frame: s_j = r_j + sum of eta over M_j, ascending rows
 //            (eq. lambda_j); frames whose previous syndrome was zero are frozen there.
-// A final syndrome-only pass gives the status of frames that never stopped early.
+// A final syndrome-only pass gives the status of frames that never stopped early. With
+// early stop the running frames are compacted to the front now and then, and both passes
+// then skip the frame blocks behind the positions in use (comp[1]).
 #pragma once
 
 #include "../../include/ldpc.h"
