@@ -409,7 +409,9 @@ int ldpc_set_stream_group(ldpc_t *h, int32_t frames_per_group);
  * bring one row's gathered posteriors s_j and old messages for 32 x frames_per_lane
  * frames, completing on an mbarrier, while the warp computes an earlier row (Section
  * III's row reductions).
- *   warps_per_cta in {0 (automatic: 12), 1..12};
+ *   warps_per_cta in {0 (automatic: 12; for FP32 codes with compressed messages on rows
+ *                     of 16 slots, the largest of 12, 8 and 4 whose stages fit the
+ *                     device's shared memory), 1..12};
  *   stages in {-1 (off: one thread per row and frame vector loads its row itself),
  *              0 (automatic: 2), 2..8};
  *   frames_per_lane in {0 (automatic: the mode's 16-byte vector, 4 FP32 or 8 int16 frames),

@@ -75,6 +75,7 @@ struct ldpc {
     size_t dense_cap = 0;
     int32_t stream_group = -1;   // streaming: -1 no frame groups, 0 L2-sized groups, > 0 group size
     int l2_bytes = 0;
+    int smem_optin = 0;           // shared memory a CTA may opt in to on this device
     int32_t* counters = nullptr;  // [0] resident / cluster tile counter, [1] streaming done
                                   // count, [2] device error word (bounded waits that ran out),
                                   // [4..7] the debug checks' report (two 64-bit words)
@@ -136,11 +137,29 @@ static void free_stream_work(ldpc_t* h) {
 // Largest batch of one streaming decode (its grids put frame blocks on the y dimension).
 constexpr int32_t kMaxStreamFrames = 65535 * 32;
 
+// Warps per CTA of the staged check pass: the caller's, else the default; but an FP32 code
+// on rows of 16 slots keeps its messages compressed only with fewer warps (their stages do
+// not fit 12 warps' shared memory, and the decode would fall back to per-edge messages), so
+// there the automatic choice is the largest of 8 and 4 warps that fits (QC N=2304, 65536
+// frames, 10 iterations: 16.8 ms compressed with 8 warps against 23.3 ms per edge).
+static int32_t stage_warps_of(const ldpc_t* h) {
+    if (h->st_warps > 0) return h->st_warps;
+    if (h->mode != kModeFP32 || !h->st_msg || h->dg.ell_D == 0 || h->st_stages < 0) return kStageWarpsDefault;
+    if (h->w_rows > 0 && h->dg.n_classes > 256) return kStageWarpsDefault;
+    const int stages = h->st_stages > 0 ? h->st_stages : kStagesDefault;
+    const int vw = h->st_vw ? h->st_vw : 4;
+    for (int32_t w : {kStageWarpsDefault, 8, 4})
+        if (staged_smem_bytes(kModeFP32, vw, h->dg.ell_D, true, w, stages, h->w_rows > 0) <=
+            (size_t)h->smem_optin)
+            return w;
+    return kStageWarpsDefault;
+}
+
 // The staged check pass settings of a handle, applied to a streaming workspace.
 static void apply_staging(const ldpc_t* h, StreamWork& w) {
     w.err = h->counters + 2;
     w.num_sms = h->num_sms;
-    w.stage_warps = h->st_warps > 0 ? h->st_warps : kStageWarpsDefault;
+    w.stage_warps = stage_warps_of(h);
     w.stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
     w.stage_vw = h->st_vw;
     w.wait_limit = h->wait_limit;
@@ -315,6 +334,8 @@ static ldpc_t* create_from_graph(HostGraph& hg, int32_t mode, int32_t flags) {
     if (e != cudaSuccess) return bail(cuda_fail(e));
     e = cudaDeviceGetAttribute(&h->l2_bytes, cudaDevAttrL2CacheSize, h->device);
     if (e != cudaSuccess) return bail(cuda_fail(e));
+    e = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e));
     // the static scratch array of ldpc_decode_noalloc is mapped now, so that the entry
     // point never maps or allocates anything itself
     if ((rc = noalloc_setup(h->device)) != LDPC_OK) return bail(fail(rc));
@@ -389,7 +410,7 @@ int ldpc_impl::handle_view(ldpc_t* h, HandleView* v) {
                     &h->last_launches, h->w_rows, h->w_alpha};
     v->num_sms = h->num_sms;
     v->err = h->counters + 2;
-    v->stage_warps = h->st_warps > 0 ? h->st_warps : kStageWarpsDefault;
+    v->stage_warps = stage_warps_of(h);
     v->stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
     v->stage_vw = h->st_vw;
     v->wait_limit = h->wait_limit;
@@ -760,7 +781,8 @@ static int autotune_stream(ldpc_t* h, int32_t frames, int32_t max_iter, float* b
     // of 16 slots fit more warps), and the unstaged kernel
     // (shapes whose shared memory does not fit run the unstaged kernel and lose)
     static const int32_t shapes[][3] = {{8, 3, 0}, {12, 2, 0}, {6, 3, 0}, {4, 4, 0}, {8, 2, 0},
-                                        {12, 3, 0}, {8, 4, 0}, {12, 2, 2}, {8, 3, 2}, {0, -1, 0}};
+                                        {12, 3, 0}, {8, 4, 0}, {4, 2, 0}, {6, 2, 0}, {12, 2, 2},
+                                        {8, 3, 2}, {0, -1, 0}};
     constexpr int n_shapes = (int)(sizeof(shapes) / sizeof(shapes[0]));
     // FP32 on the padded layout: every staged shape with compressed and with per-edge
     // messages (the unstaged kernel keeps per-edge messages)
@@ -1012,7 +1034,7 @@ int ldpc_get_stream_messages(const ldpc_t* h, int32_t* compressed) {
 int ldpc_get_stream_staging(const ldpc_t* h, int32_t* warps_per_cta, int32_t* stages,
                             int32_t* frames_per_lane) {
     if (!h) return fail(LDPC_ERR_BAD_POINTER);
-    if (warps_per_cta) *warps_per_cta = h->st_warps > 0 ? h->st_warps : kStageWarpsDefault;
+    if (warps_per_cta) *warps_per_cta = stage_warps_of(h);
     if (stages) *stages = h->st_stages < 0 ? 0 : (h->st_stages > 0 ? h->st_stages : kStagesDefault);
     if (frames_per_lane) *frames_per_lane = h->st_vw;
     return LDPC_OK;

@@ -77,6 +77,13 @@ def test_staging_settings_round_trip(torch_cuda):
         with pytest.raises(LdpcError):
             dec.set_stream_staging(*bad)
     dec.close()
+    # rows of 16 slots: compressed FP32 stages do not fit 12 warps' shared memory, so the
+    # automatic shape takes 8 warps and keeps the messages compressed; fixed point keeps 12
+    qc = Decoder.from_code(inputs.cfg_qc_2304())
+    assert qc.stream_staging() == (8, 2, 0) and qc.stream_messages_compressed()
+    qc.set_mode("fixed")
+    assert qc.stream_staging() == (12, 2, 0) and not qc.stream_messages_compressed()
+    qc.close()
 
 
 @pytest.mark.parametrize("mode", ["fp32", "fixed"])
